@@ -1,0 +1,250 @@
+/*
+ * hpvm.h -- C-ABI of the GB300 runtime for HPVM hierarchical dataflow graphs
+ * (Kotsifakou et al., "HPVM: A Portable Virtual Instruction Set for
+ * Heterogeneous Parallel Systems", arXiv 1611.00860).
+ *
+ * The calls mirror the paper's intrinsics (Table 1 and the intrinsic list of
+ * Section 3.2): a program builds a hierarchical dataflow graph (DFG) of
+ * internal nodes (which only hold child graphs), allocation leaves and
+ * compute leaves, connects them with ordinary edges, binds parent inputs to
+ * child inputs, then launches the graph on a CUDA stream and waits for it.
+ * The runtime lowers the one graph shape it supports -- the sgemm example of
+ * Section 5.1 -- onto hand-written sm_103a kernels.
+ *
+ * Conventions shared by every call
+ *   - Every function returns HPVM_OK (0) or a negative HPVM_ERR_* code and
+ *     never aborts. On error, hpvm_last_error() returns a message for the
+ *     calling thread; nothing the call would have created is created.
+ *   - Handles (hpvm_ctx, hpvm_node, hpvm_edge, hpvm_graph) are opaque. Nodes
+ *     and edges belong to the context that created them and are freed by
+ *     hpvm_cleanup(). A graph handle returned by hpvm_launch() is freed by a
+ *     hpvm_wait() that returns HPVM_OK or an error other than HPVM_ERR_TIMEOUT.
+ *   - Pointers inside argument records are device pointers (CUDA device or
+ *     managed memory), or host pointers previously registered with
+ *     hpvm_track_mem(). They are borrowed: the caller keeps them alive and
+ *     leaves them untouched from hpvm_launch() until hpvm_wait() returns.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef HPVM_GB300_HPVM_H
+#define HPVM_GB300_HPVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HPVM_API __attribute__((visibility("default")))
+#else
+#define HPVM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+#define HPVM_OK 0
+#define HPVM_ERR_INVALID_ARG (-1)   /* null handle, bad enum, bad port number */
+#define HPVM_ERR_INVALID_GRAPH (-2) /* breaks a rule of Section 3.1/3.2 */
+#define HPVM_ERR_UNSUPPORTED (-3)   /* valid graph the runtime cannot lower */
+#define HPVM_ERR_SHAPE (-4)         /* ld < rows, buffer bytes too small, ... */
+#define HPVM_ERR_ALIGN (-5)         /* operand alignment a kernel needs */
+#define HPVM_ERR_CUDA (-6)          /* a CUDA runtime/driver call failed */
+#define HPVM_ERR_TIMEOUT (-7)       /* hpvm_wait ran out of time */
+#define HPVM_ERR_DEVICE_FAULT (-8)  /* a kernel reported a bounded wait expired */
+#define HPVM_ERR_NO_DEVICE (-9)     /* call needs a device; context is host-only */
+#define HPVM_ERR_OUT_OF_MEMORY (-10)
+
+/* ---- node kinds: the node function a node runs ------------------------ */
+#define HPVM_NODE_INTERNAL 0   /* graph intrinsics only (Section 3.2) */
+#define HPVM_NODE_ALLOCATION 1 /* allocation leaf (Section 4.4): tile memory */
+#define HPVM_NODE_SGEMM_LEAF 2 /* the SgemmLeaf node function (Section 5.1) */
+
+/* ---- edge replication (Section 3.1) ----------------------------------- */
+#define HPVM_ONE_TO_ONE 0 /* instance i -> instance i; grids must match */
+#define HPVM_ALL_TO_ALL 1 /* every source instance -> every sink instance */
+
+/* ---- leaf precision tiers (how the runtime lowers the SgemmLeaf) ------
+ * FP32_DFG: one CUDA thread per leaf instance, one CTA per internal
+ *           instance, the Allocation node's tiles in shared memory (the
+ *           mapping of Section 4.4 taken literally); FP32 FMA.
+ * FP32:     register-tiled FP32 CUDA-core kernel (same result definition).
+ * BF16X3:   tcgen05 tensor cores, each FP32 operand split into BF16
+ *           hi + lo, three products hi*hi + hi*lo + lo*hi, FP32 accumulate.
+ * BF16:     tcgen05 tensor cores, operands rounded to BF16, FP32 accumulate.
+ */
+#define HPVM_TIER_FP32_DFG 0
+#define HPVM_TIER_FP32 1
+#define HPVM_TIER_BF16X3 2
+#define HPVM_TIER_BF16 3
+
+/* A replication extent that is not a constant but the value of input port p
+ * of the parent node at run time (the example passes its own block_x,
+ * block_y, grid_x, grid_y arguments to createNode2D, Section 5.1). */
+#define HPVM_DIM_FROM_INPUT(p) (-1 - (int64_t)(p))
+
+/* launch flags (hpvm_sgemm_root_args.flags) */
+#define HPVM_LAUNCH_NO_EVENT 1 /* no completion event: hpvm_wait syncs the
+                                  stream (use inside CUDA graph capture) */
+
+typedef struct hpvm_ctx hpvm_ctx;
+typedef struct hpvm_node hpvm_node;
+typedef struct hpvm_edge hpvm_edge;
+typedef struct hpvm_graph hpvm_graph;
+
+/* ---- the argument record of the sgemm root ----------------------------
+ * The first 88 bytes are the paper's packed %struct.RootIn (Section 5.1:
+ * A, bytesA, lda, B, bytesB, ldb, C, bytesC, ldc, k, alpha, beta, block_x,
+ * block_y, grid_x, grid_y; the host code mallocs 88 bytes and packs them).
+ * Root input port p is field p of this record for p = 0..15; the trailer
+ * adds M (port 16), N (17), transA (18), transB (19), which the example
+ * leaves implicit, then two launch options that are not graph inputs.
+ *
+ * Meaning: C <- alpha * op(A) * op(B) + beta * C with column-major storage
+ * (element (r, c) of a matrix with leading dimension ld at r + c*ld);
+ * op(A) = A (M x K, lda >= M) when transA == 0, else A^T (A stored K x M,
+ * lda >= K); op(B) = B (K x N, ldb >= K) when transB == 0, else B^T (B
+ * stored N x K, ldb >= N). The example's form is transA = 0, transB = 1.
+ * C is M x N, ldc >= M. bytesX is the size of buffer X in bytes. When
+ * beta == 0, C is not read. k = K. */
+#pragma pack(push, 1)
+typedef struct hpvm_sgemm_root_args {
+  float* A;
+  int64_t bytesA;
+  int32_t lda;
+  float* B;
+  int64_t bytesB;
+  int32_t ldb;
+  float* C;
+  int64_t bytesC;
+  int32_t ldc;
+  int32_t k;
+  float alpha;
+  float beta;
+  int32_t block_x;
+  int32_t block_y;
+  int32_t grid_x;
+  int32_t grid_y;
+  /* trailer */
+  int32_t M;
+  int32_t N;
+  int32_t transA;
+  int32_t transB;
+  int32_t tier;  /* HPVM_TIER_* */
+  int32_t flags; /* HPVM_LAUNCH_* */
+} hpvm_sgemm_root_args;
+#pragma pack(pop)
+
+#define HPVM_ROOTIN_PAPER_BYTES 88
+#define HPVM_SGEMM_ROOT_ARGS_BYTES 112
+
+/* What a launch ran (filled by hpvm_graph_info). */
+typedef struct hpvm_launch_info {
+  int32_t tier;
+  int32_t kernels;       /* kernels launched for this graph */
+  int32_t grid_x, grid_y, grid_z;  /* grid of the main (leaf) kernel */
+  int32_t block_threads; /* threads per CTA of the main kernel */
+  int32_t tile_m, tile_n, tile_k;  /* output tile per CTA, K slab */
+  int32_t smem_bytes;    /* dynamic shared memory of the main kernel */
+  int32_t literal;       /* 1: internal instance == CTA, leaf instance ==
+                            thread (Section 4.4 mapping); 0: re-tiled */
+  int64_t workspace_bytes;
+  int64_t h2d_bytes, d2h_bytes; /* memory-tracker copies this launch made */
+} hpvm_launch_info;
+
+/* ---- runtime set-up (llvm.hpvm.init / llvm.hpvm.cleanup, Section 5.1) --
+ * device >= 0: a context on that CUDA device (made current for the calling
+ * thread). device < 0: a host-only context that can build and validate
+ * graphs but not launch them (HPVM_ERR_NO_DEVICE from hpvm_launch). */
+HPVM_API int hpvm_init(int device, hpvm_ctx** out);
+/* Frees every node, edge, graph handle, tracked device copy and owned
+ * workspace of the context, after synchronising its device. */
+HPVM_API int hpvm_cleanup(hpvm_ctx* ctx);
+
+/* ---- graph intrinsics (Table 1; Section 3.2 list) ----------------------
+ * createNode / createNode{1,2,3}D: a child of `parent` (NULL for the root)
+ * running node function `kind`, with `ndims` in 0..3 (0 = one instance) and
+ * extents dims[0..ndims-1], each > 0 or HPVM_DIM_FROM_INPUT(p). Only an
+ * internal node may be a parent. */
+HPVM_API int hpvm_create_node(hpvm_ctx* ctx, hpvm_node* parent, int kind, int ndims,
+                     const int64_t* dims, hpvm_node** out);
+/* createEdge(Src, Dst, ReplTy, sp, dp, Stream): from output sp of src to
+ * input dp of dst; both children of the same internal node; repl is
+ * HPVM_ONE_TO_ONE or HPVM_ALL_TO_ALL; one-to-one needs identical grids.
+ * stream != 0 (a streaming edge) is rejected with HPVM_ERR_UNSUPPORTED.
+ * `out` may be NULL. */
+HPVM_API int hpvm_create_edge(hpvm_node* src, hpvm_node* dst, int repl, int sp, int dp,
+                     int stream, hpvm_edge** out);
+/* bind.input(N, ip, ic, Stream): input ip of N's parent feeds input ic of N. */
+HPVM_API int hpvm_bind_input(hpvm_node* child, int ip, int ic, int stream);
+/* bind.output(N, oc, op, Stream): output oc of N becomes output op of its
+ * parent. */
+HPVM_API int hpvm_bind_output(hpvm_node* child, int oc, int op, int stream);
+
+/* ---- query intrinsics, host side (Table 1) ----------------------------- */
+HPVM_API int hpvm_get_parent_node(hpvm_node* node, hpvm_node** out); /* NULL for root */
+HPVM_API int hpvm_get_num_dims(hpvm_node* node, int* out);
+/* Static extent of dimension dim (or HPVM_DIM_FROM_INPUT(p)); dims beyond
+ * the node's rank report 1. */
+HPVM_API int hpvm_get_num_node_instances(hpvm_node* node, int dim, int64_t* out);
+
+/* Check the graph under `root` against the rules of Sections 3.1-3.2:
+ * root is a single-instance internal node; leaves have no children; edges
+ * join siblings, ports are in range, one-to-one edges join equal grids, no
+ * cycle of ordinary edges; every leaf input is fed exactly once. */
+HPVM_API int hpvm_validate(hpvm_node* root);
+
+/* ---- host integration (llvm.hpvm.launch / llvm.hpvm.wait) -------------
+ * Launch the graph under `root` asynchronously on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream) with the argument record
+ * `args` (hpvm_sgemm_root_args, args_size >= 112). stream_graph != 0 (a
+ * graph with streaming edges) is rejected with HPVM_ERR_UNSUPPORTED.
+ * Errors found before any work is enqueued (graph, shape, alignment) leave
+ * the stream untouched. */
+HPVM_API int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args,
+                size_t args_size, int stream_graph, void* cuda_stream,
+                hpvm_graph** out);
+/* Wait until the launched graph finished, at most timeout_ms milliseconds
+ * (< 0: no limit). HPVM_ERR_TIMEOUT leaves the handle valid; any other
+ * return frees it. HPVM_ERR_DEVICE_FAULT: a kernel gave up a bounded wait
+ * (the results are not valid). */
+HPVM_API int hpvm_wait(hpvm_graph* graph, int64_t timeout_ms);
+/* Copy the description of what `graph` launched into *out. */
+HPVM_API int hpvm_graph_info(hpvm_graph* graph, hpvm_launch_info* out);
+
+/* ---- memory tracker (Section 3.3) -------------------------------------
+ * track_mem: host region [p, p+bytes) may be named in argument records; its
+ * latest copy is the host's. A launch copies it to a device copy the
+ * runtime owns when the copy there is stale and the leaf reads it (A, B;
+ * C unless beta == 0), and marks C's latest copy as the device's.
+ * request_mem: make the host copy of [p, p+bytes) current (waits for the
+ * context's work, then copies device -> host if needed).
+ * untrack_mem: forget the region and free its device copy. */
+HPVM_API int hpvm_track_mem(hpvm_ctx* ctx, void* p, int64_t bytes);
+HPVM_API int hpvm_request_mem(hpvm_ctx* ctx, void* p, int64_t bytes);
+HPVM_API int hpvm_untrack_mem(hpvm_ctx* ctx, void* p);
+
+/* ---- workspace ----------------------------------------------------------
+ * Device scratch the tensor-core tiers use (split operands). Bytes a launch
+ * of `root` with `args` needs: */
+HPVM_API int hpvm_workspace_size(hpvm_ctx* ctx, hpvm_node* root, const void* args,
+                        size_t args_size, size_t* out);
+/* Use caller-owned device memory as workspace (NULL/0: the runtime
+ * allocates and caches its own). Must stay valid while launches use it. */
+HPVM_API int hpvm_set_workspace(hpvm_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* ---- planning -----------------------------------------------------------
+ * Leaf instance grid and internal grid for an M x N result in `tier`:
+ * the tile each kernel computes natively (block_x x block_y outputs per
+ * internal instance) and the grid that covers M x N with it. */
+HPVM_API int hpvm_plan_sgemm(int tier, int64_t M, int64_t N, int64_t K, int32_t* block_x,
+                    int32_t* block_y, int32_t* grid_x, int32_t* grid_y);
+
+/* Thread-local message of the last failed call ("" if none). */
+HPVM_API const char* hpvm_last_error(void);
+/* ABI version (major * 100 + minor). */
+HPVM_API int hpvm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPVM_GB300_HPVM_H */

@@ -1,0 +1,249 @@
+"""ctypes binding of the C-ABI in ``include/hpvm.h``.
+
+Argument marshalling only: every function here forwards to the function of
+the same name in ``_lib/libhpvm_gb300.so`` and raises ``HpvmError`` when it
+returns a negative status. There is no other code path: when the library is
+missing, importing this module raises ``ImportError`` (call
+``paper_1611_00860_gb300.build.build()`` first).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhpvm_gb300.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hpvm.h")
+
+# ---- constants of include/hpvm.h -------------------------------------------
+HPVM_OK = 0
+HPVM_ERR_INVALID_ARG = -1
+HPVM_ERR_INVALID_GRAPH = -2
+HPVM_ERR_UNSUPPORTED = -3
+HPVM_ERR_SHAPE = -4
+HPVM_ERR_ALIGN = -5
+HPVM_ERR_CUDA = -6
+HPVM_ERR_TIMEOUT = -7
+HPVM_ERR_DEVICE_FAULT = -8
+HPVM_ERR_NO_DEVICE = -9
+HPVM_ERR_OUT_OF_MEMORY = -10
+
+HPVM_NODE_INTERNAL = 0
+HPVM_NODE_ALLOCATION = 1
+HPVM_NODE_SGEMM_LEAF = 2
+
+HPVM_ONE_TO_ONE = 0
+HPVM_ALL_TO_ALL = 1
+
+HPVM_TIER_FP32_DFG = 0
+HPVM_TIER_FP32 = 1
+HPVM_TIER_BF16X3 = 2
+HPVM_TIER_BF16 = 3
+
+HPVM_LAUNCH_NO_EVENT = 1
+HPVM_ROOTIN_PAPER_BYTES = 88
+HPVM_SGEMM_ROOT_ARGS_BYTES = 112
+
+
+def HPVM_DIM_FROM_INPUT(p: int) -> int:
+    return -1 - int(p)
+
+
+class HpvmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hpvm error {code}: {msg}")
+        self.code = code
+
+
+class RootArgs(ctypes.Structure):
+    """hpvm_sgemm_root_args: the paper's packed RootIn record + trailer."""
+    _pack_ = 1
+    _fields_ = [
+        ("A", ctypes.c_void_p), ("bytesA", ctypes.c_int64), ("lda", ctypes.c_int32),
+        ("B", ctypes.c_void_p), ("bytesB", ctypes.c_int64), ("ldb", ctypes.c_int32),
+        ("C", ctypes.c_void_p), ("bytesC", ctypes.c_int64), ("ldc", ctypes.c_int32),
+        ("k", ctypes.c_int32), ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+        ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32),
+        ("grid_x", ctypes.c_int32), ("grid_y", ctypes.c_int32),
+        ("M", ctypes.c_int32), ("N", ctypes.c_int32),
+        ("transA", ctypes.c_int32), ("transB", ctypes.c_int32),
+        ("tier", ctypes.c_int32), ("flags", ctypes.c_int32),
+    ]
+
+
+class LaunchInfo(ctypes.Structure):
+    _fields_ = [
+        ("tier", ctypes.c_int32), ("kernels", ctypes.c_int32),
+        ("grid_x", ctypes.c_int32), ("grid_y", ctypes.c_int32), ("grid_z", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32), ("tile_k", ctypes.c_int32),
+        ("smem_bytes", ctypes.c_int32), ("literal", ctypes.c_int32),
+        ("workspace_bytes", ctypes.c_int64),
+        ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()'); there is no fallback path")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, I64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "hpvm_init": (I, [I, PP]),
+        "hpvm_cleanup": (I, [P]),
+        "hpvm_create_node": (I, [P, P, I, I, ctypes.POINTER(ctypes.c_int64), PP]),
+        "hpvm_create_edge": (I, [P, P, I, I, I, I, PP]),
+        "hpvm_bind_input": (I, [P, I, I, I]),
+        "hpvm_bind_output": (I, [P, I, I, I]),
+        "hpvm_get_parent_node": (I, [P, PP]),
+        "hpvm_get_num_dims": (I, [P, ctypes.POINTER(ctypes.c_int)]),
+        "hpvm_get_num_node_instances": (I, [P, I, ctypes.POINTER(ctypes.c_int64)]),
+        "hpvm_validate": (I, [P]),
+        "hpvm_launch": (I, [P, P, P, SZ, I, P, PP]),
+        "hpvm_wait": (I, [P, I64]),
+        "hpvm_graph_info": (I, [P, ctypes.POINTER(LaunchInfo)]),
+        "hpvm_track_mem": (I, [P, P, I64]),
+        "hpvm_request_mem": (I, [P, P, I64]),
+        "hpvm_untrack_mem": (I, [P, P]),
+        "hpvm_workspace_size": (I, [P, P, P, SZ, ctypes.POINTER(ctypes.c_size_t)]),
+        "hpvm_set_workspace": (I, [P, P, SZ]),
+        "hpvm_plan_sgemm": (I, [I, I64, I64, I64] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+        "hpvm_last_error": (ctypes.c_char_p, []),
+        "hpvm_version": (I, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/hpvm.h declares."""
+    with open(HEADER_PATH) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"HPVM_API\s+[\w\s\*]*?\b(hpvm_\w+)\s*\(", text)))
+
+
+def _check(rc: int) -> None:
+    if rc != HPVM_OK:
+        raise HpvmError(rc, LIB.hpvm_last_error().decode())
+
+
+# ---- the C-ABI, one wrapper per function --------------------------------------
+def hpvm_init(device: int) -> int:
+    out = ctypes.c_void_p()
+    _check(LIB.hpvm_init(int(device), ctypes.byref(out)))
+    return out.value
+
+
+def hpvm_cleanup(ctx: int) -> None:
+    _check(LIB.hpvm_cleanup(ctx))
+
+
+def hpvm_create_node(ctx: int, parent: int | None, kind: int, dims=()) -> int:
+    nd = len(dims)
+    arr = (ctypes.c_int64 * max(nd, 1))(*[int(d) for d in dims]) if nd else None
+    out = ctypes.c_void_p()
+    _check(LIB.hpvm_create_node(ctx, parent, int(kind), nd, arr, ctypes.byref(out)))
+    return out.value
+
+
+def hpvm_create_edge(src: int, dst: int, repl: int, sp: int, dp: int, stream: bool = False) -> int:
+    out = ctypes.c_void_p()
+    _check(LIB.hpvm_create_edge(src, dst, int(repl), int(sp), int(dp), int(bool(stream)), ctypes.byref(out)))
+    return out.value
+
+
+def hpvm_bind_input(child: int, ip: int, ic: int, stream: bool = False) -> None:
+    _check(LIB.hpvm_bind_input(child, int(ip), int(ic), int(bool(stream))))
+
+
+def hpvm_bind_output(child: int, oc: int, op: int, stream: bool = False) -> None:
+    _check(LIB.hpvm_bind_output(child, int(oc), int(op), int(bool(stream))))
+
+
+def hpvm_get_parent_node(node: int) -> int | None:
+    out = ctypes.c_void_p()
+    _check(LIB.hpvm_get_parent_node(node, ctypes.byref(out)))
+    return out.value
+
+
+def hpvm_get_num_dims(node: int) -> int:
+    out = ctypes.c_int()
+    _check(LIB.hpvm_get_num_dims(node, ctypes.byref(out)))
+    return out.value
+
+
+def hpvm_get_num_node_instances(node: int, dim: int) -> int:
+    out = ctypes.c_int64()
+    _check(LIB.hpvm_get_num_node_instances(node, int(dim), ctypes.byref(out)))
+    return out.value
+
+
+def hpvm_validate(root: int) -> None:
+    _check(LIB.hpvm_validate(root))
+
+
+def hpvm_launch(ctx: int, root: int, args: RootArgs, stream_graph: bool = False,
+                cuda_stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(LIB.hpvm_launch(ctx, root, ctypes.byref(args), ctypes.sizeof(args),
+                           int(bool(stream_graph)), cuda_stream or None, ctypes.byref(out)))
+    return out.value
+
+
+def hpvm_wait(graph: int, timeout_ms: int = -1) -> None:
+    _check(LIB.hpvm_wait(graph, int(timeout_ms)))
+
+
+def hpvm_graph_info(graph: int) -> LaunchInfo:
+    info = LaunchInfo()
+    _check(LIB.hpvm_graph_info(graph, ctypes.byref(info)))
+    return info
+
+
+def hpvm_track_mem(ctx: int, ptr: int, nbytes: int) -> None:
+    _check(LIB.hpvm_track_mem(ctx, ptr, int(nbytes)))
+
+
+def hpvm_request_mem(ctx: int, ptr: int, nbytes: int) -> None:
+    _check(LIB.hpvm_request_mem(ctx, ptr, int(nbytes)))
+
+
+def hpvm_untrack_mem(ctx: int, ptr: int) -> None:
+    _check(LIB.hpvm_untrack_mem(ctx, ptr))
+
+
+def hpvm_workspace_size(ctx: int, root: int, args: RootArgs) -> int:
+    out = ctypes.c_size_t()
+    _check(LIB.hpvm_workspace_size(ctx, root, ctypes.byref(args), ctypes.sizeof(args), ctypes.byref(out)))
+    return out.value
+
+
+def hpvm_set_workspace(ctx: int, ptr: int | None, nbytes: int) -> None:
+    _check(LIB.hpvm_set_workspace(ctx, ptr, int(nbytes)))
+
+
+def hpvm_plan_sgemm(tier: int, M: int, N: int, K: int) -> tuple[int, int, int, int]:
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(LIB.hpvm_plan_sgemm(int(tier), int(M), int(N), int(K), *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def hpvm_last_error() -> str:
+    return LIB.hpvm_last_error().decode()
+
+
+def hpvm_version() -> int:
+    return LIB.hpvm_version()

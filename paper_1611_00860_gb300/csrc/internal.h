@@ -1,0 +1,65 @@
+// Internal interface between the graph runtime (runtime.cpp) and the kernel
+// launchers (fp32_leaf.cu, tc_leaf.cu). Not part of the C-ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+namespace hpvm {
+
+// One lowered sgemm leaf: C <- alpha*op(A)*op(B) + beta*C, column-major.
+struct SgemmDesc {
+  int64_t M = 0, N = 0, K = 0;
+  const float* A = nullptr;
+  int64_t lda = 1;
+  const float* B = nullptr;
+  int64_t ldb = 1;
+  float* C = nullptr;
+  int64_t ldc = 1;
+  float alpha = 1.f, beta = 0.f;
+  int transA = 0, transB = 0;
+};
+
+// What a launcher ran (copied into hpvm_launch_info).
+struct KernelReport {
+  int kernels = 0;
+  int grid_x = 0, grid_y = 0, grid_z = 0;
+  int block_threads = 0;
+  int tile_m = 0, tile_n = 0, tile_k = 0;
+  int smem_bytes = 0;
+  int literal = 0;
+  int64_t workspace_bytes = 0;
+};
+
+// Status word the tensor-core kernels write when a bounded wait expires.
+// Bits: which wait gave up (see tc_leaf.cu).
+struct DeviceStatus {
+  int* dev = nullptr;   // device-visible address (mapped pinned memory)
+  int* host = nullptr;  // host address of the same word
+};
+
+// ---- FP32 CUDA-core leaves (fp32_leaf.cu) ---------------------------------
+// Literal Section 4.4 mapping: CTA (bx, by) = internal instance, thread
+// (tx, ty) = leaf instance, tiles of the Allocation node in shared memory.
+cudaError_t launch_fp32_dfg(const SgemmDesc& d, int block, int grid_x,
+                            int grid_y, size_t tile_bytes, cudaStream_t s,
+                            KernelReport* rep);
+// Register-tiled FP32 kernel.
+cudaError_t launch_fp32_tiled(const SgemmDesc& d, cudaStream_t s,
+                              KernelReport* rep);
+void fp32_tiled_tile(int* tm, int* tn);
+
+// ---- tensor-core leaves (tc_leaf.cu) --------------------------------------
+// tier: 2 = BF16x3 split, 3 = BF16.
+size_t tc_workspace_bytes(const SgemmDesc& d, int tier);
+// Returns a cudaError_t; on a host-side precondition failure returns
+// cudaErrorInvalidValue and fills *err.
+cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes,
+                      const DeviceStatus& st, cudaStream_t s,
+                      KernelReport* rep, std::string* err);
+void tc_tile(int tier, int* tm, int* tn);
+
+}  // namespace hpvm

@@ -14,6 +14,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+# Build the CUDA library and the oracle's C checker before any test module
+# imports them (both builds are no-ops when up to date).
+from paper_1611_00860_gb300.build import build as _build_lib  # noqa: E402
+from oracle.build import build as _build_oracle  # noqa: E402
+
+_build_lib()
+_build_oracle()
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds")
