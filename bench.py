@@ -1,0 +1,389 @@
+"""Benchmark of the sgemm dataflow graph on GB300.
+
+Default (``--impl gb300``): one step is one launch of the whole sgemm DFG
+through the C-ABI (``hpvm_launch``: the BF16 split pre-pass of A and B, then
+the tcgen05 leaf kernel) on the large workload, M = N = K = 8192, op(A) = A,
+op(B) = B^T (column-major), A, B, C ~ N(0,1), alpha = beta = 1. Inputs are
+resident in HBM when the timed region starts and larger than L2 (768 MiB of
+FP32 operands plus 512 MiB of split planes), so no L2 flush is needed.
+
+Printed (rank 0, one JSON line): useful TFLOP/s (2*M*N*K per step) of the
+split-BF16x3 DFG; the roofline of its leaf kernel (tensor FLOP = 3 products
+x 2*M*N*K, over the kernel's own CUDA-event time, against the measured dense
+BF16 peak); the plain FP32 CUDA-core DFG on the same workload; the normwise
+error of both against the FP64 oracle on sampled blocks (computed in the
+CPU-baseline leg, which times that oracle); the end-to-end figure through
+the memory tracker with host buffers; SM clocks sampled during the timed
+region; the number of kernels launched.
+
+``--impl reference``: the FP64 oracle timed on the host cores, each step one
+256 x 256 output block of the same workload (full K), rank 0 only.
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own replica of
+the workload (weak scaling, no data exchange); value = FLOP of all ranks /
+max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sgemm-DFG TFLOP/s and % of roofline at ≤5e-6 rel. err, split-BF16 vs plain FP32"
+WORKLOAD = ("sgemm DFG, M=N=K=8192, op(A)=A, op(B)=B^T column-major, A,B,C ~ N(0,1) seed 1, "
+            "alpha=beta=1; leaf = split-BF16x3 tcgen05 (3 products, FP32 accumulate)")
+WORKLOAD_REF = ("sgemm DFG, M=N=K=8192, op(A)=A, op(B)=B^T column-major, A,B,C ~ N(0,1) seed 1, "
+                "alpha=beta=1; FP64 oracle on the host cores")
+N_SIZE = 8192
+TILE_BLOCK = 256
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_SIZE, help="M = N = K")
+    ap.add_argument("--fp32-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "_source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("tc_leaf.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1611_00860_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(src_hash: str):
+    """DRAM bytes per launch of the leaf kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sgemm_tc_bf16x3_8192.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel source sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
+    m_bytes = re.search(r"dram bytes per launch \(read \+ write\):\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != src_hash:
+        return None
+    return float(m_bytes.group(1))
+
+
+def gpu_id(local: int) -> str:
+    """nvidia-smi --id of the CUDA device `local` (its UUID when torch knows it)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u and u != "None":
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [x for x in vis.split(",") if x.strip()]
+    return parts[local] if local < len(parts) else str(local)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"hpvm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def cpu_oracle_leg(p, got_blocks_fn, seconds: float):
+    """Time the oracle (as it stands) on sampled 256 x 256 blocks of the
+    workload for about ``seconds``; also return the blocks' FP64 values."""
+    from oracle import sgemm as O
+    blocks = __import__("workloads").sample_blocks(p.M, p.N, bs=TILE_BLOCK, count=16)
+    refs, t0, done = [], time.perf_counter(), 0
+    flops = 0
+    for (i0, j0) in blocks:
+        refs.append(((i0, j0), O.sgemm_block_f64(p, i0, j0, TILE_BLOCK, TILE_BLOCK)))
+        done += 1
+        flops += 2 * min(TILE_BLOCK, p.M - i0) * min(TILE_BLOCK, p.N - j0) * p.K
+        if time.perf_counter() - t0 > seconds and done >= 3:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"{done} sampled {TILE_BLOCK}x{TILE_BLOCK} output blocks of the "
+                      f"{p.M}x{p.N}x{p.K} workload (full K), FP64 triple loop, {dt:.1f} s"}, refs
+
+
+def block_error(C_dev, p, refs):
+    import workloads as W
+    from oracle import sgemm as O
+    Cv = W.col_major(C_dev, p.M, p.N, p.ldc)
+    pairs = [(Cv[i0:i0 + TILE_BLOCK, j0:j0 + TILE_BLOCK].double().cpu().numpy(), r)
+             for (i0, j0), r in refs]
+    return O.block_errors(pairs)
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads as W
+    from oracle import sgemm as O
+    p = W.large_dfg_problem(args.n)
+    blocks = W.sample_blocks(p.M, p.N, bs=TILE_BLOCK, count=max(16, args.steps + args.warmup))
+    seq = [blocks[i % len(blocks)] for i in range(args.steps + args.warmup)]
+    for (i0, j0) in seq[:args.warmup]:
+        O.sgemm_block_f64(p, i0, j0, TILE_BLOCK, TILE_BLOCK)
+    t0 = time.perf_counter()
+    flops = 0
+    for (i0, j0) in seq[args.warmup:]:
+        O.sgemm_block_f64(p, i0, j0, TILE_BLOCK, TILE_BLOCK)
+        flops += 2 * min(TILE_BLOCK, p.M - i0) * min(TILE_BLOCK, p.N - j0) * p.K
+    dt = time.perf_counter() - t0
+    v = flops / dt / 1e12
+    sample = (f"each step one {TILE_BLOCK}x{TILE_BLOCK} output block of the {p.M}x{p.N}x{p.K} "
+              "workload (full K), FP64 triple loop on the host cores")
+    print(json.dumps({
+        "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD_REF, "M": p.M, "N": p.N, "K": p.K},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": O.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import workloads as W
+    from paper_1611_00860_gb300 import _lib as H
+    from paper_1611_00860_gb300.sgemm import SgemmDFG
+
+    peaks = load_peaks()
+    n = args.n
+    p = W.large_dfg_problem(n)
+    flop = 2.0 * p.M * p.N * p.K
+    A, B, C0 = (t.to(f"cuda:{local}") for t in (p.A, p.B, p.C))
+    C = C0.clone()
+    dfg = SgemmDFG(local)
+    stream = torch.cuda.current_stream(local)
+
+    def launch_args(tier, Cbuf):
+        return dfg.args_for(p.M, p.N, p.K, A, p.lda, B, p.ldb, Cbuf, p.ldc, p.alpha, p.beta,
+                            p.transA, p.transB, tier=tier)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(local)
+
+    def timed(tier, steps, warmup, Cbuf, clocks=False):
+        a = launch_args(tier, Cbuf)
+        dfg.ensure_workspace(a)
+        for _ in range(warmup):
+            dfg.wait(dfg.launch(a))
+        barrier()
+        sampler = ClockSampler(gpu_id(local)) if clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)  # let the sampler start before the load
+        H.hpvm_set_kernel_timing(dfg.ctx, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        graphs, kernels = [], 0
+        for _ in range(steps):
+            g = dfg.launch(a)
+            kernels += H.hpvm_graph_info(g).kernels
+            graphs.append(g)
+        ev1.record(stream)
+        barrier()
+        H.hpvm_set_kernel_timing(dfg.ctx, False)
+        kms, klaunch = H.hpvm_kernel_timing(dfg.ctx)
+        for g in graphs:
+            dfg.wait(g)
+        clk = sampler.stop() if sampler else None
+        ms = ev0.elapsed_time(ev1)
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), kms / max(1, klaunch), kernels, clk
+
+    # 1) correctness run of both tiers on a fresh C (checked below against the oracle)
+    C_bf = C0.clone()
+    dfg.wait(dfg.launch(launch_args(H.HPVM_TIER_BF16X3, C_bf)))
+    C_fp = C0.clone()
+    dfg.wait(dfg.launch(launch_args(H.HPVM_TIER_FP32, C_fp)))
+
+    # 2) timed split-BF16x3 DFG (headline)
+    ms_total, kern_ms, launches, clocks = timed(H.HPVM_TIER_BF16X3, args.steps, args.warmup, C, True)
+    ms_step = ms_total / args.steps
+    value = flop * world * args.steps / (ms_total * 1e-3) / 1e12
+    tensor_flop = 3 * flop
+    achieved = tensor_flop / (kern_ms * 1e-3) / 1e12
+    src_hash = kernel_source_hash()
+    traffic = traffic_from_profiles(src_hash)
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"], "traffic": traffic,
+                "peak_source": f"{peaks['_source']} dense BF16 burst (MEASURED_PEAKS.json bf16_tflops)",
+                "frac_of_sustained": achieved / peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]),
+                "kernel": "sgemm_tc<3>", "kernel_ms": kern_ms,
+                "algorithmic": "3 x 2*M*N*K tensor FLOP per launch", "kernel_source": src_hash}
+
+    # 3) plain FP32 CUDA-core DFG on the same workload
+    fp_total, fp_kern_ms, fp_launches, _ = timed(H.HPVM_TIER_FP32, args.fp32_steps, 2, C)
+    props = torch.cuda.get_device_properties(local)
+    fp32_peak = props.multi_processor_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32 = {"value": flop * world * args.fp32_steps / (fp_total * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "ms_per_step": fp_total / args.fp32_steps, "steps": args.fp32_steps,
+            "kernel_frac_of_fp32_peak": flop / (fp_kern_ms * 1e-3) / 1e12 / fp32_peak,
+            "fp32_peak_tflops": fp32_peak,
+            "fp32_peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x max SM clock"}
+
+    # 4) end to end through the memory tracker with pinned host buffers
+    hA, hB, hC = (t.pin_memory() for t in (p.A, p.B, p.C))
+    ctx = dfg.ctx
+    for t in (hA, hB, hC):
+        H.hpvm_track_mem(ctx, t.data_ptr(), t.numel() * 4)
+    from paper_1611_00860_gb300.sgemm import make_args
+    ha = make_args(p.M, p.N, p.K, hA.data_ptr(), hA.numel() * 4, p.lda, hB.data_ptr(),
+                   hB.numel() * 4, p.ldb, hC.data_ptr(), hC.numel() * 4, p.ldc, p.alpha, p.beta,
+                   p.transA, p.transB, H.HPVM_TIER_BF16X3)
+
+    def e2e_step():
+        for t in (hA, hB, hC):
+            H.hpvm_track_mem(ctx, t.data_ptr(), t.numel() * 4)  # host copy is the latest
+        g = H.hpvm_launch(ctx, dfg.nodes["root"], ha, False, stream.cuda_stream)
+        h2d = H.hpvm_graph_info(g).h2d_bytes
+        H.hpvm_wait(g, 60000)
+        H.hpvm_request_mem(ctx, hC.data_ptr(), hC.numel() * 4)
+        return h2d
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    h2d = 0
+    for _ in range(args.e2e_steps):
+        h2d = e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    for t in (hA, hB, hC):
+        H.hpvm_untrack_mem(ctx, t.data_ptr())
+    e2e = {"value": flop * world / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(hC.numel() * 4), "ms_per_step": e2e_s * 1e3,
+           "path": "hpvm_track_mem(A,B,C) + hpvm_launch + hpvm_wait + hpvm_request_mem(C), pinned host memory"}
+
+    # 5) CPU baseline (the oracle, timed) and the error of the runs of step 1
+    cpu, err = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, refs = cpu_oracle_leg(p, None, args.cpu_seconds)
+        err = {"bf16x3": block_error(C_bf, p, refs), "fp32": block_error(C_fp, p, refs),
+               "blocks": len(refs), "metric": "normwise ||C-C_ref||_F/||C_ref||_F over sampled blocks",
+               "tolerance": 5e-6}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "M": p.M, "N": p.N, "K": p.K, "transA": "N",
+                       "transB": "T", "tier": "bf16x3", "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (768 MiB FP32 operands + 512 MiB split planes); no flush"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches, "rel_err": err, "fp32_cuda_core": fp32,
+        }
+        print(json.dumps(line), flush=True)
+    dfg.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

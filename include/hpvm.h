@@ -239,6 +239,14 @@ HPVM_API int hpvm_set_workspace(hpvm_ctx* ctx, void* dev_ptr, size_t bytes);
 HPVM_API int hpvm_plan_sgemm(int tier, int64_t M, int64_t N, int64_t K, int32_t* block_x,
                     int32_t* block_y, int32_t* grid_x, int32_t* grid_y);
 
+/* ---- kernel timing ------------------------------------------------------
+ * When enabled, every launch records CUDA events on its stream right before
+ * and right after its main (leaf) kernel. hpvm_kernel_timing waits for the
+ * recorded events, returns the summed main-kernel time in milliseconds and
+ * the number of timed launches, and forgets them. */
+HPVM_API int hpvm_set_kernel_timing(hpvm_ctx* ctx, int enable);
+HPVM_API int hpvm_kernel_timing(hpvm_ctx* ctx, double* total_ms, int64_t* launches);
+
 /* Thread-local message of the last failed call ("" if none). */
 HPVM_API const char* hpvm_last_error(void);
 /* ABI version (major * 100 + minor). */

@@ -115,6 +115,8 @@ def _load() -> ctypes.CDLL:
         "hpvm_workspace_size": (I, [P, P, P, SZ, ctypes.POINTER(ctypes.c_size_t)]),
         "hpvm_set_workspace": (I, [P, P, SZ]),
         "hpvm_plan_sgemm": (I, [I, I64, I64, I64] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+        "hpvm_set_kernel_timing": (I, [P, I]),
+        "hpvm_kernel_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "hpvm_last_error": (ctypes.c_char_p, []),
         "hpvm_version": (I, []),
     }
@@ -239,6 +241,17 @@ def hpvm_plan_sgemm(tier: int, M: int, N: int, K: int) -> tuple[int, int, int, i
     v = [ctypes.c_int32() for _ in range(4)]
     _check(LIB.hpvm_plan_sgemm(int(tier), int(M), int(N), int(K), *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def hpvm_set_kernel_timing(ctx: int, enable: bool) -> None:
+    _check(LIB.hpvm_set_kernel_timing(ctx, int(bool(enable))))
+
+
+def hpvm_kernel_timing(ctx: int) -> tuple[float, int]:
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(LIB.hpvm_kernel_timing(ctx, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def hpvm_last_error() -> str:

@@ -226,7 +226,8 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 }  // namespace
 
 cudaError_t launch_fp32_dfg(const SgemmDesc& d, int block, int grid_x, int grid_y,
-                            size_t tile_bytes, cudaStream_t s, KernelReport* rep) {
+                            size_t tile_bytes, cudaStream_t s, KernelReport* rep,
+                            const LaunchHooks* hooks) {
   dim3 grid(grid_x, grid_y), thr(block, block);
   size_t smem = 2 * tile_bytes;  // the Allocation node's B tile and A tile
   if (smem > 48 * 1024) {
@@ -239,6 +240,7 @@ cudaError_t launch_fp32_dfg(const SgemmDesc& d, int block, int grid_x, int grid_
     HPVM_SET_SMEM(true, false) HPVM_SET_SMEM(true, true)
 #undef HPVM_SET_SMEM
   }
+  hook_begin(hooks, s);
   if (d.transA) {
     if (d.transB) sgemm_leaf_dfg<true, true><<<grid, thr, smem, s>>>(d, block);
     else sgemm_leaf_dfg<true, false><<<grid, thr, smem, s>>>(d, block);
@@ -246,6 +248,7 @@ cudaError_t launch_fp32_dfg(const SgemmDesc& d, int block, int grid_x, int grid_
     if (d.transB) sgemm_leaf_dfg<false, true><<<grid, thr, smem, s>>>(d, block);
     else sgemm_leaf_dfg<false, false><<<grid, thr, smem, s>>>(d, block);
   }
+  hook_end(hooks, s);
   if (rep) {
     rep->kernels = 1;
     rep->grid_x = grid_x; rep->grid_y = grid_y; rep->grid_z = 1;
@@ -260,12 +263,14 @@ cudaError_t launch_fp32_dfg(const SgemmDesc& d, int block, int grid_x, int grid_
 
 void fp32_tiled_tile(int* tm, int* tn) { *tm = TBM; *tn = TBN; }
 
-cudaError_t launch_fp32_tiled(const SgemmDesc& d, cudaStream_t s, KernelReport* rep) {
+cudaError_t launch_fp32_tiled(const SgemmDesc& d, cudaStream_t s, KernelReport* rep,
+                              const LaunchHooks* hooks) {
   dim3 grid((unsigned)((d.M + TBM - 1) / TBM), (unsigned)((d.N + TBN - 1) / TBN));
   // float4 access needs 16-byte aligned columns: base aligned and ld % 4 == 0
   int vec_a = aligned16(d.A) && d.lda % 4 == 0;
   int vec_b = aligned16(d.B) && d.ldb % 4 == 0;
   int vec_c = aligned16(d.C) && d.ldc % 4 == 0;
+  hook_begin(hooks, s);
   if (d.transA) {
     if (d.transB) sgemm_fp32_tiled<true, true><<<grid, TTHREADS, 0, s>>>(d, vec_a, vec_b, vec_c);
     else sgemm_fp32_tiled<true, false><<<grid, TTHREADS, 0, s>>>(d, vec_a, vec_b, vec_c);
@@ -273,6 +278,7 @@ cudaError_t launch_fp32_tiled(const SgemmDesc& d, cudaStream_t s, KernelReport* 
     if (d.transB) sgemm_fp32_tiled<false, true><<<grid, TTHREADS, 0, s>>>(d, vec_a, vec_b, vec_c);
     else sgemm_fp32_tiled<false, false><<<grid, TTHREADS, 0, s>>>(d, vec_a, vec_b, vec_c);
   }
+  hook_end(hooks, s);
   if (rep) {
     rep->kernels = 1;
     rep->grid_x = (int)grid.x; rep->grid_y = (int)grid.y; rep->grid_z = 1;

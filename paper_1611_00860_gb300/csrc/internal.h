@@ -41,15 +41,28 @@ struct DeviceStatus {
   int* host = nullptr;  // host address of the same word
 };
 
+// Optional CUDA events recorded on the launch stream right before and right
+// after the main (leaf) kernel of a launch, for timing that kernel alone.
+struct LaunchHooks {
+  cudaEvent_t main_begin = nullptr;
+  cudaEvent_t main_end = nullptr;
+};
+inline void hook_begin(const LaunchHooks* h, cudaStream_t s) {
+  if (h && h->main_begin) cudaEventRecord(h->main_begin, s);
+}
+inline void hook_end(const LaunchHooks* h, cudaStream_t s) {
+  if (h && h->main_end) cudaEventRecord(h->main_end, s);
+}
+
 // ---- FP32 CUDA-core leaves (fp32_leaf.cu) ---------------------------------
 // Literal Section 4.4 mapping: CTA (bx, by) = internal instance, thread
 // (tx, ty) = leaf instance, tiles of the Allocation node in shared memory.
 cudaError_t launch_fp32_dfg(const SgemmDesc& d, int block, int grid_x,
                             int grid_y, size_t tile_bytes, cudaStream_t s,
-                            KernelReport* rep);
+                            KernelReport* rep, const LaunchHooks* hooks);
 // Register-tiled FP32 kernel.
 cudaError_t launch_fp32_tiled(const SgemmDesc& d, cudaStream_t s,
-                              KernelReport* rep);
+                              KernelReport* rep, const LaunchHooks* hooks);
 void fp32_tiled_tile(int* tm, int* tn);
 
 // ---- tensor-core leaves (tc_leaf.cu) --------------------------------------
@@ -59,7 +72,8 @@ size_t tc_workspace_bytes(const SgemmDesc& d, int tier);
 // cudaErrorInvalidValue and fills *err.
 cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes,
                       const DeviceStatus& st, cudaStream_t s,
-                      KernelReport* rep, std::string* err);
+                      KernelReport* rep, std::string* err,
+                      const LaunchHooks* hooks);
 void tc_tile(int tier, int* tm, int* tn);
 
 }  // namespace hpvm

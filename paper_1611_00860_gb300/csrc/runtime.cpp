@@ -136,6 +136,8 @@ struct hpvm_ctx {
   size_t ws_bytes = 0;
   bool ws_owned = false;
   hpvm::DeviceStatus status;
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed;  // main-kernel events
 };
 
 // ---------------------------------------------------------------------------
@@ -606,6 +608,10 @@ int hpvm_cleanup(hpvm_ctx* ctx) {
       if (t.dev) cudaFree(t.dev);
     if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
     if (ctx->status.host) cudaFreeHost(ctx->status.host);
+    for (auto& pr : ctx->timed) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
   }
   delete ctx;
   return ok();
@@ -827,16 +833,22 @@ int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args, size_t args_si
     size_t need = workspace_need(L, tier);
     if ((rc = ensure_workspace(ctx, need, &ws)) != HPVM_OK) return rc;
     std::string err;
+    hpvm::LaunchHooks hooks;
+    if (ctx->timing) {
+      if (cudaEventCreate(&hooks.main_begin) != cudaSuccess || cudaEventCreate(&hooks.main_end) != cudaSuccess)
+        return fail(HPVM_ERR_CUDA, "cannot create timing events");
+      ctx->timed.emplace_back(hooks.main_begin, hooks.main_end);
+    }
     switch (tier) {
       case HPVM_TIER_FP32_DFG:
         e = hpvm::launch_fp32_dfg(d, (int)L.block_x, (int)L.grid_x, (int)L.grid_y,
-                                  (size_t)(L.block_x * L.block_y * 4), s, &rep);
+                                  (size_t)(L.block_x * L.block_y * 4), s, &rep, &hooks);
         break;
       case HPVM_TIER_FP32:
-        e = hpvm::launch_fp32_tiled(d, s, &rep);
+        e = hpvm::launch_fp32_tiled(d, s, &rep, &hooks);
         break;
       default:
-        e = hpvm::launch_tc(d, tier, ws, ctx->ws_bytes, ctx->status, s, &rep, &err);
+        e = hpvm::launch_tc(d, tier, ws, ctx->ws_bytes, ctx->status, s, &rep, &err, &hooks);
         if (e == cudaErrorInvalidValue && !err.empty()) return fail(HPVM_ERR_SHAPE, "%s", err.c_str());
         break;
     }
@@ -917,6 +929,34 @@ int hpvm_graph_info(hpvm_graph* g, hpvm_launch_info* out) {
   if (!g->ctx->graphs.count(g)) return fail(HPVM_ERR_INVALID_ARG, "unknown or finished graph handle");
   *out = g->info;
   return ok();
+}
+
+int hpvm_set_kernel_timing(hpvm_ctx* ctx, int enable) {
+  if (!ctx) return fail(HPVM_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->device < 0) return fail(HPVM_ERR_NO_DEVICE, "host-only context");
+  ctx->timing = enable != 0;
+  return ok();
+}
+
+int hpvm_kernel_timing(hpvm_ctx* ctx, double* total_ms, int64_t* launches) {
+  if (!ctx || !total_ms || !launches) return fail(HPVM_ERR_INVALID_ARG, "NULL argument");
+  double sum = 0.0;
+  int64_t n = 0;
+  int rc = HPVM_OK;
+  for (auto& pr : ctx->timed) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(pr.second);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+    if (e != cudaSuccess && rc == HPVM_OK) rc = cuda_fail(e, "reading kernel timing events");
+    sum += ms;
+    ++n;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  ctx->timed.clear();
+  *total_ms = sum;
+  *launches = n;
+  return rc == HPVM_OK ? ok() : rc;
 }
 
 int hpvm_track_mem(hpvm_ctx* ctx, void* p, int64_t bytes) {

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -42,8 +43,14 @@ constexpr int BM = 128;             // tile rows (M) = tensor-memory lanes
 constexpr int BN = 256;             // tile columns (N) = accumulator columns
 constexpr int BK = 32;              // K slab in BF16 elements = 64 bytes
 constexpr int MMA_K = 16;           // K per tcgen05.mma kind::f16
-constexpr int THREADS = 192;        // 6 warps
-constexpr uint32_t TMEM_COLS = 256; // FP32 accumulator BM x BN
+constexpr int EPI_WARPS = 8;        // two per tensor-memory lane quarter
+constexpr int THREADS = 64 + EPI_WARPS * 32;  // producer, MMA, epilogue warps
+constexpr uint32_t TMEM_COLS = 2 * BN;        // two FP32 BM x BN chunk buffers
+constexpr int KC_SLABS = 4;         // K chunk = 4 slabs = 128 elements; its
+                                    // sum is added to FP32 registers with
+                                    // round-to-nearest (the tensor-core
+                                    // accumulation truncates)
+constexpr int GROUP_N = 8;          // column tiles per rasterisation group
 constexpr uint32_t A_SLAB = BM * BK * 2;  // bytes of one A plane slab
 constexpr uint32_t B_SLAB = BN * BK * 2;  // bytes of one B plane slab
 constexpr uint32_t SMEM_BUDGET = 200 * 1024;
@@ -59,6 +66,7 @@ struct Cfg {
   static constexpr int STAGES = (int)((SMEM_BUDGET - 2048) / STAGE_BYTES) > 8
                                     ? 8 : (int)((SMEM_BUDGET - 2048) / STAGE_BYTES);
   static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
+  static_assert(2 * STAGES * 8 + 4 * 8 + 8 <= 512, "barrier area");
 };
 
 struct TcParams {
@@ -233,6 +241,22 @@ __global__ void __launch_bounds__(256) split_kmajor(const float* __restrict__ X,
 }
 
 // ---- the leaf kernel -------------------------------------------------------------
+// Persistent: CTA b handles tiles b, b + gridDim.x, ... in a grouped order
+// (GROUP_N column tiles at a time, M fastest) so CTAs that run together share
+// operand panels in L2.
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int* m0, int* n0) {
+  const int group = GROUP_N * tiles_m;
+  const int g = t / group, r = t % group;
+  const int first_n = g * GROUP_N;
+  const int gn = min(GROUP_N, tiles_n - first_n);
+  *m0 = (r / gn) * BM;
+  *n0 = (first_n + r % gn) * BN;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 template <int NPROD>
 __global__ void __launch_bounds__(THREADS, 1)
     sgemm_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
@@ -244,13 +268,16 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * C_::STAGE_BYTES);
   uint64_t* empty = full + S;
-  uint64_t* accb = empty + S;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
+  uint64_t* tfull = empty + S;   // [2] MMA -> epilogue: chunk accumulated in buffer b
+  uint64_t* tempty = tfull + 2;  // [2] epilogue -> MMA: buffer b read out
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int num_kb = (p.K + BK - 1) / BK;
+  const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
+  const int tiles_m = (p.M + BM - 1) / BM, tiles_n = (p.N + BN - 1) / BN;
+  const int num_tiles = tiles_m * tiles_n;
 
   // stage s: [A hi][A lo][B hi][B lo] (lo planes only for NPROD == 3)
   auto a_hi = [&](int s) { return smem + s * C_::STAGE_BYTES; };
@@ -263,7 +290,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EPI_WARPS);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -280,80 +310,126 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   // bookkeeping for the drain after an abort
-  int issued = 0;       // producer: slabs requested
-  int committed = 0;    // MMA: slabs whose MMAs were committed
+  int issued = 0;     // producer: slabs requested (ring position)
+  int committed = 0;  // MMA: slabs whose MMAs were committed (ring position)
+  int chunks_committed = 0;
 
   if (warp == 0 && lane == 0) {
     // ---- producer: TMA loads of the operand slabs into the ring
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA_hi)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
-    for (int kb = 0; kb < num_kb; ++kb) {
-      const int s = kb % S;
-      const uint32_t ph = (kb / S) & 1;
-      if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, p.status, ST_PRODUCER)) break;
-      mbar_expect_tx(&full[s], C_::STAGE_BYTES);
-      const int k = kb * BK;
-      tma_load_2d(&tmA_hi, &full[s], a_hi(s), k, m0);
-      if (NPROD == 3) tma_load_2d(&tmA_lo, &full[s], a_lo(s), k, m0);
-      tma_load_2d(&tmB_hi, &full[s], b_hi(s), k, n0);
-      if (NPROD == 3) tma_load_2d(&tmB_lo, &full[s], b_lo(s), k, n0);
-      issued = kb + 1;
+    int it = 0;
+    bool go = true;
+    for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
+      int m0, n0;
+      tile_coords(t, tiles_m, tiles_n, &m0, &n0);
+      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (it / S) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, p.status, ST_PRODUCER)) {
+          go = false;
+          break;
+        }
+        mbar_expect_tx(&full[s], C_::STAGE_BYTES);
+        const int k = kb * BK;
+        tma_load_2d(&tmA_hi, &full[s], a_hi(s), k, m0);
+        if (NPROD == 3) tma_load_2d(&tmA_lo, &full[s], a_lo(s), k, m0);
+        tma_load_2d(&tmB_hi, &full[s], b_hi(s), k, n0);
+        if (NPROD == 3) tma_load_2d(&tmB_lo, &full[s], b_lo(s), k, n0);
+        issued = it + 1;
+      }
     }
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: three (or one) BF16 products per 16-wide K step
+    // ---- MMA issuer: per K chunk, a fresh accumulation in tensor-memory
+    // buffer (chunk parity); three (or one) BF16 products per 16-wide K step
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
-    for (int kb = 0; kb < num_kb; ++kb) {
-      const int s = kb % S;
-      const uint32_t ph = (kb / S) & 1;
-      if (!mbar_wait(&full[s], ph, abort_flag, p.status, ST_MMA)) break;
-      tc_fence_after();
-      const uint32_t ah = smem_u32(a_hi(s)), al = smem_u32(a_lo(s));
-      const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_lo(s));
-#pragma unroll
-      for (int kk = 0; kk < BK / MMA_K; ++kk) {
-        const uint32_t off = kk * MMA_K * 2;  // bytes along the 64-byte row
-        const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-        if (NPROD == 3) {
-          umma_bf16(tmem, sdesc_k_sw64(al + off), sdesc_k_sw64(bh + off), idesc, first);
-          umma_bf16(tmem, sdesc_k_sw64(ah + off), sdesc_k_sw64(bl + off), idesc, 1u);
-          umma_bf16(tmem, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, 1u);
-        } else {
-          umma_bf16(tmem, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, first);
+    int it = 0, g = 0;
+    bool go = true;
+    for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
+      for (int c = 0; go && c < num_chunks; ++c, ++g) {
+        const int buf = g & 1;
+        const uint32_t use = (uint32_t)(g >> 1);
+        if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag, p.status, ST_MMA)) {
+          go = false;
+          break;
         }
-      }
-      umma_commit(&empty[s]);  // frees the slab once these MMAs have read it
-      committed = kb + 1;
-    }
-    if (committed == num_kb && num_kb > 0) umma_commit(accb);  // accumulator complete
-  } else if (warp >= 2) {
-    // ---- epilogue: tensor memory -> registers -> C (coalesced per column)
-    const int q = warp & 3;  // lane quarter this warp may access
-    const int row = m0 + q * 32 + lane;
-    bool have_acc = num_kb > 0;
-    bool ok = true;
-    if (have_acc) ok = mbar_wait(accb, 0, abort_flag, p.status, ST_EPILOGUE);
-    tc_fence_after();
-    __syncwarp();
-    if (ok) {
-      for (int c = 0; c < BN / 32; ++c) {
-        const int col0 = n0 + c * 32;
-        if (col0 >= p.N) break;
-        uint32_t r[32];
-        if (have_acc) {
-          tmem_ld_x32(tmem + (static_cast<uint32_t>(q * 32) << 16) + c * 32, r);
-        } else {
+        tc_fence_after();
+        const uint32_t dst = tmem + buf * BN;
+        const int kb_end = min(num_kb, (c + 1) * KC_SLABS);
+        for (int kb = c * KC_SLABS; kb < kb_end; ++kb, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (it / S) & 1;
+          if (!mbar_wait(&full[s], ph, abort_flag, p.status, ST_MMA)) {
+            go = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(a_hi(s)), al = smem_u32(a_lo(s));
+          const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_lo(s));
 #pragma unroll
-          for (int u = 0; u < 32; ++u) r[u] = 0u;
-        }
-        if (row < p.M) {
-          float* cp = p.C + row + (int64_t)col0 * p.ldc;
-#pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            if (col0 + u < p.N) {
-              const float acc = __uint_as_float(r[u]);
-              float* e = cp + (int64_t)u * p.ldc;
-              *e = (p.beta == 0.f) ? p.alpha * acc : fmaf(p.alpha, acc, p.beta * *e);
+          for (int kk = 0; kk < BK / MMA_K; ++kk) {
+            const uint32_t off = kk * MMA_K * 2;  // bytes along the 64-byte row
+            const uint32_t acc = (kb == c * KC_SLABS && kk == 0) ? 0u : 1u;
+            if (NPROD == 3) {
+              umma_bf16(dst, sdesc_k_sw64(al + off), sdesc_k_sw64(bh + off), idesc, acc);
+              umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bl + off), idesc, 1u);
+              umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, 1u);
+            } else {
+              umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, acc);
             }
+          }
+          umma_commit(&empty[s]);  // frees the slab once these MMAs have read it
+          committed = it + 1;
+        }
+        if (!go) break;
+        umma_commit(&tfull[buf]);  // chunk complete in buffer buf
+        chunks_committed = g + 1;
+      }
+    }
+  } else if (warp >= 2) {
+    // ---- epilogue: every chunk, tensor memory -> FP32 registers (round to
+    // nearest); at the end of a tile, registers -> C, coalesced per column
+    const int q = warp & 3;          // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;   // which half of the BN columns
+    int g = 0;
+    bool go = true;
+    for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
+      int m0, n0;
+      tile_coords(t, tiles_m, tiles_n, &m0, &n0);
+      float acc[BN / 2];
+#pragma unroll
+      for (int u = 0; u < BN / 2; ++u) acc[u] = 0.f;
+      for (int c = 0; c < num_chunks; ++c, ++g) {
+        const int buf = g & 1;
+        const uint32_t use = (uint32_t)(g >> 1);
+        if (!mbar_wait(&tfull[buf], use & 1, abort_flag, p.status, ST_EPILOGUE)) {
+          go = false;
+          break;
+        }
+        tc_fence_after();
+        __syncwarp();
+        const uint32_t src = tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * BN + h * (BN / 2);
+#pragma unroll
+        for (int i = 0; i < BN / 64; ++i) {
+          uint32_t r[32];
+          tmem_ld_x32(src + i * 32, r);
+#pragma unroll
+          for (int u = 0; u < 32; ++u) acc[i * 32 + u] += __uint_as_float(r[u]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+      }
+      if (!go) break;
+      const int row = m0 + q * 32 + lane;
+      const int col0 = n0 + h * (BN / 2);
+      if (row < p.M) {
+        float* cp = p.C + row + (int64_t)col0 * p.ldc;
+#pragma unroll
+        for (int u = 0; u < BN / 2; ++u) {
+          if (col0 + u < p.N) {
+            float* e = cp + (int64_t)u * p.ldc;
+            *e = (p.beta == 0.f) ? p.alpha * acc[u] : fmaf(p.alpha, acc[u], p.beta * *e);
           }
         }
       }
@@ -363,12 +439,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_before();
   __syncthreads();
   if (*abort_flag) {
-    // Drain what this CTA itself started before returning (bounded waits).
+    // Drain what this CTA itself started before returning (bounded waits):
+    // TMA loads not yet consumed, and the MMAs of the last commit.
     if (warp == 0 && lane == 0) {
-      for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb) {
-        const int s = kb % S;
+      for (int it = (issued > S ? issued - S : 0); it < issued; ++it) {
+        const int s = it % S;
         const uint64_t t0 = globaltimer();
-        while (!mbar_try_wait(&full[s], (kb / S) & 1)) {
+        while (!mbar_try_wait(&full[s], (it / S) & 1)) {
           if (globaltimer() - t0 > WAIT_LIMIT_NS) {
             if (p.status) atomicOr_system(p.status, ST_DRAIN);
             break;
@@ -377,16 +454,17 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
     if (warp == 1 && lane == 0 && committed > 0) {
-      const int kb = committed - 1;
-      const int s = kb % S;
+      const int it = committed - 1;
+      const int s = it % S;
       const uint64_t t0 = globaltimer();
-      while (!mbar_try_wait(&empty[s], (kb / S) & 1)) {
+      while (!mbar_try_wait(&empty[s], (it / S) & 1)) {
         if (globaltimer() - t0 > WAIT_LIMIT_NS) {
           if (p.status) atomicOr_system(p.status, ST_DRAIN);
           break;
         }
       }
     }
+    (void)chunks_committed;
     __syncthreads();
   }
   if (warp == 1) {
@@ -434,6 +512,16 @@ bool encode_plane(CUtensorMap* map, const void* base, int rows, int K, int Kp, i
   return true;
 }
 
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 inline int64_t kpad(int64_t K) { return (K + 7) / 8 * 8; }
 
@@ -455,7 +543,7 @@ cudaError_t launch_split(const float* X, int64_t ld, bool mmajor, int rows, int 
 
 template <int NPROD>
 cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStream_t s, KernelReport* rep,
-                   std::string* err) {
+                   std::string* err, const LaunchHooks* hooks) {
   using C_ = Cfg<NPROD>;
   const int M = (int)d.M, N = (int)d.N, K = (int)d.K;
   const int Kp = (int)kpad(K);
@@ -495,8 +583,11 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
     attr_set = true;
   }
   TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, st.dev};
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  dim3 grid((unsigned)std::min(tiles, num_sms()));
+  hook_begin(hooks, s);
   sgemm_tc<NPROD><<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm);
+  hook_end(hooks, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   kernels += 1;
@@ -526,7 +617,7 @@ size_t tc_workspace_bytes(const SgemmDesc& d, int tier) {
 }
 
 cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, const DeviceStatus& st,
-                      cudaStream_t s, KernelReport* rep, std::string* err) {
+                      cudaStream_t s, KernelReport* rep, std::string* err, const LaunchHooks* hooks) {
   if (d.M > INT32_MAX / 2 || d.N > INT32_MAX / 2 || d.K > INT32_MAX / 2) {
     *err = "M, N and K must each fit in 30 bits for the tensor-core tiers";
     return cudaErrorInvalidValue;
@@ -535,8 +626,8 @@ cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, c
     *err = "workspace too small or not 256-byte aligned";
     return cudaErrorInvalidValue;
   }
-  if (tier == 2) return run_tc<3>(d, ws, st, s, rep, err);
-  return run_tc<1>(d, ws, st, s, rep, err);
+  if (tier == 2) return run_tc<3>(d, ws, st, s, rep, err, hooks);
+  return run_tc<1>(d, ws, st, s, rep, err, hooks);
 }
 
 }  // namespace hpvm

@@ -16,11 +16,9 @@ if ROOT not in sys.path:
 
 # Build the CUDA library and the oracle's C checker before any test module
 # imports them (both builds are no-ops when up to date).
-from paper_1611_00860_gb300.build import build as _build_lib  # noqa: E402
-from oracle.build import build as _build_oracle  # noqa: E402
+import __graft_entry__  # noqa: E402
 
-_build_lib()
-_build_oracle()
+__graft_entry__.build()
 
 
 def pytest_configure(config):
