@@ -38,9 +38,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sgemm-DFG TFLOP/s and % of roofline at ≤5e-6 rel. err, split-BF16 vs plain FP32"
-WORKLOAD = ("sgemm DFG, M=N=K=8192, op(A)=A, op(B)=B^T column-major, A,B,C ~ N(0,1) seed 1, "
+WORKLOAD = ("sgemm DFG, M=N=K={n}, op(A)=A, op(B)=B^T column-major, A,B,C ~ N(0,1) seed 1, "
             "alpha=beta=1; leaf = split-BF16x3 tcgen05 (3 products, FP32 accumulate)")
-WORKLOAD_REF = ("sgemm DFG, M=N=K=8192, op(A)=A, op(B)=B^T column-major, A,B,C ~ N(0,1) seed 1, "
+WORKLOAD_REF = ("sgemm DFG, M=N=K={n}, op(A)=A, op(B)=B^T column-major, A,B,C ~ N(0,1) seed 1, "
                 "alpha=beta=1; FP64 oracle on the host cores")
 N_SIZE = 8192
 TILE_BLOCK = 256
@@ -168,18 +168,24 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def cpu_oracle_leg(p, got_blocks_fn, seconds: float):
+def cpu_oracle_leg(p, seconds: float):
     """Time the oracle (as it stands) on sampled 256 x 256 blocks of the
-    workload for about ``seconds``; also return the blocks' FP64 values."""
+    workload for about ``seconds``: first the 16 seeded positions plus the
+    first and last block (whose FP64 values are returned for the error
+    check), then further seeded positions until the time is used."""
+    import workloads as W
     from oracle import sgemm as O
-    blocks = __import__("workloads").sample_blocks(p.M, p.N, bs=TILE_BLOCK, count=16)
+    check = W.sample_blocks(p.M, p.N, bs=TILE_BLOCK, count=16)
+    extra = [b for b in W.sample_blocks(p.M, p.N, bs=TILE_BLOCK, count=4096, seed=12) if b not in check]
     refs, t0, done = [], time.perf_counter(), 0
     flops = 0
-    for (i0, j0) in blocks:
-        refs.append(((i0, j0), O.sgemm_block_f64(p, i0, j0, TILE_BLOCK, TILE_BLOCK)))
+    for idx, (i0, j0) in enumerate(check + extra):
+        blk = O.sgemm_block_f64(p, i0, j0, TILE_BLOCK, TILE_BLOCK)
+        if idx < len(check):
+            refs.append(((i0, j0), blk))
         done += 1
         flops += 2 * min(TILE_BLOCK, p.M - i0) * min(TILE_BLOCK, p.N - j0) * p.K
-        if time.perf_counter() - t0 > seconds and done >= 3:
+        if idx + 1 >= len(check) and time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": O.num_threads(),
@@ -222,7 +228,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD_REF, "M": p.M, "N": p.N, "K": p.K},
+        "config": {"workload": WORKLOAD_REF.format(n=p.M), "M": p.M, "N": p.N, "K": p.K},
         "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": O.num_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -362,7 +368,7 @@ def main():
     # 5) CPU baseline (the oracle, timed) and the error of the runs of step 1
     cpu, err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, refs = cpu_oracle_leg(p, None, args.cpu_seconds)
+        cpu, refs = cpu_oracle_leg(p, args.cpu_seconds)
         err = {"bf16x3": block_error(C_bf, p, refs), "fp32": block_error(C_fp, p, refs),
                "blocks": len(refs), "metric": "normwise ||C-C_ref||_F/||C_ref||_F over sampled blocks",
                "tolerance": 5e-6}
@@ -373,7 +379,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "M": p.M, "N": p.N, "K": p.K, "transA": "N",
+            "config": {"workload": WORKLOAD.format(n=p.M), "M": p.M, "N": p.N, "K": p.K, "transA": "N",
                        "transB": "T", "tier": "bf16x3", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (768 MiB FP32 operands + 512 MiB split planes); no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
