@@ -247,6 +247,42 @@ HPVM_API int hpvm_plan_sgemm(int tier, int64_t M, int64_t N, int64_t K, int32_t*
 HPVM_API int hpvm_set_kernel_timing(hpvm_ctx* ctx, int enable);
 HPVM_API int hpvm_kernel_timing(hpvm_ctx* ctx, double* total_ms, int64_t* launches);
 
+/* ---- allocation-free BF16x3 leaf ------------------------------------------
+ * No counterpart in the paper. For callers that cannot allocate device
+ * memory at call time -- code inside another framework's memory pool, code on
+ * a latency-critical thread where cudaMalloc/cudaFree may synchronise the
+ * device, code that must not run out of memory mid-job -- this computes
+ * C <- alpha*op(A)*op(B) + beta*C exactly like the BF16X3 tier of
+ * hpvm_launch (same kernels, same result), with the same column-major
+ * argument meaning as hpvm_sgemm_root_args (transA/transB select op()), but
+ * without a context, a graph or a workspace: the split BF16 planes live in a
+ * fixed device array of HPVM_NOALLOC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   - A, B, C: device pointers owned by the caller; C is read (unless
+ *     beta == 0) and written. dev_status: optional device-visible int the
+ *     kernel ORs a nonzero bit into if one of its bounded waits expires (C is
+ *     then not valid); NULL: not reported. cuda_stream: cudaStream_t, NULL =
+ *     legacy default stream. The call is asynchronous on that stream.
+ *   - It allocates nothing: no cudaMalloc, cudaFree or allocating library
+ *     call. The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it, so make
+ *     the first call on each device before any stream capture.
+ *   - Every call uses the same array, and the array keeps the contents the
+ *     last call left. Nothing in it needs to start at zero: every byte a call
+ *     reads, the same call writes first. Calls whose executions overlap on the
+ *     GPU (concurrent streams, or several threads) race on the array and give
+ *     wrong results: serialise them.
+ *   - Errors: HPVM_ERR_SHAPE when the planes, 4*(M+N)*roundup(K,8) bytes with
+ *     256-byte alignment per plane, exceed HPVM_NOALLOC_SCRATCH_BYTES (use
+ *     hpvm_launch with a workspace then), or for a bad leading dimension;
+ *     HPVM_ERR_INVALID_ARG for a NULL matrix; HPVM_ERR_CUDA if the launch
+ *     fails. M == 0 or N == 0 is a no-op. */
+#define HPVM_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+HPVM_API int hpvm_sgemm_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, float alpha,
+                                       const float* A, int64_t lda, const float* B, int64_t ldb,
+                                       float beta, float* C, int64_t ldc, int transA, int transB,
+                                       int* dev_status, void* cuda_stream);
+
 /* Thread-local message of the last failed call ("" if none). */
 HPVM_API const char* hpvm_last_error(void);
 /* ABI version (major * 100 + minor). */

@@ -42,6 +42,7 @@ HPVM_TIER_BF16X3 = 2
 HPVM_TIER_BF16 = 3
 
 HPVM_LAUNCH_NO_EVENT = 1
+HPVM_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 HPVM_ROOTIN_PAPER_BYTES = 88
 HPVM_SGEMM_ROOT_ARGS_BYTES = 112
 
@@ -117,6 +118,8 @@ def _load() -> ctypes.CDLL:
         "hpvm_plan_sgemm": (I, [I, I64, I64, I64] + [ctypes.POINTER(ctypes.c_int32)] * 4),
         "hpvm_set_kernel_timing": (I, [P, I]),
         "hpvm_kernel_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+        "hpvm_sgemm_bf16x3_noalloc": (I, [I64, I64, I64, ctypes.c_float, P, I64, P, I64,
+                                          ctypes.c_float, P, I64, I, I, P, P]),
         "hpvm_last_error": (ctypes.c_char_p, []),
         "hpvm_version": (I, []),
     }
@@ -252,6 +255,17 @@ def hpvm_kernel_timing(ctx: int) -> tuple[float, int]:
     n = ctypes.c_int64()
     _check(LIB.hpvm_kernel_timing(ctx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def hpvm_sgemm_bf16x3_noalloc(M: int, N: int, K: int, alpha: float, A: int, lda: int,
+                              B: int, ldb: int, beta: float, C: int, ldc: int,
+                              transA: bool, transB: bool, dev_status: int | None = None,
+                              cuda_stream: int = 0) -> None:
+    """The allocation-free BF16x3 leaf: device pointers in, C updated on
+    ``cuda_stream`` (asynchronous); see include/hpvm.h."""
+    _check(LIB.hpvm_sgemm_bf16x3_noalloc(int(M), int(N), int(K), float(alpha), A, int(lda), B,
+                                         int(ldb), float(beta), C, int(ldc), int(bool(transA)),
+                                         int(bool(transB)), dev_status, cuda_stream or None))
 
 
 def hpvm_last_error() -> str:

@@ -76,4 +76,8 @@ cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes,
                       const LaunchHooks* hooks);
 void tc_tile(int tier, int* tm, int* tn);
 
+// Sets the calling thread's hpvm_last_error() message (cleared for HPVM_OK)
+// and returns `code` (runtime.cpp).
+int set_last_error(int code, const char* msg);
+
 }  // namespace hpvm

@@ -85,6 +85,11 @@ const char* kind_name(int k) {
 }
 }  // namespace
 
+int hpvm::set_last_error(int code, const char* msg) {
+  if (code == HPVM_OK) return ok();
+  return fail(code, "%s", msg);
+}
+
 // ---------------------------------------------------------------------------
 // handles
 struct hpvm_edge {

@@ -34,6 +34,7 @@
 #include <mutex>
 #include <string>
 
+#include "../../include/hpvm.h"
 #include "internal.h"
 
 namespace hpvm {
@@ -631,3 +632,99 @@ cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, c
 }
 
 }  // namespace hpvm
+
+// ===========================================================================
+// Allocation-free BF16x3 leaf (hpvm_sgemm_bf16x3_noalloc).
+//
+// Some callers cannot allocate device memory when they call the leaf: code
+// that runs inside another framework's memory pool (which has reserved the
+// device memory and forbids its plugins to call cudaMalloc), code on a
+// latency-critical thread (cudaMalloc and cudaFree may synchronise the
+// device), or code that must not fail for lack of memory halfway through a
+// job. For them this entry point keeps the split BF16 planes in a fixed
+// file-scope device array instead of a workspace. The array is allocated
+// when the library's kernels are loaded onto a GPU and stays allocated on
+// every GPU that loads the library until the process exits.
+namespace hpvm {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = HPVM_NOALLOC_SCRATCH_BYTES;
+
+// The scratch planes. Host code must not use this name as a device address;
+// it gets the address through cudaGetSymbolAddress (see noalloc_scratch).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (with that device current) and cached. Returns nullptr and a
+// message on failure.
+void* noalloc_scratch(std::string* err) {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static void* addr[kMaxDevices] = {nullptr};
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    *err = "no usable current CUDA device";
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      *err = std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e);
+      return nullptr;
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+}  // namespace
+}  // namespace hpvm
+
+extern "C" int hpvm_sgemm_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                                         int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                                         int64_t ldc, int transA, int transB, int* dev_status,
+                                         void* cuda_stream) {
+  using namespace hpvm;
+  if (M < 0 || N < 0 || K < 0) return set_last_error(HPVM_ERR_SHAPE, "negative M, N or K");
+  const int64_t ar = transA ? K : M, br = transB ? N : K;
+  if (lda < std::max<int64_t>(1, ar) || ldb < std::max<int64_t>(1, br) || ldc < std::max<int64_t>(1, M))
+    return set_last_error(HPVM_ERR_SHAPE, "a leading dimension is smaller than the rows of its matrix");
+  if (M == 0 || N == 0) return set_last_error(HPVM_OK, "");
+  if (!C || (K > 0 && (!A || !B))) return set_last_error(HPVM_ERR_INVALID_ARG, "A, B or C is NULL");
+  SgemmDesc d;
+  d.M = M;
+  d.N = N;
+  d.K = K;
+  d.A = A;
+  d.lda = lda;
+  d.B = B;
+  d.ldb = ldb;
+  d.C = C;
+  d.ldc = ldc;
+  d.alpha = alpha;
+  d.beta = beta;
+  d.transA = transA != 0;
+  d.transB = transB != 0;
+  const size_t need = tc_workspace_bytes(d, 2);
+  if (need > kNoAllocScratchBytes || M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "the split planes need %zu bytes, more than the %zu-byte scratch array of the "
+             "allocation-free entry point: use hpvm_launch with a workspace",
+             need, kNoAllocScratchBytes);
+    return set_last_error(HPVM_ERR_SHAPE, buf);
+  }
+  std::string err;
+  void* ws = noalloc_scratch(&err);
+  if (!ws) return set_last_error(HPVM_ERR_CUDA, err.c_str());
+  DeviceStatus st;
+  st.dev = dev_status;
+  cudaError_t e = launch_tc(d, 2, ws, kNoAllocScratchBytes, st, static_cast<cudaStream_t>(cuda_stream),
+                            nullptr, &err, nullptr);
+  if (e == cudaErrorInvalidValue && !err.empty()) return set_last_error(HPVM_ERR_SHAPE, err.c_str());
+  if (e != cudaSuccess) return set_last_error(HPVM_ERR_CUDA, cudaGetErrorString(e));
+  return set_last_error(HPVM_OK, "");
+}
