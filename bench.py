@@ -94,7 +94,7 @@ def traffic_from_profiles(src_hash: str):
         return None
     text = open(path).read()
     m_hash = re.search(r"kernel source sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
-    m_bytes = re.search(r"dram bytes per launch \(read \+ write\):\s*([0-9.eE+]+)", text)
+    m_bytes = re.search(r"dram bytes per launch \(read \+ write\)\W*([0-9.eE+]+)", text)
     if not m_hash or not m_bytes or m_hash.group(1) != src_hash:
         return None
     return float(m_bytes.group(1))
