@@ -71,11 +71,16 @@ extern "C" {
  * BF16X3:   tcgen05 tensor cores, each FP32 operand split into BF16
  *           hi + lo, three products hi*hi + hi*lo + lo*hi, FP32 accumulate.
  * BF16:     tcgen05 tensor cores, operands rounded to BF16, FP32 accumulate.
+ * FP8:      tcgen05 kind::f8f6f4, op(A) and op(B) quantised to E4M3 with one
+ *           FP32 scale per 128 x 128 block (scale = amax/448, round to
+ *           nearest even, saturating); each 128-wide K block's product is
+ *           scaled by its two block scales and summed in FP32 registers.
  */
 #define HPVM_TIER_FP32_DFG 0
 #define HPVM_TIER_FP32 1
 #define HPVM_TIER_BF16X3 2
 #define HPVM_TIER_BF16 3
+#define HPVM_TIER_FP8 4
 
 /* A replication extent that is not a constant but the value of input port p
  * of the parent node at run time (the example passes its own block_x,
@@ -246,6 +251,26 @@ HPVM_API int hpvm_plan_sgemm(int tier, int64_t M, int64_t N, int64_t K, int32_t*
  * the number of timed launches, and forgets them. */
 HPVM_API int hpvm_set_kernel_timing(hpvm_ctx* ctx, int enable);
 HPVM_API int hpvm_kernel_timing(hpvm_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* ---- operand preparation (the tensor-core tiers' pre-pass) ---------------
+ * The first step of the BF16x3 / BF16 / FP8 leaves, callable on its own.
+ * Y is a rows x K operand read from the column-major buffer X: element
+ * (r, k) is X[r + k*ld] when kcontig == 0 (op(A) = A with rows = M, or
+ * op(B) = B^T with rows = N), X[k + r*ld] when kcontig != 0 (op(A) = A^T, or
+ * op(B) = B). Outputs are K-major, device pointers, 16-byte aligned;
+ * asynchronous on cuda_stream.
+ * hpvm_split_bf16: hi[r*Kp + k] = bf16_rn(Y(r,k)) and, when lo != NULL,
+ *   lo[r*Kp + k] = bf16_rn(Y(r,k) - hi) (the difference is exact in FP32),
+ *   with Kp = roundup(K, 8) and zeros for K <= k < Kp; hi, lo hold rows*Kp
+ *   BF16 values.
+ * hpvm_quant_fp8: for each 128 x 128 block (rb, kb) of Y, scales[rb*nkb + kb]
+ *   = amax / 448 (1 for an all-zero block), nkb = ceil(K/128), both
+ *   divisions IEEE FP32; q[r*Kq + k] = e4m3_rn_satfinite(Y(r,k) / scale) with
+ *   Kq = roundup(K, 16) and zero codes for K <= k < Kq. */
+HPVM_API int hpvm_split_bf16(const float* X, int64_t ld, int kcontig, int64_t rows, int64_t K,
+                             void* hi, void* lo, void* cuda_stream);
+HPVM_API int hpvm_quant_fp8(const float* X, int64_t ld, int kcontig, int64_t rows, int64_t K,
+                            void* q, float* scales, void* cuda_stream);
 
 /* ---- allocation-free BF16x3 leaf ------------------------------------------
  * No counterpart in the paper. For callers that cannot allocate device

@@ -11,6 +11,7 @@ from ._lib import (  # noqa: F401
     HPVM_TIER_BF16X3,
     HPVM_TIER_FP32,
     HPVM_TIER_FP32_DFG,
+    HPVM_TIER_FP8,
     HpvmError,
 )
 from .sgemm import SgemmDFG, build_sgemm_graph, make_args  # noqa: F401
@@ -20,4 +21,5 @@ TIERS = {
     "fp32": HPVM_TIER_FP32,
     "bf16x3": HPVM_TIER_BF16X3,
     "bf16": HPVM_TIER_BF16,
+    "fp8": HPVM_TIER_FP8,
 }

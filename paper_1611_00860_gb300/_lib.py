@@ -40,6 +40,7 @@ HPVM_TIER_FP32_DFG = 0
 HPVM_TIER_FP32 = 1
 HPVM_TIER_BF16X3 = 2
 HPVM_TIER_BF16 = 3
+HPVM_TIER_FP8 = 4
 
 HPVM_LAUNCH_NO_EVENT = 1
 HPVM_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
@@ -118,6 +119,8 @@ def _load() -> ctypes.CDLL:
         "hpvm_plan_sgemm": (I, [I, I64, I64, I64] + [ctypes.POINTER(ctypes.c_int32)] * 4),
         "hpvm_set_kernel_timing": (I, [P, I]),
         "hpvm_kernel_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+        "hpvm_split_bf16": (I, [P, I64, I, I64, I64, P, P, P]),
+        "hpvm_quant_fp8": (I, [P, I64, I, I64, I64, P, P, P]),
         "hpvm_sgemm_bf16x3_noalloc": (I, [I64, I64, I64, ctypes.c_float, P, I64, P, I64,
                                           ctypes.c_float, P, I64, I, I, P, P]),
         "hpvm_last_error": (ctypes.c_char_p, []),
@@ -255,6 +258,18 @@ def hpvm_kernel_timing(ctx: int) -> tuple[float, int]:
     n = ctypes.c_int64()
     _check(LIB.hpvm_kernel_timing(ctx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def hpvm_split_bf16(X: int, ld: int, kcontig: bool, rows: int, K: int, hi: int,
+                    lo: int | None, cuda_stream: int = 0) -> None:
+    _check(LIB.hpvm_split_bf16(X, int(ld), int(bool(kcontig)), int(rows), int(K), hi, lo,
+                               cuda_stream or None))
+
+
+def hpvm_quant_fp8(X: int, ld: int, kcontig: bool, rows: int, K: int, q: int, scales: int,
+                   cuda_stream: int = 0) -> None:
+    _check(LIB.hpvm_quant_fp8(X, int(ld), int(bool(kcontig)), int(rows), int(K), q, scales,
+                              cuda_stream or None))
 
 
 def hpvm_sgemm_bf16x3_noalloc(M: int, N: int, K: int, alpha: float, A: int, lda: int,

@@ -556,7 +556,8 @@ int ensure_workspace(hpvm_ctx* ctx, size_t need, void** ws) {
 }
 
 size_t workspace_need(const Lowered& L, int tier) {
-  if (tier == HPVM_TIER_BF16X3 || tier == HPVM_TIER_BF16) return hpvm::tc_workspace_bytes(L.d, tier);
+  if (tier == HPVM_TIER_BF16X3 || tier == HPVM_TIER_BF16 || tier == HPVM_TIER_FP8)
+    return hpvm::tc_workspace_bytes(L.d, tier);
   return 0;
 }
 
@@ -748,7 +749,8 @@ int hpvm_plan_sgemm(int tier, int64_t M, int64_t N, int64_t K, int32_t* block_x,
     case HPVM_TIER_FP32_DFG: tm = tn = 16; break;
     case HPVM_TIER_FP32: hpvm::fp32_tiled_tile(&tm, &tn); break;
     case HPVM_TIER_BF16X3:
-    case HPVM_TIER_BF16: hpvm::tc_tile(tier, &tm, &tn); break;
+    case HPVM_TIER_BF16:
+    case HPVM_TIER_FP8: hpvm::tc_tile(tier, &tm, &tn); break;
     default: return fail(HPVM_ERR_INVALID_ARG, "unknown tier %d", tier);
   }
   *block_x = tm;
@@ -796,7 +798,7 @@ int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args, size_t args_si
   int32_t tier, flags;
   memcpy(&tier, static_cast<const uint8_t*>(args) + 104, 4);
   memcpy(&flags, static_cast<const uint8_t*>(args) + 108, 4);
-  if (tier < HPVM_TIER_FP32_DFG || tier > HPVM_TIER_BF16) return fail(HPVM_ERR_INVALID_ARG, "unknown tier %d", tier);
+  if (tier < HPVM_TIER_FP32_DFG || tier > HPVM_TIER_FP8) return fail(HPVM_ERR_INVALID_ARG, "unknown tier %d", tier);
   if (tier == HPVM_TIER_FP32_DFG) {
     if (L.block_x != L.block_y)
       return fail(HPVM_ERR_UNSUPPORTED, "the FP32_DFG lowering needs a square leaf grid (got %lld x %lld)",

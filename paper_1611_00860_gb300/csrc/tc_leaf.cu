@@ -24,6 +24,7 @@
 //       copies and MMAs (bounded again), frees tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -42,32 +43,40 @@ namespace {
 
 constexpr int BM = 128;             // tile rows (M) = tensor-memory lanes
 constexpr int BN = 256;             // tile columns (N) = accumulator columns
-constexpr int BK = 32;              // K slab in BF16 elements = 64 bytes
-constexpr int MMA_K = 16;           // K per tcgen05.mma kind::f16
+constexpr int SLAB_ROW_BYTES = 64;  // one K slab row: 64 bytes (64-byte swizzle)
 constexpr int EPI_WARPS = 8;        // two per tensor-memory lane quarter
 constexpr int THREADS = 64 + EPI_WARPS * 32;  // producer, MMA, epilogue warps
 constexpr uint32_t TMEM_COLS = 2 * BN;        // two FP32 BM x BN chunk buffers
-constexpr int KC_SLABS = 4;         // K chunk = 4 slabs = 128 elements; its
-                                    // sum is added to FP32 registers with
-                                    // round-to-nearest (the tensor-core
-                                    // accumulation truncates)
 constexpr int GROUP_N = 8;          // column tiles per rasterisation group
-constexpr uint32_t A_SLAB = BM * BK * 2;  // bytes of one A plane slab
-constexpr uint32_t B_SLAB = BN * BK * 2;  // bytes of one B plane slab
+constexpr uint32_t A_SLAB = BM * SLAB_ROW_BYTES;  // bytes of one A plane slab
+constexpr uint32_t B_SLAB = BN * SLAB_ROW_BYTES;  // bytes of one B plane slab
 constexpr uint32_t SMEM_BUDGET = 200 * 1024;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per bounded wait
+constexpr int FP8_BLOCK = 128;      // FP8 scale block (rows x K) of each operand
 
 // status bits (DeviceStatus word)
 constexpr int ST_PRODUCER = 1, ST_MMA = 2, ST_EPILOGUE = 4, ST_DRAIN = 8;
 
-template <int NPROD>
+// Leaf modes: 3 = BF16x3 split (hi*hi + hi*lo + lo*hi), 1 = BF16, 8 = FP8
+// E4M3 with one FP32 scale per 128 x 128 block of each operand.
+template <int MODE>
 struct Cfg {
-  static constexpr int PLANES = NPROD == 3 ? 2 : 1;
+  static constexpr bool FP8 = MODE == 8;
+  static constexpr int PLANES = MODE == 3 ? 2 : 1;
+  static constexpr int ELEM_BYTES = FP8 ? 1 : 2;
+  static constexpr int BK = SLAB_ROW_BYTES / ELEM_BYTES;  // K elements per slab
+  static constexpr int MMA_K = 32 / ELEM_BYTES;           // K per tcgen05.mma
+  // K chunk accumulated afresh in tensor memory and then added to FP32
+  // registers with round-to-nearest (the tensor-core accumulation
+  // truncates): 128 elements; for FP8 this is exactly one scale block, and
+  // the chunk is multiplied by its two block scales when it is added.
+  static constexpr int KC_SLABS = 128 / BK;
   static constexpr uint32_t STAGE_BYTES = PLANES * (A_SLAB + B_SLAB);
   static constexpr int STAGES = (int)((SMEM_BUDGET - 2048) / STAGE_BYTES) > 8
                                     ? 8 : (int)((SMEM_BUDGET - 2048) / STAGE_BYTES);
   static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
   static_assert(2 * STAGES * 8 + 4 * 8 + 8 <= 512, "barrier area");
+  static_assert(KC_SLABS * BK == 128, "chunk of 128 K elements");
 };
 
 struct TcParams {
@@ -75,6 +84,9 @@ struct TcParams {
   float* C;
   int64_t ldc;
   float alpha, beta;
+  const float* scaleA;  // FP8: [ceil(M/128)][nkb] block scales of op(A)
+  const float* scaleB;  // FP8: [ceil(N/128)][nkb] block scales of op(B)^T
+  int nkb;              // FP8: ceil(K/128)
   int* status;
 };
 
@@ -165,10 +177,35 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// Instruction descriptor of tcgen05.mma kind::f8f6f4 with E4M3 A and B
+// (format 0 in bits 7-9 and 10-12), F32 D, K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int m, int n) {
+  return (1u << 4) | (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
+}
+__device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
                : "memory");
+}
+// (a0, a1) <- (s*v0 + a0, s*v1 + a1), one rounding each (packed FP32 FMA).
+__device__ __forceinline__ void ffma2(float& a0, float& a1, float s, uint32_t v0, uint32_t v1) {
+  asm("{\n\t.reg .b64 acc, val, sc;\n\t"
+      "mov.b64 acc, {%0, %1};\n\t"
+      "mov.b64 val, {%3, %4};\n\t"
+      "mov.b64 sc, {%2, %2};\n\t"
+      "fma.rn.f32x2 acc, sc, val, acc;\n\t"
+      "mov.b64 {%0, %1}, acc;\n\t}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(s), "r"(v0), "r"(v1));
 }
 __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -241,6 +278,83 @@ __global__ void __launch_bounds__(256) split_kmajor(const float* __restrict__ X,
   }
 }
 
+// Y (rows x K; element (r, k) at X[k + r*ld] when KCONTIG, else X[r + k*ld])
+// -> E4M3 codes q[r*Kp + k] and one FP32 scale per 128 x 128 block,
+// scales[rb*nkb + kb] = amax / 448 (1 when the block is all zero), codes
+// e4m3_rn_satfinite(x / scale). One CTA of 512 threads per block: every
+// thread first issues all eight of its (float4 when VEC) loads, then the
+// block is staged in shared memory, reduced to its amax, and quantised.
+constexpr int QTHREADS = 512;
+template <bool KCONTIG, bool VEC>
+__global__ void __launch_bounds__(QTHREADS) quant_fp8(const float* __restrict__ X, int64_t ld, int rows, int K,
+                                                      int Kp, uint8_t* __restrict__ q, float* __restrict__ scales,
+                                                      int nkb) {
+  extern __shared__ float tile[];  // [128][129]
+  __shared__ float red[QTHREADS / 32];
+  __shared__ float s_sh;
+  constexpr int T = FP8_BLOCK + 1;
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * FP8_BLOCK, k0 = (int64_t)blockIdx.y * FP8_BLOCK;
+  // 4096 groups of 4 elements consecutive in memory: g % 32 runs along the
+  // contiguous dimension, g / 32 along the other one
+  float4 v[8];
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int g = tid + it * QTHREADS;
+    const int c = (g % 32) * 4, o = g / 32;
+    const int64_t gr = r0 + (KCONTIG ? o : c), gk = k0 + (KCONTIG ? c : o);
+    const float* src = KCONTIG ? X + gk + gr * ld : X + gr + gk * ld;
+    const bool full4 = KCONTIG ? (gr < rows && gk + 3 < K) : (gk < K && gr + 3 < rows);
+    if (VEC && full4) {
+      v[it] = *reinterpret_cast<const float4*>(src);
+    } else {
+      float t[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = KCONTIG ? (gr < rows && gk + u < K) : (gk < K && gr + u < rows);
+        t[u] = ok ? src[u] : 0.f;
+      }
+      v[it] = make_float4(t[0], t[1], t[2], t[3]);
+    }
+  }
+  float amax = 0.f;
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int g = tid + it * QTHREADS;
+    const int c = (g % 32) * 4, o = g / 32;
+    const float t[4] = {v[it].x, v[it].y, v[it].z, v[it].w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      amax = fmaxf(amax, fabsf(t[u]));
+      if (KCONTIG) tile[o * T + c + u] = t[u];
+      else tile[(c + u) * T + o] = t[u];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((tid & 31) == 0) red[tid >> 5] = amax;
+  __syncthreads();
+  if (tid == 0) {
+    float m = red[0];
+    for (int w = 1; w < QTHREADS / 32; ++w) m = fmaxf(m, red[w]);
+    const float s = m > 0.f ? __fdiv_rn(m, 448.f) : 1.f;
+    scales[(int64_t)blockIdx.x * nkb + blockIdx.y] = s;
+    s_sh = s;
+  }
+  __syncthreads();
+  const float s = s_sh;
+  for (int task = tid; task < FP8_BLOCK * (FP8_BLOCK / 16); task += QTHREADS) {
+    const int r = task / (FP8_BLOCK / 16), kc = (task % (FP8_BLOCK / 16)) * 16;
+    const int64_t gr = r0 + r, gk = k0 + kc;
+    if (gr >= rows || gk >= Kp) continue;
+    __align__(16) uint8_t c[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      c[u] = __nv_cvt_float_to_fp8(__fdiv_rn(tile[r * T + kc + u], s), __NV_SATFINITE, __NV_E4M3);
+    *reinterpret_cast<uint4*>(q + gr * Kp + gk) = *reinterpret_cast<const uint4*>(c);
+  }
+}
+
 // ---- the leaf kernel -------------------------------------------------------------
 // Persistent: CTA b handles tiles b, b + gridDim.x, ... in a grouped order
 // (GROUP_N column tiles at a time, M fastest) so CTAs that run together share
@@ -258,13 +372,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int NPROD>
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
     sgemm_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
              TcParams p) {
-  using C_ = Cfg<NPROD>;
+  using C_ = Cfg<MODE>;
   constexpr int S = C_::STAGES;
+  constexpr int NPROD = MODE == 3 ? 3 : 1;
+  constexpr int BK = C_::BK, MMA_K = C_::MMA_K, KC_SLABS = C_::KC_SLABS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * C_::STAGE_BYTES);
@@ -343,7 +459,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: per K chunk, a fresh accumulation in tensor-memory
     // buffer (chunk parity); three (or one) BF16 products per 16-wide K step
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    constexpr uint32_t idesc = C_::FP8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
     int it = 0, g = 0;
     bool go = true;
     for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
@@ -369,9 +485,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_lo(s));
 #pragma unroll
           for (int kk = 0; kk < BK / MMA_K; ++kk) {
-            const uint32_t off = kk * MMA_K * 2;  // bytes along the 64-byte row
+            const uint32_t off = kk * MMA_K * C_::ELEM_BYTES;  // bytes along the 64-byte row
             const uint32_t acc = (kb == c * KC_SLABS && kk == 0) ? 0u : 1u;
-            if (NPROD == 3) {
+            if (C_::FP8) {
+              umma_e4m3(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, acc);
+            } else if (NPROD == 3) {
               umma_bf16(dst, sdesc_k_sw64(al + off), sdesc_k_sw64(bh + off), idesc, acc);
               umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bl + off), idesc, 1u);
               umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, 1u);
@@ -400,9 +518,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       float acc[BN / 2];
 #pragma unroll
       for (int u = 0; u < BN / 2; ++u) acc[u] = 0.f;
+      // FP8: this warp's 128 columns are exactly one 128-wide block of
+      // op(B)^T rows and its tile rows one block of op(A) rows
+      const float* sa = nullptr;
+      const float* sb = nullptr;
+      if (C_::FP8) {
+        sa = p.scaleA + (int64_t)(m0 / FP8_BLOCK) * p.nkb;
+        sb = p.scaleB + (int64_t)((n0 + h * (BN / 2)) / FP8_BLOCK) * p.nkb;
+      }
+      const bool cols_live = n0 + h * (BN / 2) < p.N;
       for (int c = 0; c < num_chunks; ++c, ++g) {
         const int buf = g & 1;
         const uint32_t use = (uint32_t)(g >> 1);
+        float scale = 1.f;
+        if (C_::FP8) scale = cols_live ? __ldg(sa + c) * __ldg(sb + c) : 0.f;
         if (!mbar_wait(&tfull[buf], use & 1, abort_flag, p.status, ST_EPILOGUE)) {
           go = false;
           break;
@@ -415,7 +544,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint32_t r[32];
           tmem_ld_x32(src + i * 32, r);
 #pragma unroll
-          for (int u = 0; u < 32; ++u) acc[i * 32 + u] += __uint_as_float(r[u]);
+          for (int u = 0; u < 32; u += 2) ffma2(acc[i * 32 + u], acc[i * 32 + u + 1], scale, r[u], r[u + 1]);
         }
         tc_fence_before();
         __syncwarp();
@@ -425,12 +554,24 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int row = m0 + q * 32 + lane;
       const int col0 = n0 + h * (BN / 2);
       if (row < p.M) {
+        // C in groups of 8 columns: all loads of old C values first, so
+        // their DRAM round trips overlap, then the stores (streaming hints:
+        // C is touched once and should not displace operand panels in L2)
         float* cp = p.C + row + (int64_t)col0 * p.ldc;
+        const int ncols = min(BN / 2, p.N - col0);
 #pragma unroll
-        for (int u = 0; u < BN / 2; ++u) {
-          if (col0 + u < p.N) {
-            float* e = cp + (int64_t)u * p.ldc;
-            *e = (p.beta == 0.f) ? p.alpha * acc[u] : fmaf(p.alpha, acc[u], p.beta * *e);
+        for (int u0 = 0; u0 < BN / 2; u0 += 8) {
+          float old[8];
+          if (p.beta != 0.f) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) old[u] = (u0 + u < ncols) ? __ldcs(cp + (int64_t)(u0 + u) * p.ldc) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (u0 + u < ncols) {
+              const float v = (p.beta == 0.f) ? p.alpha * acc[u0 + u] : fmaf(p.alpha, acc[u0 + u], p.beta * old[u]);
+              __stcs(cp + (int64_t)(u0 + u) * p.ldc, v);
+            }
           }
         }
       }
@@ -489,8 +630,9 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
   return fn;
 }
 
-// K-major BF16 plane: rows x K elements, row stride Kp elements; box BK x box_rows.
-bool encode_plane(CUtensorMap* map, const void* base, int rows, int K, int Kp, int box_rows,
+// K-major operand plane: rows x K elements of `elem_bytes` bytes, row stride
+// Kp elements; TMA box of one 64-byte slab row width x box_rows rows.
+bool encode_plane(CUtensorMap* map, const void* base, int rows, int K, int Kp, int box_rows, int elem_bytes,
                   std::string* err) {
   auto enc = get_encoder();
   if (!enc) {
@@ -498,12 +640,12 @@ bool encode_plane(CUtensorMap* map, const void* base, int rows, int K, int Kp, i
     return false;
   }
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * elem_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)(SLAB_ROW_BYTES / elem_bytes), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapDataType dt = elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     char buf[160];
     snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for a %d x %d plane", (int)r, rows, K);
@@ -524,7 +666,31 @@ int num_sms() {
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-inline int64_t kpad(int64_t K) { return (K + 7) / 8 * 8; }
+
+// Workspace layout of a mode: operand planes (and FP8 block scales).
+struct WsLayout {
+  int64_t Kp = 0;  // row stride of the planes, in elements (16-byte rows)
+  size_t a_hi = 0, a_lo = 0, b_hi = 0, b_lo = 0, sa = 0, sb = 0, total = 0;
+  int nkb = 0;     // FP8: scale blocks along K
+};
+WsLayout ws_layout(const SgemmDesc& d, int mode) {
+  WsLayout L;
+  const int eb = mode == 8 ? 1 : 2;
+  L.Kp = (d.K + 16 / eb - 1) / (16 / eb) * (16 / eb);
+  const size_t ap = align256((size_t)d.M * L.Kp * eb), bp = align256((size_t)d.N * L.Kp * eb);
+  size_t off = 0;
+  L.a_hi = off; off += ap;
+  if (mode == 3) { L.a_lo = off; off += ap; }
+  L.b_hi = off; off += bp;
+  if (mode == 3) { L.b_lo = off; off += bp; }
+  if (mode == 8) {
+    L.nkb = (int)((d.K + FP8_BLOCK - 1) / FP8_BLOCK);
+    L.sa = off; off += align256((size_t)((d.M + FP8_BLOCK - 1) / FP8_BLOCK) * L.nkb * 4);
+    L.sb = off; off += align256((size_t)((d.N + FP8_BLOCK - 1) / FP8_BLOCK) * L.nkb * 4);
+  }
+  L.total = off;
+  return L;
+}
 
 template <int NPROD>
 cudaError_t launch_split(const float* X, int64_t ld, bool mmajor, int rows, int K, int Kp,
@@ -542,35 +708,76 @@ cudaError_t launch_split(const float* X, int64_t ld, bool mmajor, int rows, int 
   return cudaGetLastError();
 }
 
-template <int NPROD>
+cudaError_t launch_quant(const float* X, int64_t ld, bool mmajor, int rows, int K, int Kp, uint8_t* q,
+                         float* scales, int nkb, cudaStream_t s) {
+  if (rows == 0 || K == 0) return cudaSuccess;
+  constexpr int smem = FP8_BLOCK * (FP8_BLOCK + 1) * 4;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(quant_fp8<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(quant_fp8<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(quant_fp8<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(quant_fp8<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  // float4 loads need 16-byte aligned groups: base aligned and ld % 4 == 0
+  const bool vec = (reinterpret_cast<uintptr_t>(X) & 15u) == 0 && ld % 4 == 0;
+  dim3 grid((rows + FP8_BLOCK - 1) / FP8_BLOCK, nkb);
+  if (mmajor) {
+    if (vec) quant_fp8<false, true><<<grid, QTHREADS, smem, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
+    else quant_fp8<false, false><<<grid, QTHREADS, smem, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
+  } else {
+    if (vec) quant_fp8<true, true><<<grid, QTHREADS, smem, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
+    else quant_fp8<true, false><<<grid, QTHREADS, smem, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
+  }
+  return cudaGetLastError();
+}
+
+template <int MODE>
 cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStream_t s, KernelReport* rep,
                    std::string* err, const LaunchHooks* hooks) {
-  using C_ = Cfg<NPROD>;
+  using C_ = Cfg<MODE>;
+  constexpr int NPROD = MODE == 3 ? 3 : 1;
   const int M = (int)d.M, N = (int)d.N, K = (int)d.K;
-  const int Kp = (int)kpad(K);
+  const WsLayout L = ws_layout(d, MODE);
+  const int Kp = (int)L.Kp;
   uint8_t* w = static_cast<uint8_t*>(ws);
-  const size_t a_plane = align256((size_t)M * Kp * 2), b_plane = align256((size_t)N * Kp * 2);
-  __nv_bfloat16* ah = reinterpret_cast<__nv_bfloat16*>(w);
-  __nv_bfloat16* al = reinterpret_cast<__nv_bfloat16*>(w + a_plane);
-  __nv_bfloat16* bh = reinterpret_cast<__nv_bfloat16*>(w + C_::PLANES * a_plane);
-  __nv_bfloat16* bl = reinterpret_cast<__nv_bfloat16*>(w + C_::PLANES * a_plane + b_plane);
+  void* ah = w + L.a_hi;
+  void* al = w + L.a_lo;
+  void* bh = w + L.b_hi;
+  void* bl = w + L.b_lo;
+  float* sa = reinterpret_cast<float*>(w + L.sa);
+  float* sb = reinterpret_cast<float*>(w + L.sb);
   int kernels = 0;
   cudaError_t e;
   if (K > 0) {
     // op(A) rows are contiguous when A is not transposed; op(B)'s N rows when B is
-    e = launch_split<NPROD>(d.A, d.lda, !d.transA, M, K, Kp, ah, al, s);
-    if (e != cudaSuccess) return e;
-    e = launch_split<NPROD>(d.B, d.ldb, d.transB != 0, N, K, Kp, bh, bl, s);
+    if (C_::FP8) {
+      e = launch_quant(d.A, d.lda, !d.transA, M, K, Kp, static_cast<uint8_t*>(ah), sa, L.nkb, s);
+      if (e != cudaSuccess) return e;
+      e = launch_quant(d.B, d.ldb, d.transB != 0, N, K, Kp, static_cast<uint8_t*>(bh), sb, L.nkb, s);
+    } else {
+      e = launch_split<NPROD>(d.A, d.lda, !d.transA, M, K, Kp, static_cast<__nv_bfloat16*>(ah),
+                              static_cast<__nv_bfloat16*>(al), s);
+      if (e != cudaSuccess) return e;
+      e = launch_split<NPROD>(d.B, d.ldb, d.transB != 0, N, K, Kp, static_cast<__nv_bfloat16*>(bh),
+                              static_cast<__nv_bfloat16*>(bl), s);
+    }
     if (e != cudaSuccess) return e;
     kernels += 2;
   }
   alignas(64) CUtensorMap maps[4];
   memset(maps, 0, sizeof maps);
   if (K > 0) {
-    if (!encode_plane(&maps[0], ah, M, K, Kp, BM, err) || !encode_plane(&maps[2], bh, N, K, Kp, BN, err))
+    if (!encode_plane(&maps[0], ah, M, K, Kp, BM, C_::ELEM_BYTES, err) ||
+        !encode_plane(&maps[2], bh, N, K, Kp, BN, C_::ELEM_BYTES, err))
       return cudaErrorInvalidValue;
     if (NPROD == 3) {
-      if (!encode_plane(&maps[1], al, M, K, Kp, BM, err) || !encode_plane(&maps[3], bl, N, K, Kp, BN, err))
+      if (!encode_plane(&maps[1], al, M, K, Kp, BM, 2, err) || !encode_plane(&maps[3], bl, N, K, Kp, BN, 2, err))
         return cudaErrorInvalidValue;
     } else {
       maps[1] = maps[0];
@@ -579,15 +786,15 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
   }
   static bool attr_set = false;
   if (!attr_set) {
-    e = cudaFuncSetAttribute(sgemm_tc<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
+    e = cudaFuncSetAttribute(sgemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, st.dev};
+  TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, st.dev};
   const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   dim3 grid((unsigned)std::min(tiles, num_sms()));
   hook_begin(hooks, s);
-  sgemm_tc<NPROD><<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm);
+  sgemm_tc<MODE><<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm);
   hook_end(hooks, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -596,13 +803,15 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
     rep->kernels = kernels;
     rep->grid_x = (int)grid.x; rep->grid_y = (int)grid.y; rep->grid_z = 1;
     rep->block_threads = THREADS;
-    rep->tile_m = BM; rep->tile_n = BN; rep->tile_k = BK;
+    rep->tile_m = BM; rep->tile_n = BN; rep->tile_k = C_::BK;
     rep->smem_bytes = (int)C_::SMEM_BYTES;
     rep->literal = 0;
-    rep->workspace_bytes = (int64_t)(C_::PLANES * (a_plane + b_plane));
+    rep->workspace_bytes = (int64_t)L.total;
   }
   return cudaSuccess;
 }
+
+int mode_of_tier(int tier) { return tier == 2 ? 3 : tier == 4 ? 8 : 1; }
 
 }  // namespace
 
@@ -611,11 +820,7 @@ void tc_tile(int /*tier*/, int* tm, int* tn) {
   *tn = BN;
 }
 
-size_t tc_workspace_bytes(const SgemmDesc& d, int tier) {
-  const int planes = tier == 2 ? 2 : 1;
-  const int64_t Kp = kpad(d.K);
-  return planes * (align256((size_t)d.M * Kp * 2) + align256((size_t)d.N * Kp * 2));
-}
+size_t tc_workspace_bytes(const SgemmDesc& d, int tier) { return ws_layout(d, mode_of_tier(tier)).total; }
 
 cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, const DeviceStatus& st,
                       cudaStream_t s, KernelReport* rep, std::string* err, const LaunchHooks* hooks) {
@@ -628,6 +833,7 @@ cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, c
     return cudaErrorInvalidValue;
   }
   if (tier == 2) return run_tc<3>(d, ws, st, s, rep, err, hooks);
+  if (tier == 4) return run_tc<8>(d, ws, st, s, rep, err, hooks);
   return run_tc<1>(d, ws, st, s, rep, err, hooks);
 }
 
@@ -725,6 +931,45 @@ extern "C" int hpvm_sgemm_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, float 
   cudaError_t e = launch_tc(d, 2, ws, kNoAllocScratchBytes, st, static_cast<cudaStream_t>(cuda_stream),
                             nullptr, &err, nullptr);
   if (e == cudaErrorInvalidValue && !err.empty()) return set_last_error(HPVM_ERR_SHAPE, err.c_str());
+  if (e != cudaSuccess) return set_last_error(HPVM_ERR_CUDA, cudaGetErrorString(e));
+  return set_last_error(HPVM_OK, "");
+}
+
+// ===========================================================================
+// Operand preparation of the tensor-core tiers, callable on its own.
+extern "C" int hpvm_split_bf16(const float* X, int64_t ld, int kcontig, int64_t rows, int64_t K, void* hi,
+                               void* lo, void* cuda_stream) {
+  using namespace hpvm;
+  if (rows < 0 || K < 0 || rows > INT32_MAX / 2 || K > INT32_MAX / 2)
+    return set_last_error(HPVM_ERR_SHAPE, "rows and K must be in [0, 2^30)");
+  if (rows == 0 || K == 0) return set_last_error(HPVM_OK, "");
+  if (!X || !hi) return set_last_error(HPVM_ERR_INVALID_ARG, "X or hi is NULL");
+  if (ld < (kcontig ? K : rows)) return set_last_error(HPVM_ERR_SHAPE, "ld is smaller than the contiguous extent");
+  if ((reinterpret_cast<uintptr_t>(hi) & 15u) || (reinterpret_cast<uintptr_t>(lo) & 15u))
+    return set_last_error(HPVM_ERR_ALIGN, "hi and lo must be 16-byte aligned");
+  const int Kp = (int)((K + 7) / 8 * 8);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = lo ? launch_split<3>(X, ld, !kcontig, (int)rows, (int)K, Kp, static_cast<__nv_bfloat16*>(hi),
+                                       static_cast<__nv_bfloat16*>(lo), s)
+                     : launch_split<1>(X, ld, !kcontig, (int)rows, (int)K, Kp, static_cast<__nv_bfloat16*>(hi),
+                                       nullptr, s);
+  if (e != cudaSuccess) return set_last_error(HPVM_ERR_CUDA, cudaGetErrorString(e));
+  return set_last_error(HPVM_OK, "");
+}
+
+extern "C" int hpvm_quant_fp8(const float* X, int64_t ld, int kcontig, int64_t rows, int64_t K, void* q,
+                              float* scales, void* cuda_stream) {
+  using namespace hpvm;
+  if (rows < 0 || K < 0 || rows > INT32_MAX / 2 || K > INT32_MAX / 2)
+    return set_last_error(HPVM_ERR_SHAPE, "rows and K must be in [0, 2^30)");
+  if (rows == 0 || K == 0) return set_last_error(HPVM_OK, "");
+  if (!X || !q || !scales) return set_last_error(HPVM_ERR_INVALID_ARG, "X, q or scales is NULL");
+  if (ld < (kcontig ? K : rows)) return set_last_error(HPVM_ERR_SHAPE, "ld is smaller than the contiguous extent");
+  if (reinterpret_cast<uintptr_t>(q) & 15u) return set_last_error(HPVM_ERR_ALIGN, "q must be 16-byte aligned");
+  const int Kp = (int)((K + 15) / 16 * 16);
+  const int nkb = (int)((K + FP8_BLOCK - 1) / FP8_BLOCK);
+  cudaError_t e = launch_quant(X, ld, !kcontig, (int)rows, (int)K, Kp, static_cast<uint8_t*>(q), scales, nkb,
+                               static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return set_last_error(HPVM_ERR_CUDA, cudaGetErrorString(e));
   return set_last_error(HPVM_OK, "");
 }
