@@ -30,8 +30,10 @@ passes it, i.e. the code between two barriers is one phase.
 Readings where the paper is silent (also listed in the design notes):
   * createEdge takes (src, dst, repl, sp, dp, stream), the order of the
     intrinsic list and of the example listing; repl True = all-to-all.
-  * An all-to-all edge is only interpreted from a single-instance source
-    (the example's Allocation node); its value is broadcast.
+  * An all-to-all edge carries one value to every sink instance: from a
+    single-instance source (the example's Allocation node), or from a
+    replicated source whose instances all produce the same value (the
+    result buffer a tile grid writes, in the chain of sgemm stages).
   * Replication extents may be given as values known to the parent function
     at the time it runs (the example passes its own arguments block_x,
     block_y, grid_x, grid_y).
@@ -267,10 +269,13 @@ def _run_child_graph(rt: Runtime, parent: Node, pinst: _Instance, pargs: list) -
             for e in in_edges:
                 src_outs = outs[id(e.src)]
                 if e.all_to_all:
-                    if len(src_outs) != 1:
-                        raise DFGError("all-to-all edge from a replicated source")
-                    (only,) = src_outs.values()
-                    a[e.dp] = only[e.sp]
+                    # every source instance feeds every sink instance; the
+                    # value carried must be the same from all of them (a
+                    # shared buffer, or a single-instance source)
+                    vals = [o[e.sp] for o in src_outs.values()]
+                    if any(v != vals[0] for v in vals[1:]):
+                        raise DFGError("all-to-all edge carries different values from different instances")
+                    a[e.dp] = vals[0]
                 else:
                     a[e.dp] = src_outs[idx][e.sp]
             if any(v is None for v in a):
@@ -397,7 +402,8 @@ def make_sgemm_graph():
             if beta != 0.0:
                 r += beta * mem.load(C, i + j * ldc)
             mem.store(C, i + j * ldc, r)
-        return ()
+        # outputs 0, 1: the result matrix, for a dependent elementwise leaf
+        return (C, bytesC)
 
     @internal(18)
     def SgemmInternal(rt, A, bytesA, lda, B, bytesB, ldb, C, bytesC, ldc, k,
@@ -447,3 +453,138 @@ def run_sgemm_dfg(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, transA, transB,
     launch(rt, root, args)
     out = list(mem.objs[pC[0]])
     return (out, rt) if return_runtime else out
+
+
+# ---------------------------------------------------------------------------
+# Elementwise leaves and the streamed chain.
+#
+# A chain of sgemm stages joined by elementwise tanh leaves, with items fed
+# through streaming edges (Section 3.1 streaming edges; Section 4.5: a
+# streaming graph's nodes stay alive and process every item pushed).
+# Row-major items X (rows x w_in) and weights W (w_in x w_out) are stored so
+# that the column-major sgemm leaf computes Y^T = W^T X^T: M = w_out,
+# N = rows, K = w_in, op(A) = the W buffer read as a column-major
+# w_out x w_in matrix, op(B) = the X buffer read as a column-major w_in x rows
+# matrix. The output buffer, read row-major, is Y = X W.
+# ---------------------------------------------------------------------------
+
+@leaf(5)
+def TanhLeaf(rt, X, bytesX, ldx, M, N):
+    """Instance (tx, ty) of tile (bx, by) applies tanh to element
+    (bx*nx + tx, by*ny + ty) of the column-major M x N matrix X."""
+    me = rt.getNode()
+    par = rt.getParentNode(me)
+    nx, ny = rt.getNumNodeInstances(me, 0), rt.getNumNodeInstances(me, 1)
+    i = rt.getNodeInstanceID(par, 0) * nx + rt.getNodeInstanceID(me, 0)
+    j = rt.getNodeInstanceID(par, 1) * ny + rt.getNodeInstanceID(me, 1)
+    if i < M and j < N:
+        rt.mem.store(X, i + j * ldx, math.tanh(rt.mem.load(X, i + j * ldx)))
+    return (X, bytesX)
+
+
+def make_chain_graph(layers: int):
+    """Node functions of the chain. Stage input ports: 0..19 as the sgemm
+    internal node's record (A = W_l, B = X_l, C = Y_l, ...), except that B of
+    stages after the first arrives over a streaming edge from the previous
+    stage's output 0; ports 20, 21 select tanh (1) or not (0)."""
+    _, _, Allocation, SgemmLeaf = make_sgemm_graph()
+
+    def stage_func(with_tanh: bool):
+        @internal(20)
+        def ChainStage(rt, A, bytesA, lda, B, bytesB, ldb, C, bytesC, ldc, k, alpha, beta,
+                       block_x, block_y, M, N, transA, transB, _r0, _r1):
+            alloc = rt.createNode(Allocation)
+            sg = rt.createNode2D(SgemmLeaf, block_x, block_y)
+            for sp, dp in ((0, 12), (1, 13), (2, 14), (3, 15)):
+                rt.createEdge(alloc, sg, True, sp, dp, False)
+            for p in range(12):
+                rt.bind_input(sg, p, p, False)
+            rt.bind_input(alloc, 12, 0, False)
+            rt.bind_input(alloc, 13, 1, False)
+            for q in range(4):
+                rt.bind_input(sg, 14 + q, 16 + q, False)
+            last = sg
+            if with_tanh:
+                th = rt.createNode2D(TanhLeaf, block_x, block_y)
+                rt.createEdge(sg, th, False, 0, 0, False)  # one-to-one: same grid
+                rt.createEdge(sg, th, False, 1, 1, False)
+                rt.bind_input(th, 8, 2, False)   # ldc
+                rt.bind_input(th, 14, 3, False)  # M
+                rt.bind_input(th, 15, 4, False)  # N
+                last = th
+            rt.bind_output(last, 0, 0, False)
+            rt.bind_output(last, 1, 1, False)
+        return ChainStage
+
+    stages = [stage_func(l + 1 < layers) for l in range(layers)]
+    per = 22  # root ports per stage: the 20 stage inputs + grid_x, grid_y
+
+    @internal(per * layers)
+    def ChainRoot(rt, *a):
+        nodes = []
+        for l in range(layers):
+            base = per * l
+            node = rt.createNode2D(stages[l], a[base + 20], a[base + 21])
+            for p in range(20):
+                if l > 0 and p in (3, 4):
+                    continue  # B and bytesB come from the previous stage
+                rt.bind_input(node, base + p, p, False)
+            if l > 0:
+                rt.createEdge(nodes[-1], node, True, 0, 3, True)  # streaming
+                rt.createEdge(nodes[-1], node, True, 1, 4, True)
+            nodes.append(node)
+        rt.bind_output(nodes[-1], 0, 0, True)
+
+    return ChainRoot
+
+
+class StreamingGraph:
+    """launch(F, args, Stream=true) / push / pop of Table 1: every pushed
+    argument record is one item that flows through the graph; pop returns
+    the outputs of the items in the order they were pushed."""
+
+    def __init__(self, rt: Runtime, root_func):
+        self.rt = rt
+        self.root_func = root_func
+        self.queue: list = []
+
+    def push(self, args: list) -> None:
+        self.queue.append(launch(self.rt, self.root_func, args))
+
+    def pop(self):
+        if not self.queue:
+            raise DFGError("pop on an empty stream")
+        return self.queue.pop(0)
+
+
+def run_chain(items, Ws, block: int = 4):
+    """Push row-major FP64 items (each rows x w) through the chain of
+    weights Ws (w x w each) and pop the outputs, as row-major arrays."""
+    import numpy as np
+
+    layers = len(Ws)
+    root = make_chain_graph(layers)
+    mem = Memory()
+    rt = Runtime(mem)
+    g = StreamingGraph(rt, root)
+    w = Ws[0].shape[0]
+    wptr = [mem.new(np.asarray(Wl, np.float64).reshape(-1).tolist()) for Wl in Ws]
+    outs = []
+    for X in items:
+        rows = X.shape[0]
+        xp = mem.new(np.asarray(X, np.float64).reshape(-1).tolist())
+        bufs = [mem.new([0.0] * (rows * w)) for _ in range(layers)]
+        args = []
+        for l in range(layers):
+            # Y_l^T = W_l^T X_l^T: M = w, N = rows, K = w, A = W_l (lda = w), B = X_l (ldb = w)
+            args += [wptr[l], w * w * 8, w, xp if l == 0 else None, rows * w * 8, w,
+                     bufs[l], rows * w * 8, w, w, 1.0, 0.0, block, block, w, rows, False, False,
+                     0, 0, -(-w // block), -(-rows // block)]
+        g.push(args)
+        outs.append((bufs[-1], rows))
+    results = []
+    for buf, rows in outs:
+        C = g.pop()[0]
+        assert C == buf
+        results.append(np.array(mem.objs[buf[0]]).reshape(rows, w))
+    return results
