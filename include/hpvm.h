@@ -57,7 +57,17 @@ extern "C" {
 /* ---- node kinds: the node function a node runs ------------------------ */
 #define HPVM_NODE_INTERNAL 0   /* graph intrinsics only (Section 3.2) */
 #define HPVM_NODE_ALLOCATION 1 /* allocation leaf (Section 4.4): tile memory */
-#define HPVM_NODE_SGEMM_LEAF 2 /* the SgemmLeaf node function (Section 5.1) */
+#define HPVM_NODE_SGEMM_LEAF 2 /* the SgemmLeaf node function (Section 5.1);
+                                  outputs 0, 1: its result C and bytesC */
+/* Elementwise leaves over a column-major M x N matrix, updated in place;
+ * outputs 0, 1: the matrix and its bytes. Joined to a SgemmLeaf of the same
+ * grid by one-to-one edges (SgemmLeaf out 0 -> in 0, out 1 -> in 1) they are
+ * merged into it (MergeDependentNodes, Section 4.6).
+ * TANH_LEAF inputs: 0 X, 1 bytesX, 2 ldx, 3 M, 4 N; X <- tanh(X).
+ * TANH_GRAD_LEAF inputs: 0 G, 1 bytesG, 2 ldg, 3 M, 4 N, 5 H, 6 bytesH,
+ * 7 ldh; G <- G * (1 - H^2) (the adjoint of tanh at the output H). */
+#define HPVM_NODE_TANH_LEAF 3
+#define HPVM_NODE_TANH_GRAD_LEAF 4
 
 /* ---- edge replication (Section 3.1) ----------------------------------- */
 #define HPVM_ONE_TO_ONE 0 /* instance i -> instance i; grids must match */
@@ -90,6 +100,8 @@ extern "C" {
 /* launch flags (hpvm_sgemm_root_args.flags) */
 #define HPVM_LAUNCH_NO_EVENT 1 /* no completion event: hpvm_wait syncs the
                                   stream (use inside CUDA graph capture) */
+#define HPVM_LAUNCH_NO_FUSION 2 /* run a dependent elementwise leaf as its own
+                                   kernel instead of merging it */
 
 typedef struct hpvm_ctx hpvm_ctx;
 typedef struct hpvm_node hpvm_node;
@@ -102,7 +114,13 @@ typedef struct hpvm_graph hpvm_graph;
  * block_y, grid_x, grid_y; the host code mallocs 88 bytes and packs them).
  * Root input port p is field p of this record for p = 0..15; the trailer
  * adds M (port 16), N (17), transA (18), transB (19), which the example
- * leaves implicit, then two launch options that are not graph inputs.
+ * leaves implicit, two launch options that are not graph inputs (tier,
+ * flags), then aux (port 20), bytesAux (21), ldaux (22) for a leaf that
+ * reads one more matrix (the H of TANH_GRAD_LEAF).
+ * A launch passes an array of these records: port p of the root is field
+ * p % 23 of record p / 23 (multi-stage graphs give each stage a record; at
+ * most 16). The tier and flags of a stage come from the record holding its
+ * C.
  *
  * Meaning: C <- alpha * op(A) * op(B) + beta * C with column-major storage
  * (element (r, c) of a matrix with leading dimension ld at r + c*ld);
@@ -136,11 +154,15 @@ typedef struct hpvm_sgemm_root_args {
   int32_t transB;
   int32_t tier;  /* HPVM_TIER_* */
   int32_t flags; /* HPVM_LAUNCH_* */
+  float* aux;
+  int64_t bytesAux;
+  int32_t ldaux;
+  int32_t reserved;
 } hpvm_sgemm_root_args;
 #pragma pack(pop)
 
 #define HPVM_ROOTIN_PAPER_BYTES 88
-#define HPVM_SGEMM_ROOT_ARGS_BYTES 112
+#define HPVM_SGEMM_ROOT_ARGS_BYTES 136
 
 /* What a launch ran (filled by hpvm_graph_info). */
 typedef struct hpvm_launch_info {
@@ -175,7 +197,8 @@ HPVM_API int hpvm_create_node(hpvm_ctx* ctx, hpvm_node* parent, int kind, int nd
 /* createEdge(Src, Dst, ReplTy, sp, dp, Stream): from output sp of src to
  * input dp of dst; both children of the same internal node; repl is
  * HPVM_ONE_TO_ONE or HPVM_ALL_TO_ALL; one-to-one needs identical grids.
- * stream != 0 (a streaming edge) is rejected with HPVM_ERR_UNSUPPORTED.
+ * stream != 0 makes it a streaming edge (items flow through it repeatedly,
+ * Section 3.1); the lowering supports streaming edges between tile grids.
  * `out` may be NULL. */
 HPVM_API int hpvm_create_edge(hpvm_node* src, hpvm_node* dst, int repl, int sp, int dp,
                      int stream, hpvm_edge** out);
@@ -198,13 +221,19 @@ HPVM_API int hpvm_get_num_node_instances(hpvm_node* node, int dim, int64_t* out)
  * cycle of ordinary edges; every leaf input is fed exactly once. */
 HPVM_API int hpvm_validate(hpvm_node* root);
 
-/* ---- host integration (llvm.hpvm.launch / llvm.hpvm.wait) -------------
+/* ---- host integration (llvm.hpvm.launch / wait / push / pop) ----------
+ * The lowered graph shapes: the root holds one or more 2-D internal nodes
+ * (tile grids, one per stage, ordered by their edges: an all-to-all edge
+ * from a stage's output 0 to the next stage's input carries the result
+ * matrix); each holds one Allocation, one SgemmLeaf and at most one
+ * elementwise leaf.
  * Launch the graph under `root` asynchronously on `cuda_stream` (a
- * cudaStream_t; NULL = the legacy default stream) with the argument record
- * `args` (hpvm_sgemm_root_args, args_size >= 112). stream_graph != 0 (a
- * graph with streaming edges) is rejected with HPVM_ERR_UNSUPPORTED.
- * Errors found before any work is enqueued (graph, shape, alignment) leave
- * the stream untouched. */
+ * cudaStream_t; NULL = the legacy default stream) with the argument records
+ * `args` (hpvm_sgemm_root_args[], args_size >= 136). Errors found before any
+ * work is enqueued (graph, shape, alignment) leave the stream untouched.
+ * stream_graph != 0 launches a streaming graph (Section 4.5): it is
+ * validated against `args` and stays alive; nothing runs until items are
+ * pushed. */
 HPVM_API int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args,
                 size_t args_size, int stream_graph, void* cuda_stream,
                 hpvm_graph** out);
@@ -213,6 +242,19 @@ HPVM_API int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args,
  * return frees it. HPVM_ERR_DEVICE_FAULT: a kernel gave up a bounded wait
  * (the results are not valid). */
 HPVM_API int hpvm_wait(hpvm_graph* graph, int64_t timeout_ms);
+/* Push one item into a streaming graph: `args` holds the item's records
+ * (as for hpvm_launch). The item runs asynchronously on the next of the
+ * graph's CUDA streams (4, round robin), so successive items overlap on
+ * the GPU; every stream first waits for the work the caller's stream had
+ * when the graph was launched. Items must not write the same buffers. */
+HPVM_API int hpvm_push(hpvm_graph* graph, const void* args, size_t args_size);
+/* Pop the oldest pushed item: wait for it (at most timeout_ms, < 0: no
+ * limit; HPVM_ERR_TIMEOUT leaves it queued), then copy its records into
+ * out (up to out_size bytes) so the caller knows which buffers hold its
+ * result. HPVM_ERR_INVALID_ARG when nothing was pushed. hpvm_wait on a
+ * streaming graph waits for every item still queued and frees the graph. */
+HPVM_API int hpvm_pop(hpvm_graph* graph, void* out, size_t out_size, int64_t timeout_ms);
+
 /* Copy the description of what `graph` launched into *out. */
 HPVM_API int hpvm_graph_info(hpvm_graph* graph, hpvm_launch_info* out);
 

@@ -32,6 +32,8 @@ HPVM_ERR_OUT_OF_MEMORY = -10
 HPVM_NODE_INTERNAL = 0
 HPVM_NODE_ALLOCATION = 1
 HPVM_NODE_SGEMM_LEAF = 2
+HPVM_NODE_TANH_LEAF = 3
+HPVM_NODE_TANH_GRAD_LEAF = 4
 
 HPVM_ONE_TO_ONE = 0
 HPVM_ALL_TO_ALL = 1
@@ -43,9 +45,11 @@ HPVM_TIER_BF16 = 3
 HPVM_TIER_FP8 = 4
 
 HPVM_LAUNCH_NO_EVENT = 1
+HPVM_LAUNCH_NO_FUSION = 2
 HPVM_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 HPVM_ROOTIN_PAPER_BYTES = 88
-HPVM_SGEMM_ROOT_ARGS_BYTES = 112
+HPVM_SGEMM_ROOT_ARGS_BYTES = 136
+HPVM_RECORD_PORTS = 23
 
 
 def HPVM_DIM_FROM_INPUT(p: int) -> int:
@@ -71,6 +75,8 @@ class RootArgs(ctypes.Structure):
         ("M", ctypes.c_int32), ("N", ctypes.c_int32),
         ("transA", ctypes.c_int32), ("transB", ctypes.c_int32),
         ("tier", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("aux", ctypes.c_void_p), ("bytesAux", ctypes.c_int64), ("ldaux", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -110,6 +116,8 @@ def _load() -> ctypes.CDLL:
         "hpvm_validate": (I, [P]),
         "hpvm_launch": (I, [P, P, P, SZ, I, P, PP]),
         "hpvm_wait": (I, [P, I64]),
+        "hpvm_push": (I, [P, P, SZ]),
+        "hpvm_pop": (I, [P, P, SZ, I64]),
         "hpvm_graph_info": (I, [P, ctypes.POINTER(LaunchInfo)]),
         "hpvm_track_mem": (I, [P, P, I64]),
         "hpvm_request_mem": (I, [P, P, I64]),
@@ -203,12 +211,25 @@ def hpvm_validate(root: int) -> None:
     _check(LIB.hpvm_validate(root))
 
 
-def hpvm_launch(ctx: int, root: int, args: RootArgs, stream_graph: bool = False,
+def hpvm_launch(ctx: int, root: int, args, stream_graph: bool = False,
                 cuda_stream: int = 0) -> int:
+    """``args``: one RootArgs or a ctypes array of them (one per stage)."""
     out = ctypes.c_void_p()
     _check(LIB.hpvm_launch(ctx, root, ctypes.byref(args), ctypes.sizeof(args),
                            int(bool(stream_graph)), cuda_stream or None, ctypes.byref(out)))
     return out.value
+
+
+def hpvm_push(graph: int, args) -> None:
+    _check(LIB.hpvm_push(graph, ctypes.byref(args), ctypes.sizeof(args)))
+
+
+def hpvm_pop(graph: int, out=None, timeout_ms: int = -1) -> None:
+    """Pop the oldest item; ``out`` (RootArgs or array) receives its records."""
+    if out is None:
+        _check(LIB.hpvm_pop(graph, None, 0, int(timeout_ms)))
+    else:
+        _check(LIB.hpvm_pop(graph, ctypes.byref(out), ctypes.sizeof(out), int(timeout_ms)))
 
 
 def hpvm_wait(graph: int, timeout_ms: int = -1) -> None:
@@ -233,7 +254,7 @@ def hpvm_untrack_mem(ctx: int, ptr: int) -> None:
     _check(LIB.hpvm_untrack_mem(ctx, ptr))
 
 
-def hpvm_workspace_size(ctx: int, root: int, args: RootArgs) -> int:
+def hpvm_workspace_size(ctx: int, root: int, args) -> int:
     out = ctypes.c_size_t()
     _check(LIB.hpvm_workspace_size(ctx, root, ctypes.byref(args), ctypes.sizeof(args), ctypes.byref(out)))
     return out.value

@@ -1,0 +1,264 @@
+"""The differentiable streamed chain: sgemm stages joined by tanh leaves.
+
+Row-major items X (rows x w) flow through L weights W_l (w x w):
+Z_0 = X W_0, Z_l = tanh(Z_{l-1}) W_l, Y = Z_{L-1}. In the dataflow graph
+each stage is a tile grid holding the sgemm example's Allocation and
+SgemmLeaf plus, between stages, a TanhLeaf joined to the SgemmLeaf by
+one-to-one edges (merged into the leaf's epilogue, MergeDependentNodes);
+stages are joined by streaming all-to-all edges that carry the result
+matrix (Sections 3.1, 4.5, 4.6).
+
+A row-major matrix is a column-major matrix of the transposed shape, so
+Z = H W is computed as the column-major sgemm Z^T = W^T H^T (M = w_out,
+N = rows, K = w_in, op(A) = A, op(B) = B), and the adjoint products of the
+sgemm leaf are sgemm leaves with the roles reversed:
+    dW^T = dZ^T H     (M = w_out, N = w_in, K = rows, op(B) = B^T)
+    dH^T = W dZ^T     (M = w_in,  N = rows, K = w_out, op(A) = A^T)
+and the adjoint of the tanh leaf is the TanhGradLeaf, dZ_{l-1} =
+dH_l * (1 - H_l^2), merged into the dH product's epilogue.
+
+Argument marshalling only: every product and elementwise leaf runs in the
+library's kernels through the C-ABI. PyTorch provides memory and streams.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as H
+from .sgemm import make_args
+
+REC = H.HPVM_RECORD_PORTS  # root ports per stage record
+
+
+def _add_stage(ctx: int, root: int, base: int, ew_kind: int | None, b_from_edge: bool):
+    """One tile-grid stage under ``root`` whose inputs are root ports
+    base + field (see hpvm_sgemm_root_args). Returns the stage node."""
+    st = H.hpvm_create_node(ctx, root, H.HPVM_NODE_INTERNAL,
+                            (H.HPVM_DIM_FROM_INPUT(base + 14), H.HPVM_DIM_FROM_INPUT(base + 15)))
+    # stage inputs: 0..19 = the record fields 0..13, 16..19 as in the sgemm
+    # internal node; 20..22 = aux, bytesAux, ldaux
+    for p in range(14):
+        if b_from_edge and p in (3, 4):
+            continue  # B and bytesB arrive over the streaming edge
+        H.hpvm_bind_input(st, base + p, p)
+    for q in range(4):
+        H.hpvm_bind_input(st, base + 16 + q, 14 + q)
+    if ew_kind == H.HPVM_NODE_TANH_GRAD_LEAF:
+        for q in range(3):
+            H.hpvm_bind_input(st, base + 20 + q, 18 + q)
+    alloc = H.hpvm_create_node(ctx, st, H.HPVM_NODE_ALLOCATION)
+    leaf = H.hpvm_create_node(ctx, st, H.HPVM_NODE_SGEMM_LEAF,
+                              (H.HPVM_DIM_FROM_INPUT(12), H.HPVM_DIM_FROM_INPUT(13)))
+    for sp, dp in ((0, 12), (1, 13), (2, 14), (3, 15)):
+        H.hpvm_create_edge(alloc, leaf, H.HPVM_ALL_TO_ALL, sp, dp)
+    for p in range(12):
+        H.hpvm_bind_input(leaf, p, p)
+    for q in range(4):
+        H.hpvm_bind_input(leaf, 14 + q, 16 + q)
+    H.hpvm_bind_input(alloc, 12, 0)
+    H.hpvm_bind_input(alloc, 13, 1)
+    last = leaf
+    if ew_kind is not None:
+        ew = H.hpvm_create_node(ctx, st, ew_kind,
+                                (H.HPVM_DIM_FROM_INPUT(12), H.HPVM_DIM_FROM_INPUT(13)))
+        H.hpvm_create_edge(leaf, ew, H.HPVM_ONE_TO_ONE, 0, 0)
+        H.hpvm_create_edge(leaf, ew, H.HPVM_ONE_TO_ONE, 1, 1)
+        H.hpvm_bind_input(ew, 8, 2)    # ld = ldc
+        H.hpvm_bind_input(ew, 14, 3)   # M
+        H.hpvm_bind_input(ew, 15, 4)   # N
+        if ew_kind == H.HPVM_NODE_TANH_GRAD_LEAF:
+            for q in range(3):
+                H.hpvm_bind_input(ew, 18 + q, 5 + q)  # H, bytesH, ldh
+        last = ew
+    H.hpvm_bind_output(last, 0, 0)
+    H.hpvm_bind_output(last, 1, 1)
+    return st
+
+
+def build_chain_graph(ctx: int, layers: int) -> int:
+    """Root -> ``layers`` stages, tanh merged into every stage but the last,
+    stage l's result streamed into stage l+1's B. Returns the root."""
+    root = H.hpvm_create_node(ctx, None, H.HPVM_NODE_INTERNAL)
+    prev = None
+    for l in range(layers):
+        st = _add_stage(ctx, root, REC * l, H.HPVM_NODE_TANH_LEAF if l + 1 < layers else None,
+                        b_from_edge=prev is not None)
+        if prev is not None:
+            H.hpvm_create_edge(prev, st, H.HPVM_ALL_TO_ALL, 0, 3, stream=True)
+            H.hpvm_create_edge(prev, st, H.HPVM_ALL_TO_ALL, 1, 4, stream=True)
+        prev = st
+    H.hpvm_bind_output(prev, 0, 0, stream=True)
+    H.hpvm_validate(root)
+    return root
+
+
+def build_single_stage_graph(ctx: int, ew_kind: int | None) -> int:
+    """Root -> one stage with an optional merged elementwise leaf."""
+    root = H.hpvm_create_node(ctx, None, H.HPVM_NODE_INTERNAL)
+    st = _add_stage(ctx, root, 0, ew_kind, b_from_edge=False)
+    H.hpvm_bind_output(st, 0, 0)
+    H.hpvm_validate(root)
+    return root
+
+
+def _rm_product_args(out: torch.Tensor, Hm: torch.Tensor, W: torch.Tensor, tier: int, flags: int = 0):
+    """Record for the row-major product out = Hm @ W (out: r x c, Hm: r x k,
+    W: k x c) as the column-major sgemm out^T = W^T Hm^T."""
+    r, k = Hm.shape
+    c = W.shape[1]
+    return make_args(c, r, k, W.data_ptr(), W.numel() * 4, c, Hm.data_ptr(), Hm.numel() * 4, k,
+                     out.data_ptr(), out.numel() * 4, c, 1.0, 0.0, False, False, tier, flags=flags)
+
+
+class ChainEngine:
+    """The chain's graphs on one device: forward chain, one-stage graphs with
+    a merged tanh (recomputation) or tanh adjoint, and the plain sgemm stage
+    (weight gradients, input gradient)."""
+
+    def __init__(self, layers: int, device: int = 0, tier: int = H.HPVM_TIER_BF16, fuse: bool = True):
+        self.layers = layers
+        self.device = device
+        self.tier = tier
+        self.flags = 0 if fuse else H.HPVM_LAUNCH_NO_FUSION
+        self.ctx = H.hpvm_init(device)
+        self.chain = build_chain_graph(self.ctx, layers)
+        self.stage_tanh = build_single_stage_graph(self.ctx, H.HPVM_NODE_TANH_LEAF)
+        self.stage_dtanh = build_single_stage_graph(self.ctx, H.HPVM_NODE_TANH_GRAD_LEAF)
+        self.stage_plain = build_single_stage_graph(self.ctx, None)
+        self._ws = None
+
+    def close(self):
+        if self.ctx:
+            H.hpvm_cleanup(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers --------------------------------------------------------------
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _run(self, root: int, args) -> None:
+        need = H.hpvm_workspace_size(self.ctx, root, args)
+        if need and (self._ws is None or self._ws.numel() < need):
+            self._ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
+            H.hpvm_set_workspace(self.ctx, self._ws.data_ptr(), self._ws.numel())
+        g = H.hpvm_launch(self.ctx, root, args, False, self._stream())
+        H.hpvm_wait(g, 600000)
+
+    def chain_records(self, X: torch.Tensor, Ws, outs):
+        """Records of the chain graph: stage l computes outs[l] = act(in_l) W_l."""
+        arr = (H.RootArgs * self.layers)()
+        for l in range(self.layers):
+            src = X if l == 0 else outs[l - 1]
+            arr[l] = _rm_product_args(outs[l], src, Ws[l], self.tier, self.flags)
+            if l > 0:  # B arrives over the streaming edge
+                arr[l].B = None
+                arr[l].bytesB = 0
+        return arr
+
+    # -- forward ------------------------------------------------------------------
+    def forward(self, X: torch.Tensor, Ws, keep: bool = False):
+        """Y for row-major X (rows x w). With keep, also the activations
+        H_1..H_{L-1} (the tanh outputs, the chain's intermediate buffers)."""
+        outs = [torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws]
+        self._run(self.chain, self.chain_records(X, Ws, outs))
+        return (outs[-1], outs[:-1]) if keep else outs[-1]
+
+    def recompute(self, X: torch.Tensor, Ws):
+        """H_0 = X and H_l = tanh(H_{l-1} W_{l-1}) for l = 1..L-1, stage by stage."""
+        Hs = [X]
+        for l in range(self.layers - 1):
+            out = torch.empty(X.shape[0], Ws[l].shape[1], device=X.device)
+            self._run(self.stage_tanh, _rm_product_args(out, Hs[-1], Ws[l], self.tier, self.flags))
+            Hs.append(out)
+        return Hs
+
+    # -- backward -----------------------------------------------------------------
+    def backward(self, X: torch.Tensor, Ws, G: torch.Tensor):
+        """dX and dW_l of sum(Y * G), recomputing the activations."""
+        Hs = self.recompute(X, Ws)
+        L = self.layers
+        dWs = [None] * L
+        dZ = G.contiguous()
+        dX = None
+        rows = X.shape[0]
+        for l in range(L - 1, -1, -1):
+            W = Ws[l]
+            w_in, w_out = W.shape
+            # dW^T = dZ^T H_l: M = w_out, N = w_in, K = rows; A = dZ buffer, B = H_l buffer (B^T)
+            dW = torch.empty_like(W)
+            a = make_args(w_out, w_in, rows, dZ.data_ptr(), dZ.numel() * 4, w_out, Hs[l].data_ptr(),
+                          Hs[l].numel() * 4, w_in, dW.data_ptr(), dW.numel() * 4, w_out, 1.0, 0.0,
+                          False, True, self.tier, flags=self.flags)
+            self._run(self.stage_plain, a)
+            dWs[l] = dW
+            # dH^T = W dZ^T: M = w_in, N = rows, K = w_out; A = W buffer (A^T), B = dZ buffer
+            dH = torch.empty(rows, w_in, device=X.device)
+            a = make_args(w_in, rows, w_out, W.data_ptr(), W.numel() * 4, w_out, dZ.data_ptr(),
+                          dZ.numel() * 4, w_out, dH.data_ptr(), dH.numel() * 4, w_in, 1.0, 0.0,
+                          True, False, self.tier, flags=self.flags)
+            if l > 0:
+                # merged tanh adjoint: dZ_{l-1} = dH * (1 - H_l^2)
+                a.aux, a.bytesAux, a.ldaux = Hs[l].data_ptr(), Hs[l].numel() * 4, w_in
+                self._run(self.stage_dtanh, a)
+                dZ = dH
+            else:
+                self._run(self.stage_plain, a)
+                dX = dH
+        return dX, dWs
+
+    # -- streaming -----------------------------------------------------------------
+    def stream_forward(self, items, Ws, timeout_ms: int = 600000):
+        """Push every item (row-major rows x w) through the chain launched as a
+        streaming graph and pop the outputs in order (hpvm_push / hpvm_pop)."""
+        outs_all = [[torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws] for X in items]
+        rec0 = self.chain_records(items[0], Ws, outs_all[0])
+        g = H.hpvm_launch(self.ctx, self.chain, rec0, True, self._stream())
+        try:
+            for X, outs in zip(items, outs_all):
+                H.hpvm_push(g, self.chain_records(X, Ws, outs))
+            popped = []
+            for _ in items:
+                rec = (H.RootArgs * self.layers)()
+                H.hpvm_pop(g, rec, timeout_ms)
+                popped.append(rec[self.layers - 1].C)
+        finally:
+            H.hpvm_wait(g, timeout_ms)
+        results = [outs[-1] for outs in outs_all]
+        assert popped == [r.data_ptr() for r in results]
+        return results
+
+
+class ChainFunction(torch.autograd.Function):
+    """Y = chain(X; W_0..W_{L-1}) with the library's forward and adjoint
+    leaves; the backward recomputes the activations from X."""
+
+    @staticmethod
+    def forward(ctx, engine: ChainEngine, X: torch.Tensor, *Ws: torch.Tensor):
+        X = X.contiguous()
+        Ws = [W.contiguous() for W in Ws]
+        ctx.engine = engine
+        ctx.save_for_backward(X, *Ws)
+        return engine.forward(X, Ws)
+
+    @staticmethod
+    def backward(ctx, G: torch.Tensor):
+        X, *Ws = ctx.saved_tensors
+        dX, dWs = ctx.engine.backward(X, Ws, G.contiguous().float())
+        return (None, dX, *dWs)
+
+
+def chain_apply(engine: ChainEngine, X: torch.Tensor, Ws) -> torch.Tensor:
+    """Differentiable chain over X of shape (..., w): leading dimensions are
+    the items and their rows, flattened into one product per stage."""
+    shape = X.shape
+    Y = ChainFunction.apply(engine, X.reshape(-1, shape[-1]), *Ws)
+    return Y.reshape(*shape[:-1], Ws[-1].shape[1])
+
+
+__all__ = ["ChainEngine", "ChainFunction", "chain_apply", "build_chain_graph", "build_single_stage_graph"]

@@ -223,6 +223,25 @@ sgemm_fp32_tiled(SgemmDesc d, int vec_a, int vec_b, int vec_c) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Elementwise leaves over the column-major M x N result (one thread per
+// element, consecutive threads on consecutive rows): kind 1 applies tanh,
+// kind 2 multiplies by 1 - H^2 (the derivative of tanh at the forward value H).
+__global__ void elementwise_leaf(float* C, int64_t ldc, int64_t M, int64_t N, int kind, const float* H,
+                                 int64_t ldh) {
+  const int64_t total = M * N;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % M, j = t / M;
+    float* c = C + i + j * ldc;
+    if (kind == 1) {
+      *c = tanhf(*c);
+    } else {
+      const float h = H[i + j * ldh];
+      *c = *c * (1.f - h * h);
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_fp32_dfg(const SgemmDesc& d, int block, int grid_x, int grid_y,
@@ -262,6 +281,15 @@ cudaError_t launch_fp32_dfg(const SgemmDesc& d, int block, int grid_x, int grid_
 }
 
 void fp32_tiled_tile(int* tm, int* tn) { *tm = TBM; *tn = TBN; }
+
+cudaError_t launch_elementwise(const SgemmDesc& d, const Epilogue& e, cudaStream_t s) {
+  if (e.kind == 0 || d.M == 0 || d.N == 0) return cudaSuccess;
+  const int64_t total = d.M * d.N;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  elementwise_leaf<<<(unsigned)blocks, 256, 0, s>>>(d.C, d.ldc, d.M, d.N, e.kind, e.aux, e.ldaux);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fp32_tiled(const SgemmDesc& d, cudaStream_t s, KernelReport* rep,
                               const LaunchHooks* hooks) {

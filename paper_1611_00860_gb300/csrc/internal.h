@@ -54,6 +54,16 @@ inline void hook_end(const LaunchHooks* h, cudaStream_t s) {
   if (h && h->main_end) cudaEventRecord(h->main_end, s);
 }
 
+// Elementwise leaf merged into (or run after) a sgemm leaf:
+// kind 1: C <- tanh(C); kind 2: C <- C * (1 - H^2) with H column-major (ldaux).
+struct Epilogue {
+  int kind = 0;
+  const float* aux = nullptr;
+  int64_t ldaux = 0;
+};
+// Standalone elementwise kernel on the M x N column-major C (fp32_leaf.cu).
+cudaError_t launch_elementwise(const SgemmDesc& d, const Epilogue& e, cudaStream_t s);
+
 // ---- FP32 CUDA-core leaves (fp32_leaf.cu) ---------------------------------
 // Literal Section 4.4 mapping: CTA (bx, by) = internal instance, thread
 // (tx, ty) = leaf instance, tiles of the Allocation node in shared memory.
@@ -66,14 +76,15 @@ cudaError_t launch_fp32_tiled(const SgemmDesc& d, cudaStream_t s,
 void fp32_tiled_tile(int* tm, int* tn);
 
 // ---- tensor-core leaves (tc_leaf.cu) --------------------------------------
-// tier: 2 = BF16x3 split, 3 = BF16.
+// tier: 2 = BF16x3 split, 3 = BF16, 4 = FP8. `epi` is fused into the
+// leaf's epilogue (after alpha*acc + beta*C).
 size_t tc_workspace_bytes(const SgemmDesc& d, int tier);
 // Returns a cudaError_t; on a host-side precondition failure returns
 // cudaErrorInvalidValue and fills *err.
 cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes,
                       const DeviceStatus& st, cudaStream_t s,
                       KernelReport* rep, std::string* err,
-                      const LaunchHooks* hooks);
+                      const LaunchHooks* hooks, const Epilogue& epi = Epilogue());
 void tc_tile(int tier, int* tm, int* tn);
 
 // Sets the calling thread's hpvm_last_error() message (cleared for HPVM_OK)

@@ -1,9 +1,17 @@
-// Host runtime of the C-ABI (include/hpvm.h): graph builder (the paper's
-// Graph Builder pass, Section 4.2, fed by intrinsic calls instead of IR),
-// validator (rules of Sections 3.1-3.2), lowering of the sgemm graph shape
-// (Section 4.4 tiling, the host code of Section 5.3: Allocation size known
-// before the launch, local/global work sizes from the two grids), launch and
-// bounded wait, and the memory tracker of Section 3.3.
+// Host runtime of the C-ABI (include/hpvm.h).
+//
+//  * Graph builder (the paper's Graph Builder pass, Section 4.2, fed by the
+//    intrinsic calls of Table 1 instead of IR) and validator (the rules of
+//    Sections 3.1-3.2).
+//  * Lowering (Sections 4.3-4.4 and the generated host code of Section 5.3):
+//    every input of a leaf is resolved by following edges and bindings up to
+//    a field of the root's argument records; the Allocation size is computed
+//    on the host before the launch; each tile-grid stage becomes one leaf
+//    kernel launch, with a dependent elementwise leaf merged into the
+//    kernel's epilogue (MergeDependentNodes, Section 4.6) or run after it.
+//  * Launch and bounded wait; streaming graphs (Section 4.5) whose items are
+//    pushed and popped, pipelined over a ring of CUDA streams.
+//  * The memory tracker of Section 3.3.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -11,6 +19,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <memory>
 #include <set>
 #include <string>
@@ -42,26 +51,33 @@ int ok() {
   return HPVM_OK;
 }
 
-constexpr int kMaxPorts = 64;
+constexpr int kMaxPorts = 64;  // ports of an internal node below the root
 
-// Types of the sgemm root record fields (port p = field p).
+// The root's argument records: port p of the root is field p % kRecPorts of
+// record p / kRecPorts (one record per stage of a multi-stage graph).
 enum FieldType { F_PTR, F_I64, F_I32, F_F32 };
-constexpr int kRootPorts = 20;
-constexpr FieldType kRootType[kRootPorts] = {
-    F_PTR, F_I64, F_I32,  // A, bytesA, lda
-    F_PTR, F_I64, F_I32,  // B, bytesB, ldb
-    F_PTR, F_I64, F_I32,  // C, bytesC, ldc
-    F_I32, F_F32, F_F32,  // k, alpha, beta
-    F_I32, F_I32, F_I32, F_I32,  // block_x, block_y, grid_x, grid_y
-    F_I32, F_I32, F_I32, F_I32,  // M, N, transA, transB
+constexpr int kRecPorts = 23;
+constexpr int kMaxRecords = 16;
+constexpr int kRootPorts = kRecPorts * kMaxRecords;
+constexpr size_t kRecBytes = HPVM_SGEMM_ROOT_ARGS_BYTES;
+constexpr FieldType kRecType[kRecPorts] = {
+    F_PTR, F_I64, F_I32,          // A, bytesA, lda
+    F_PTR, F_I64, F_I32,          // B, bytesB, ldb
+    F_PTR, F_I64, F_I32,          // C, bytesC, ldc
+    F_I32, F_F32, F_F32,          // k, alpha, beta
+    F_I32, F_I32, F_I32, F_I32,   // block_x, block_y, grid_x, grid_y
+    F_I32, F_I32, F_I32, F_I32,   // M, N, transA, transB
+    F_PTR, F_I64, F_I32,          // aux, bytesAux, ldaux
 };
-constexpr size_t kRootOffset[kRootPorts] = {0, 8, 16, 20, 28, 36, 40, 48, 56, 60, 64, 68,
-                                            72, 76, 80, 84, 88, 92, 96, 100};
-const char* kRootName[kRootPorts] = {"A", "bytesA", "lda", "B", "bytesB", "ldb", "C",
-                                     "bytesC", "ldc", "k", "alpha", "beta", "block_x",
-                                     "block_y", "grid_x", "grid_y", "M", "N", "transA", "transB"};
+constexpr size_t kRecOffset[kRecPorts] = {0,  8,  16, 20, 28, 36, 40, 48, 56, 60, 64, 68,
+                                          72, 76, 80, 84, 88, 92, 96, 100, 112, 120, 128};
+constexpr size_t kTierOffset = 104, kFlagsOffset = 108;
+const char* kRecName[kRecPorts] = {"A",       "bytesA",  "lda",    "B",      "bytesB", "ldb",
+                                   "C",       "bytesC",  "ldc",    "k",      "alpha",  "beta",
+                                   "block_x", "block_y", "grid_x", "grid_y", "M",      "N",
+                                   "transA",  "transB",  "aux",    "bytesAux", "ldaux"};
 
-// Input ports of the SgemmLeaf node function and their types.
+// Input ports of the leaf node functions and their types.
 constexpr int kLeafPorts = 20;
 constexpr FieldType kLeafType[kLeafPorts] = {
     F_PTR, F_I64, F_I32, F_PTR, F_I64, F_I32, F_PTR, F_I64, F_I32,  // A..ldc
@@ -69,17 +85,20 @@ constexpr FieldType kLeafType[kLeafPorts] = {
     F_PTR, F_I64, F_PTR, F_I64,  // shB, bytesShB, shA, bytesShA (Allocation)
     F_I32, F_I32, F_I32, F_I32,  // M, N, transA, transB
 };
-// Leaf port -> the root field with the same meaning (for the data ports)
-constexpr int kLeafMeaning[kLeafPorts] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11,
-                                          -1, -1, -1, -1, 16, 17, 18, 19};
+constexpr int kTanhPorts = 5;      // X, bytesX, ldx, M, N
+constexpr int kTanhGradPorts = 8;  // G, bytesG, ldg, M, N, H, bytesH, ldh
+constexpr FieldType kEwType[kTanhGradPorts] = {F_PTR, F_I64, F_I32, F_I32, F_I32, F_PTR, F_I64, F_I32};
 constexpr int kAllocInPorts = 2, kAllocOutPorts = 4;
 constexpr FieldType kAllocOutType[kAllocOutPorts] = {F_PTR, F_I64, F_PTR, F_I64};
+constexpr int kStreamSlots = 4;  // CUDA streams of a streaming graph
 
 const char* kind_name(int k) {
   switch (k) {
     case HPVM_NODE_INTERNAL: return "internal";
     case HPVM_NODE_ALLOCATION: return "Allocation";
     case HPVM_NODE_SGEMM_LEAF: return "SgemmLeaf";
+    case HPVM_NODE_TANH_LEAF: return "TanhLeaf";
+    case HPVM_NODE_TANH_GRAD_LEAF: return "TanhGradLeaf";
   }
   return "?";
 }
@@ -98,9 +117,11 @@ struct hpvm_edge {
   int repl, sp, dp, stream;
 };
 
+// in_binds: input `outer` of the parent feeds input `inner` of child.
+// out_binds: output `inner` of child becomes output `outer` of the parent.
 struct Bind {
   hpvm_node* child;
-  int ip, ic, stream;
+  int outer, inner, stream;
 };
 
 struct hpvm_node {
@@ -112,8 +133,8 @@ struct hpvm_node {
   int id = 0;
   std::vector<hpvm_node*> children;
   std::vector<hpvm_edge*> edges;   // among children
-  std::vector<Bind> in_binds;      // parent input -> child input
-  std::vector<Bind> out_binds;     // child output -> parent output
+  std::vector<Bind> in_binds;
+  std::vector<Bind> out_binds;
 };
 
 struct TrackEntry {
@@ -123,11 +144,25 @@ struct TrackEntry {
   bool host_valid = true, dev_valid = false;
 };
 
+// one pushed item of a streaming graph
+struct StreamItem {
+  std::vector<uint8_t> record;
+  cudaEvent_t done = nullptr;
+};
+
 struct hpvm_graph {
   hpvm_ctx* ctx = nullptr;
   cudaEvent_t done = nullptr;
   cudaStream_t stream = nullptr;
   hpvm_launch_info info{};
+  // streaming graphs
+  bool streaming = false;
+  hpvm_node* root = nullptr;
+  std::vector<cudaStream_t> slots;
+  std::vector<void*> slot_ws;
+  std::vector<size_t> slot_ws_bytes;
+  std::deque<StreamItem> items;
+  uint64_t pushed = 0;
 };
 
 struct hpvm_ctx {
@@ -149,21 +184,29 @@ struct hpvm_ctx {
 // helpers
 namespace {
 
+bool is_leaf(const hpvm_node* n) { return n->kind != HPVM_NODE_INTERNAL; }
+bool is_elementwise(const hpvm_node* n) {
+  return n->kind == HPVM_NODE_TANH_LEAF || n->kind == HPVM_NODE_TANH_GRAD_LEAF;
+}
+
 int in_arity(const hpvm_node* n) {
   switch (n->kind) {
     case HPVM_NODE_SGEMM_LEAF: return kLeafPorts;
     case HPVM_NODE_ALLOCATION: return kAllocInPorts;
+    case HPVM_NODE_TANH_LEAF: return kTanhPorts;
+    case HPVM_NODE_TANH_GRAD_LEAF: return kTanhGradPorts;
     default: return n->parent == nullptr ? kRootPorts : kMaxPorts;
   }
 }
 int out_arity(const hpvm_node* n) {
   switch (n->kind) {
-    case HPVM_NODE_SGEMM_LEAF: return 0;
+    case HPVM_NODE_SGEMM_LEAF: return 2;  // the result matrix C and its bytes
     case HPVM_NODE_ALLOCATION: return kAllocOutPorts;
+    case HPVM_NODE_TANH_LEAF:
+    case HPVM_NODE_TANH_GRAD_LEAF: return 2;  // the matrix it updated, bytes
     default: return kMaxPorts;
   }
 }
-bool is_leaf(const hpvm_node* n) { return n->kind != HPVM_NODE_INTERNAL; }
 
 std::string node_label(const hpvm_node* n) {
   char b[64];
@@ -179,23 +222,55 @@ std::vector<int> feed_counts(const hpvm_node* child) {
   for (auto* e : par->edges)
     if (e->dst == child && e->dp < (int)cnt.size()) cnt[e->dp]++;
   for (auto& b : par->in_binds)
-    if (b.child == child && b.ic < (int)cnt.size()) cnt[b.ic]++;
+    if (b.child == child && b.inner < (int)cnt.size()) cnt[b.inner]++;
   return cnt;
 }
 
 // ports of `n` that something under it reads (bindings to its children and
 // replication extents of its children)
 std::vector<bool> used_inputs(const hpvm_node* n) {
-  std::vector<bool> used(kMaxPorts, false);
+  std::vector<bool> used(in_arity(n), false);
   for (auto& b : n->in_binds)
-    if (b.ip >= 0 && b.ip < kMaxPorts) used[b.ip] = true;
+    if (b.outer >= 0 && b.outer < (int)used.size()) used[b.outer] = true;
   for (auto* c : n->children)
     for (int d = 0; d < c->ndims; ++d)
       if (c->dims[d] < 0) {
         int64_t p = -1 - c->dims[d];
-        if (p < kMaxPorts) used[p] = true;
+        if (p < (int64_t)used.size()) used[p] = true;
       }
   return used;
+}
+
+int index_of(const hpvm_node* parent, const hpvm_node* c) {
+  for (size_t i = 0; i < parent->children.size(); ++i)
+    if (parent->children[i] == c) return (int)i;
+  return -1;
+}
+
+// Children of n in an order compatible with its edges; fails on a cycle.
+int topo_children(const hpvm_node* n, std::vector<hpvm_node*>* order) {
+  const size_t m = n->children.size();
+  std::vector<int> indeg(m, 0);
+  for (auto* e : n->edges) {
+    int v = index_of(n, e->dst);
+    if (v >= 0) indeg[v]++;
+  }
+  std::deque<int> ready;
+  for (size_t i = 0; i < m; ++i)
+    if (indeg[i] == 0) ready.push_back((int)i);
+  order->clear();
+  while (!ready.empty()) {
+    int u = ready.front();
+    ready.pop_front();
+    order->push_back(n->children[u]);
+    for (auto* e : n->edges)
+      if (e->src == n->children[u]) {
+        int v = index_of(n, e->dst);
+        if (v >= 0 && --indeg[v] == 0) ready.push_back(v);
+      }
+  }
+  if (order->size() != m) return fail(HPVM_ERR_INVALID_GRAPH, "cycle of edges under %s", node_label(n).c_str());
+  return HPVM_OK;
 }
 
 int validate_node(const hpvm_node* n) {
@@ -204,7 +279,6 @@ int validate_node(const hpvm_node* n) {
       return fail(HPVM_ERR_INVALID_GRAPH, "%s: a leaf node has children", node_label(n).c_str());
     return HPVM_OK;
   }
-  // edges among children
   for (auto* e : n->edges) {
     if (e->src->parent != n || e->dst->parent != n)
       return fail(HPVM_ERR_INVALID_GRAPH, "edge endpoints are not children of %s", node_label(n).c_str());
@@ -217,39 +291,9 @@ int validate_node(const hpvm_node* n) {
                     node_label(e->src).c_str(), node_label(e->dst).c_str());
     }
   }
-  // no cycle of ordinary edges (DFS over children)
-  {
-    std::vector<int> state(n->children.size(), 0);
-    auto index_of = [&](const hpvm_node* c) {
-      for (size_t i = 0; i < n->children.size(); ++i)
-        if (n->children[i] == c) return (int)i;
-      return -1;
-    };
-    std::vector<std::pair<int, size_t>> stack;
-    for (size_t r = 0; r < n->children.size(); ++r) {
-      if (state[r]) continue;
-      stack.push_back({(int)r, 0});
-      state[r] = 1;
-      while (!stack.empty()) {
-        auto& [u, ei] = stack.back();
-        if (ei >= n->edges.size()) {
-          state[u] = 2;
-          stack.pop_back();
-          continue;
-        }
-        auto* e = n->edges[ei++];
-        if (e->src != n->children[u]) continue;
-        int v = index_of(e->dst);
-        if (v < 0) continue;
-        if (state[v] == 1) return fail(HPVM_ERR_INVALID_GRAPH, "cycle of edges under %s", node_label(n).c_str());
-        if (state[v] == 0) {
-          state[v] = 1;
-          stack.push_back({v, 0});
-        }
-      }
-    }
-  }
-  // every input a child reads is fed exactly once
+  std::vector<hpvm_node*> order;
+  int rc = topo_children(n, &order);
+  if (rc != HPVM_OK) return rc;
   for (auto* c : n->children) {
     auto cnt = feed_counts(c);
     if (is_leaf(c)) {
@@ -264,7 +308,7 @@ int validate_node(const hpvm_node* n) {
     } else {
       auto used = used_inputs(c);
       for (int p = 0; p < (int)cnt.size(); ++p) {
-        if (used[p] && cnt[p] == 0)
+        if (p < (int)used.size() && used[p] && cnt[p] == 0)
           return fail(HPVM_ERR_INVALID_GRAPH, "input %d of %s is read but never fed", p,
                       node_label(c).c_str());
         if (cnt[p] > 1)
@@ -272,59 +316,96 @@ int validate_node(const hpvm_node* n) {
                       cnt[p]);
       }
     }
-    int rc = validate_node(c);
+    rc = validate_node(c);
     if (rc != HPVM_OK) return rc;
   }
   return HPVM_OK;
 }
 
-// ---- value resolution for lowering --------------------------------------
-// Where the value of an input port comes from: a root record field, or an
-// output of an Allocation node.
+// ---- value resolution -------------------------------------------------------
+// Where a value comes from: a field of a root record, or an output of an
+// Allocation node. Outputs of compute leaves and stages pass their inputs
+// through (the matrix a leaf wrote), so every value resolves to one of the two.
 struct Source {
-  int root_field = -1;
+  int rec = -1, field = -1;
   hpvm_node* alloc = nullptr;
   int alloc_out = -1;
 };
 
-bool input_source(const hpvm_node* n, int port, Source* out);
+bool input_source(const hpvm_node* n, int port, Source* out, int depth = 0);
 
-// value of input `port` of internal node `n` (root: the record field)
-bool value_of_input(const hpvm_node* n, int port, Source* out) {
+bool value_of_input(const hpvm_node* n, int port, Source* out, int depth) {
   if (n->parent == nullptr) {
     if (port < 0 || port >= kRootPorts) return false;
-    out->root_field = port;
+    out->rec = port / kRecPorts;
+    out->field = port % kRecPorts;
     return true;
   }
-  return input_source(n, port, out);
+  return input_source(n, port, out, depth + 1);
 }
 
-bool input_source(const hpvm_node* n, int port, Source* out) {
-  const hpvm_node* par = n->parent;
-  if (!par) return value_of_input(n, port, out);
-  for (auto* e : par->edges)
-    if (e->dst == n && e->dp == port) {
-      if (e->src->kind != HPVM_NODE_ALLOCATION) return false;
-      out->alloc = e->src;
-      out->alloc_out = e->sp;
+bool output_source(const hpvm_node* n, int port, Source* out, int depth) {
+  if (depth > 64) return false;
+  switch (n->kind) {
+    case HPVM_NODE_SGEMM_LEAF:
+      return (port == 0 || port == 1) && input_source(n, 6 + port, out, depth + 1);
+    case HPVM_NODE_TANH_LEAF:
+    case HPVM_NODE_TANH_GRAD_LEAF:
+      return (port == 0 || port == 1) && input_source(n, port, out, depth + 1);
+    case HPVM_NODE_ALLOCATION:
+      out->alloc = const_cast<hpvm_node*>(n);
+      out->alloc_out = port;
       return true;
-    }
+    default:
+      for (auto& b : n->out_binds)
+        if (b.outer == port) return output_source(b.child, b.inner, out, depth + 1);
+      return false;
+  }
+}
+
+bool input_source(const hpvm_node* n, int port, Source* out, int depth) {
+  if (depth > 64) return false;
+  const hpvm_node* par = n->parent;
+  if (!par) return value_of_input(n, port, out, depth);
+  for (auto* e : par->edges)
+    if (e->dst == n && e->dp == port) return output_source(e->src, e->sp, out, depth + 1);
   for (auto& b : par->in_binds)
-    if (b.child == n && b.ic == port) return value_of_input(par, b.ip, out);
+    if (b.child == n && b.inner == port) return value_of_input(par, b.outer, out, depth + 1);
   return false;
 }
 
-struct RootRecord {
+struct Records {
   const uint8_t* base;
+  int count;
   template <class T>
-  T get(int field) const {
+  T get(int rec, int field) const {
     T v;
-    memcpy(&v, base + kRootOffset[field], sizeof(T));
+    memcpy(&v, base + rec * kRecBytes + kRecOffset[field], sizeof(T));
     return v;
   }
 };
 
-bool extent_of(const hpvm_node* n, int d, const RootRecord& rec, int64_t* out) {
+// Read a resolved root field of the expected type.
+int read_field(const Records& R, const Source& s, FieldType want, const char* who, int port, int64_t* i,
+               double* f, void** p) {
+  if (s.rec < 0 || s.field < 0)
+    return fail(HPVM_ERR_UNSUPPORTED, "%s input %d must come from the root records", who, port);
+  if (s.rec >= R.count)
+    return fail(HPVM_ERR_INVALID_ARG, "%s input %d reads record %d, only %d records were passed", who, port, s.rec,
+                R.count);
+  if (kRecType[s.field] != want)
+    return fail(HPVM_ERR_INVALID_GRAPH, "%s input %d is bound to root field %s of another type", who, port,
+                kRecName[s.field]);
+  switch (want) {
+    case F_PTR: *p = R.get<void*>(s.rec, s.field); break;
+    case F_I64: *i = R.get<int64_t>(s.rec, s.field); break;
+    case F_I32: *i = R.get<int32_t>(s.rec, s.field); break;
+    case F_F32: *f = R.get<float>(s.rec, s.field); break;
+  }
+  return HPVM_OK;
+}
+
+bool extent_of(const hpvm_node* n, int d, const Records& R, int64_t* out) {
   if (d >= n->ndims) {
     *out = 1;
     return true;
@@ -334,143 +415,238 @@ bool extent_of(const hpvm_node* n, int d, const RootRecord& rec, int64_t* out) {
     return true;
   }
   Source s;
-  if (!value_of_input(n->parent, (int)(-1 - n->dims[d]), &s) || s.root_field < 0) return false;
-  if (kRootType[s.root_field] != F_I32) return false;
-  *out = rec.get<int32_t>(s.root_field);
+  if (!value_of_input(n->parent, (int)(-1 - n->dims[d]), &s, 0) || s.rec < 0 || s.rec >= R.count) return false;
+  if (kRecType[s.field] != F_I32) return false;
+  *out = R.get<int32_t>(s.rec, s.field);
   return true;
 }
 
-// The lowered sgemm graph.
-struct Lowered {
+// One lowered tile-grid stage: a sgemm leaf and its merged elementwise leaf.
+struct Stage {
   hpvm::SgemmDesc d;
   int64_t bytesA = 0, bytesB = 0, bytesC = 0;
   int64_t block_x = 0, block_y = 0, grid_x = 0, grid_y = 0;
   int64_t alloc_bx = 0, alloc_by = 0;
   bool has_a_tile = false;
+  hpvm::Epilogue epi;
+  int64_t bytesAux = 0;
+  int rec = 0;  // the record (holding C) whose tier and flags apply
 };
 
-int lower_sgemm(hpvm_node* root, const void* args, size_t args_size, Lowered* L) {
+int64_t need_bytes(int64_t rows, int64_t cols, int64_t ld) {
+  return (rows == 0 || cols == 0) ? 0 : 4 * (ld * (cols - 1) + rows);
+}
+
+int lower_stage(hpvm_node* stage, const Records& R, Stage* S) {
+  hpvm_node* alloc = nullptr;
+  hpvm_node* leaf = nullptr;
+  hpvm_node* ew = nullptr;
+  for (auto* c : stage->children) {
+    if (c->kind == HPVM_NODE_ALLOCATION && !alloc) alloc = c;
+    else if (c->kind == HPVM_NODE_SGEMM_LEAF && !leaf) leaf = c;
+    else if (is_elementwise(c) && !ew) ew = c;
+    else
+      return fail(HPVM_ERR_UNSUPPORTED,
+                  "a tile node must hold one Allocation, one SgemmLeaf and at most one elementwise leaf");
+  }
+  if (!alloc || !leaf) return fail(HPVM_ERR_UNSUPPORTED, "a tile node must hold one Allocation and one SgemmLeaf");
+  if (alloc->ndims != 0) return fail(HPVM_ERR_UNSUPPORTED, "the Allocation node must have one instance");
+  if (leaf->ndims != 2) return fail(HPVM_ERR_UNSUPPORTED, "the SgemmLeaf must be a 2-D grid");
+  for (auto* e : stage->edges) {
+    if (e->stream) return fail(HPVM_ERR_UNSUPPORTED, "streaming edges inside a tile node are not lowered");
+    const bool alloc_edge = e->src == alloc && e->dst == leaf && e->repl == HPVM_ALL_TO_ALL;
+    // MergeDependentNodes precondition: the elementwise leaf is joined to the
+    // sgemm leaf only by one-to-one edges, result -> operand
+    const bool merge_edge = ew && e->src == leaf && e->dst == ew && e->repl == HPVM_ONE_TO_ONE && e->sp == e->dp &&
+                            (e->sp == 0 || e->sp == 1);
+    if (!alloc_edge && !merge_edge)
+      return fail(HPVM_ERR_UNSUPPORTED,
+                  "only all-to-all Allocation -> SgemmLeaf and one-to-one SgemmLeaf -> elementwise edges are lowered");
+  }
+  for (auto& b : stage->in_binds)
+    if (b.stream) return fail(HPVM_ERR_UNSUPPORTED, "streaming bindings inside a tile node are not lowered");
+
+  int64_t vi[kLeafPorts] = {0};
+  double vf[kLeafPorts] = {0};
+  void* vp[kLeafPorts] = {nullptr};
+  int rec = -1;
+  int rc;
+  for (int p = 0; p < kLeafPorts; ++p) {
+    Source s;
+    if (!input_source(leaf, p, &s))
+      return fail(HPVM_ERR_INVALID_GRAPH,
+                  "SgemmLeaf input %d does not resolve to a root field or an Allocation output", p);
+    if (p >= 12 && p <= 15) {
+      if (!s.alloc || s.alloc != alloc)
+        return fail(HPVM_ERR_UNSUPPORTED, "SgemmLeaf input %d (tile memory) must come from the Allocation node", p);
+      if (kAllocOutType[s.alloc_out] != kLeafType[p])
+        return fail(HPVM_ERR_INVALID_GRAPH, "Allocation output %d has the wrong type for SgemmLeaf input %d",
+                    s.alloc_out, p);
+      if ((p == 12 && s.alloc_out != 0) || (p == 13 && s.alloc_out != 1))
+        return fail(HPVM_ERR_UNSUPPORTED, "SgemmLeaf inputs 12, 13 must be Allocation outputs 0, 1");
+      if (p == 14 || p == 15) S->has_a_tile = true;
+      continue;
+    }
+    if ((rc = read_field(R, s, kLeafType[p], "SgemmLeaf", p, &vi[p], &vf[p], &vp[p])) != HPVM_OK) return rc;
+    if (p == 6) rec = s.rec;
+  }
+  S->rec = rec < 0 ? 0 : rec;
+  for (int p = 0; p < kAllocInPorts; ++p) {
+    Source s;
+    if (!input_source(alloc, p, &s)) return fail(HPVM_ERR_INVALID_GRAPH, "Allocation input %d is not fed", p);
+    int64_t v = 0;
+    double f;
+    void* q;
+    if ((rc = read_field(R, s, F_I32, "Allocation", p, &v, &f, &q)) != HPVM_OK) return rc;
+    (p == 0 ? S->alloc_bx : S->alloc_by) = v;
+  }
+  if (!extent_of(leaf, 0, R, &S->block_x) || !extent_of(leaf, 1, R, &S->block_y) ||
+      !extent_of(stage, 0, R, &S->grid_x) || !extent_of(stage, 1, R, &S->grid_y))
+    return fail(HPVM_ERR_INVALID_GRAPH, "a replication extent does not resolve to an i32 root field");
+
+  auto& d = S->d;
+  d.A = static_cast<const float*>(vp[0]);
+  S->bytesA = vi[1];
+  d.lda = vi[2];
+  d.B = static_cast<const float*>(vp[3]);
+  S->bytesB = vi[4];
+  d.ldb = vi[5];
+  d.C = static_cast<float*>(vp[6]);
+  S->bytesC = vi[7];
+  d.ldc = vi[8];
+  d.K = vi[9];
+  d.alpha = (float)vf[10];
+  d.beta = (float)vf[11];
+  d.M = vi[16];
+  d.N = vi[17];
+  d.transA = vi[18] != 0;
+  d.transB = vi[19] != 0;
+
+  if (ew) {
+    // the merged leaf must update exactly the sgemm result
+    int64_t ei[kTanhGradPorts] = {0};
+    double ef;
+    void* ep[kTanhGradPorts] = {nullptr};
+    const int np = ew->kind == HPVM_NODE_TANH_LEAF ? kTanhPorts : kTanhGradPorts;
+    for (int p = 0; p < np; ++p) {
+      Source s;
+      if (!input_source(ew, p, &s))
+        return fail(HPVM_ERR_INVALID_GRAPH, "%s input %d does not resolve", kind_name(ew->kind), p);
+      if ((rc = read_field(R, s, kEwType[p], kind_name(ew->kind), p, &ei[p], &ef, &ep[p])) != HPVM_OK) return rc;
+    }
+    if (ep[0] != vp[6] || ei[2] != d.ldc || ei[3] != d.M || ei[4] != d.N)
+      return fail(HPVM_ERR_UNSUPPORTED, "the elementwise leaf must update the sgemm leaf's own M x N result");
+    S->epi.kind = ew->kind == HPVM_NODE_TANH_LEAF ? 1 : 2;
+    if (S->epi.kind == 2) {
+      S->epi.aux = static_cast<const float*>(ep[5]);
+      S->bytesAux = ei[6];
+      S->epi.ldaux = ei[7];
+      if (S->epi.ldaux < std::max<int64_t>(1, d.M))
+        return fail(HPVM_ERR_SHAPE, "ldh (%lld) < M", (long long)S->epi.ldaux);
+      if (d.M > 0 && d.N > 0 && (!S->epi.aux || S->bytesAux < need_bytes(d.M, d.N, S->epi.ldaux)))
+        return fail(HPVM_ERR_SHAPE, "H is NULL or smaller than M x N with ldh");
+    }
+  }
+
+  // shapes
+  if (d.M < 0 || d.N < 0 || d.K < 0) return fail(HPVM_ERR_SHAPE, "negative M, N or K");
+  if (S->block_x <= 0 || S->block_y <= 0 || S->grid_x <= 0 || S->grid_y <= 0)
+    return fail(HPVM_ERR_SHAPE, "replication extents must be positive");
+  if (S->grid_x * S->block_x < d.M || S->grid_y * S->block_y < d.N)
+    return fail(HPVM_ERR_SHAPE, "grid x block (%lld x %lld) does not cover M x N (%lld x %lld)",
+                (long long)(S->grid_x * S->block_x), (long long)(S->grid_y * S->block_y), (long long)d.M,
+                (long long)d.N);
+  const int64_t ar = d.transA ? d.K : d.M, ac = d.transA ? d.M : d.K;
+  const int64_t br = d.transB ? d.N : d.K, bc = d.transB ? d.K : d.N;
+  if (d.lda < std::max<int64_t>(1, ar))
+    return fail(HPVM_ERR_SHAPE, "lda (%lld) < rows of A (%lld)", (long long)d.lda, (long long)ar);
+  if (d.ldb < std::max<int64_t>(1, br))
+    return fail(HPVM_ERR_SHAPE, "ldb (%lld) < rows of B (%lld)", (long long)d.ldb, (long long)br);
+  if (d.ldc < std::max<int64_t>(1, d.M))
+    return fail(HPVM_ERR_SHAPE, "ldc (%lld) < M (%lld)", (long long)d.ldc, (long long)d.M);
+  const bool work = d.M > 0 && d.N > 0;
+  if (work && d.K > 0) {
+    if (!d.A || !d.B) return fail(HPVM_ERR_INVALID_ARG, "A or B is NULL");
+    if (S->bytesA < need_bytes(ar, ac, d.lda))
+      return fail(HPVM_ERR_SHAPE, "bytesA (%lld) < %lld needed", (long long)S->bytesA, (long long)need_bytes(ar, ac, d.lda));
+    if (S->bytesB < need_bytes(br, bc, d.ldb))
+      return fail(HPVM_ERR_SHAPE, "bytesB (%lld) < %lld needed", (long long)S->bytesB, (long long)need_bytes(br, bc, d.ldb));
+  }
+  if (work) {
+    if (!d.C) return fail(HPVM_ERR_INVALID_ARG, "C is NULL");
+    if (S->bytesC < need_bytes(d.M, d.N, d.ldc))
+      return fail(HPVM_ERR_SHAPE, "bytesC (%lld) < %lld needed", (long long)S->bytesC, (long long)need_bytes(d.M, d.N, d.ldc));
+  }
+  return HPVM_OK;
+}
+
+struct Plan {
+  std::vector<Stage> stages;
+  Records R{nullptr, 0};
+};
+
+int lower_graph(hpvm_node* root, const void* args, size_t args_size, Plan* P) {
   if (!root || root->parent != nullptr)
     return fail(HPVM_ERR_INVALID_ARG, "launch needs the root node of a graph");
   if (root->kind != HPVM_NODE_INTERNAL || root->ndims != 0)
     return fail(HPVM_ERR_INVALID_GRAPH, "the root must be a single-instance internal node");
-  if (!args || args_size < HPVM_SGEMM_ROOT_ARGS_BYTES)
-    return fail(HPVM_ERR_INVALID_ARG, "argument record too small (%zu < %d bytes)", args_size,
-                HPVM_SGEMM_ROOT_ARGS_BYTES);
+  if (!args || args_size < kRecBytes)
+    return fail(HPVM_ERR_INVALID_ARG, "argument record too small (%zu < %zu bytes)", args_size, kRecBytes);
   int rc = validate_node(root);
   if (rc != HPVM_OK) return rc;
-  // root -> one internal 2-D grid -> {Allocation (1 instance), SgemmLeaf (2-D)}
-  if (root->children.size() != 1 || root->children[0]->kind != HPVM_NODE_INTERNAL ||
-      root->children[0]->ndims != 2)
-    return fail(HPVM_ERR_UNSUPPORTED, "root must hold exactly one 2-D internal node (the tile grid)");
-  hpvm_node* inner = root->children[0];
-  hpvm_node* alloc = nullptr;
-  hpvm_node* leaf = nullptr;
-  for (auto* c : inner->children) {
-    if (c->kind == HPVM_NODE_ALLOCATION && !alloc) alloc = c;
-    else if (c->kind == HPVM_NODE_SGEMM_LEAF && !leaf) leaf = c;
-    else return fail(HPVM_ERR_UNSUPPORTED, "the tile node must hold one Allocation and one SgemmLeaf");
-  }
-  if (!alloc || !leaf) return fail(HPVM_ERR_UNSUPPORTED, "the tile node must hold one Allocation and one SgemmLeaf");
-  if (alloc->ndims != 0) return fail(HPVM_ERR_UNSUPPORTED, "the Allocation node must have one instance");
-  if (leaf->ndims != 2) return fail(HPVM_ERR_UNSUPPORTED, "the SgemmLeaf must be a 2-D grid");
-  for (auto* e : inner->edges) {
-    if (e->stream) return fail(HPVM_ERR_UNSUPPORTED, "streaming edges are not lowered");
-    if (!(e->src == alloc && e->dst == leaf && e->repl == HPVM_ALL_TO_ALL))
-      return fail(HPVM_ERR_UNSUPPORTED, "only all-to-all Allocation -> SgemmLeaf edges are lowered");
-  }
-  for (auto& b : root->in_binds)
-    if (b.stream) return fail(HPVM_ERR_UNSUPPORTED, "streaming bindings are not lowered");
-  for (auto& b : inner->in_binds)
-    if (b.stream) return fail(HPVM_ERR_UNSUPPORTED, "streaming bindings are not lowered");
-
-  RootRecord rec{static_cast<const uint8_t*>(args)};
-  // resolve the leaf's inputs
-  int64_t vals_i[kLeafPorts] = {0};
-  double vals_f[kLeafPorts] = {0};
-  void* vals_p[kLeafPorts] = {nullptr};
-  for (int p = 0; p < kLeafPorts; ++p) {
-    Source s;
-    if (!input_source(leaf, p, &s))
-      return fail(HPVM_ERR_INVALID_GRAPH, "SgemmLeaf input %d does not resolve to a root field or an Allocation output", p);
-    if (p >= 12 && p <= 15) {
-      if (!s.alloc) return fail(HPVM_ERR_UNSUPPORTED, "SgemmLeaf input %d (tile memory) must come from the Allocation node", p);
-      if (kAllocOutType[s.alloc_out] != kLeafType[p])
-        return fail(HPVM_ERR_INVALID_GRAPH, "Allocation output %d has the wrong type for SgemmLeaf input %d", s.alloc_out, p);
-      if ((p == 12 && s.alloc_out != 0) || (p == 13 && s.alloc_out != 1))
-        return fail(HPVM_ERR_UNSUPPORTED, "SgemmLeaf inputs 12, 13 must be Allocation outputs 0, 1");
-      if (p == 14 || p == 15) L->has_a_tile = true;
-      continue;
-    }
-    if (s.root_field < 0)
-      return fail(HPVM_ERR_UNSUPPORTED, "SgemmLeaf input %d must come from the root record", p);
-    if (kRootType[s.root_field] != kLeafType[p])
-      return fail(HPVM_ERR_INVALID_GRAPH, "SgemmLeaf input %d is bound to root field %s of another type", p,
-                  kRootName[s.root_field]);
-    switch (kLeafType[p]) {
-      case F_PTR: vals_p[p] = rec.get<void*>(s.root_field); break;
-      case F_I64: vals_i[p] = rec.get<int64_t>(s.root_field); break;
-      case F_I32: vals_i[p] = rec.get<int32_t>(s.root_field); break;
-      case F_F32: vals_f[p] = rec.get<float>(s.root_field); break;
-    }
-    (void)kLeafMeaning;
-  }
-  // the Allocation node's inputs (block_x, block_y)
-  for (int p = 0; p < kAllocInPorts; ++p) {
-    Source s;
-    if (!input_source(alloc, p, &s) || s.root_field < 0 || kRootType[s.root_field] != F_I32)
-      return fail(HPVM_ERR_INVALID_GRAPH, "Allocation input %d must be an i32 root field", p);
-    (p == 0 ? L->alloc_bx : L->alloc_by) = rec.get<int32_t>(s.root_field);
-  }
-  if (!extent_of(leaf, 0, rec, &L->block_x) || !extent_of(leaf, 1, rec, &L->block_y) ||
-      !extent_of(inner, 0, rec, &L->grid_x) || !extent_of(inner, 1, rec, &L->grid_y))
-    return fail(HPVM_ERR_INVALID_GRAPH, "a replication extent does not resolve to an i32 root field");
-
-  auto& d = L->d;
-  d.A = static_cast<const float*>(vals_p[0]);
-  L->bytesA = vals_i[1];
-  d.lda = vals_i[2];
-  d.B = static_cast<const float*>(vals_p[3]);
-  L->bytesB = vals_i[4];
-  d.ldb = vals_i[5];
-  d.C = static_cast<float*>(vals_p[6]);
-  L->bytesC = vals_i[7];
-  d.ldc = vals_i[8];
-  d.K = vals_i[9];
-  d.alpha = (float)vals_f[10];
-  d.beta = (float)vals_f[11];
-  d.M = vals_i[16];
-  d.N = vals_i[17];
-  d.transA = vals_i[18] != 0;
-  d.transB = vals_i[19] != 0;
-
-  // shapes
-  if (d.M < 0 || d.N < 0 || d.K < 0) return fail(HPVM_ERR_SHAPE, "negative M, N or K");
-  if (L->block_x <= 0 || L->block_y <= 0 || L->grid_x <= 0 || L->grid_y <= 0)
-    return fail(HPVM_ERR_SHAPE, "replication extents must be positive");
-  if (L->grid_x * L->block_x < d.M || L->grid_y * L->block_y < d.N)
-    return fail(HPVM_ERR_SHAPE, "grid x block (%lld x %lld) does not cover M x N (%lld x %lld)",
-                (long long)(L->grid_x * L->block_x), (long long)(L->grid_y * L->block_y), (long long)d.M,
-                (long long)d.N);
-  const int64_t ar = d.transA ? d.K : d.M, ac = d.transA ? d.M : d.K;
-  const int64_t br = d.transB ? d.N : d.K, bc = d.transB ? d.K : d.N;
-  if (d.lda < std::max<int64_t>(1, ar)) return fail(HPVM_ERR_SHAPE, "lda (%lld) < rows of A (%lld)", (long long)d.lda, (long long)ar);
-  if (d.ldb < std::max<int64_t>(1, br)) return fail(HPVM_ERR_SHAPE, "ldb (%lld) < rows of B (%lld)", (long long)d.ldb, (long long)br);
-  if (d.ldc < std::max<int64_t>(1, d.M)) return fail(HPVM_ERR_SHAPE, "ldc (%lld) < M (%lld)", (long long)d.ldc, (long long)d.M);
-  auto need = [](int64_t rows, int64_t cols, int64_t ld) -> int64_t {
-    return (rows == 0 || cols == 0) ? 0 : 4 * (ld * (cols - 1) + rows);
-  };
-  const bool work = d.M > 0 && d.N > 0;
-  if (work && d.K > 0) {
-    if (!d.A || !d.B) return fail(HPVM_ERR_INVALID_ARG, "A or B is NULL");
-    if (L->bytesA < need(ar, ac, d.lda)) return fail(HPVM_ERR_SHAPE, "bytesA (%lld) < %lld needed", (long long)L->bytesA, (long long)need(ar, ac, d.lda));
-    if (L->bytesB < need(br, bc, d.ldb)) return fail(HPVM_ERR_SHAPE, "bytesB (%lld) < %lld needed", (long long)L->bytesB, (long long)need(br, bc, d.ldb));
-  }
-  if (work) {
-    if (!d.C) return fail(HPVM_ERR_INVALID_ARG, "C is NULL");
-    if (L->bytesC < need(d.M, d.N, d.ldc)) return fail(HPVM_ERR_SHAPE, "bytesC (%lld) < %lld needed", (long long)L->bytesC, (long long)need(d.M, d.N, d.ldc));
+  P->R = Records{static_cast<const uint8_t*>(args), (int)std::min<size_t>(args_size / kRecBytes, kMaxRecords)};
+  std::vector<hpvm_node*> order;
+  if ((rc = topo_children(root, &order)) != HPVM_OK) return rc;
+  if (order.empty()) return fail(HPVM_ERR_UNSUPPORTED, "the root holds no tile node");
+  for (auto* st : order)
+    if (st->kind != HPVM_NODE_INTERNAL || st->ndims != 2)
+      return fail(HPVM_ERR_UNSUPPORTED, "every child of the root must be a 2-D internal node (a tile grid)");
+  for (auto* e : root->edges)
+    if (e->repl != HPVM_ALL_TO_ALL)
+      return fail(HPVM_ERR_UNSUPPORTED,
+                  "edges between tile grids must be all-to-all (a whole result feeds the next stage)");
+  P->stages.clear();
+  for (auto* st : order) {
+    Stage S;
+    if ((rc = lower_stage(st, P->R, &S)) != HPVM_OK) return rc;
+    P->stages.push_back(S);
   }
   return HPVM_OK;
+}
+
+int32_t record_i32(const Plan& P, int rec, size_t off) {
+  int32_t v;
+  memcpy(&v, P.R.base + rec * kRecBytes + off, 4);
+  return v;
+}
+
+int check_stage_tier(const Stage& S, int tier) {
+  if (tier < HPVM_TIER_FP32_DFG || tier > HPVM_TIER_FP8) return fail(HPVM_ERR_INVALID_ARG, "unknown tier %d", tier);
+  if (tier == HPVM_TIER_FP32_DFG) {
+    if (S.block_x != S.block_y)
+      return fail(HPVM_ERR_UNSUPPORTED, "the FP32_DFG lowering needs a square leaf grid (got %lld x %lld)",
+                  (long long)S.block_x, (long long)S.block_y);
+    if (S.block_x * S.block_y > 1024)
+      return fail(HPVM_ERR_UNSUPPORTED, "the FP32_DFG lowering maps leaf instances to threads: at most 1024");
+    if (!S.has_a_tile)
+      return fail(HPVM_ERR_UNSUPPORTED, "the FP32_DFG lowering needs the Allocation's A tile (ports 14, 15)");
+    if (S.alloc_bx * S.alloc_by < S.block_x * S.block_y)
+      return fail(HPVM_ERR_SHAPE, "the Allocation tile (%lld x %lld) is smaller than the leaf grid",
+                  (long long)S.alloc_bx, (long long)S.alloc_by);
+  }
+  return HPVM_OK;
+}
+
+size_t workspace_need(const Stage& S, int tier) {
+  if (tier == HPVM_TIER_BF16X3 || tier == HPVM_TIER_BF16 || tier == HPVM_TIER_FP8)
+    return hpvm::tc_workspace_bytes(S.d, tier);
+  return 0;
+}
+
+size_t plan_workspace(const Plan& P) {
+  size_t need = 0;
+  for (auto& S : P.stages) need = std::max(need, workspace_need(S, record_i32(P, S.rec, kTierOffset)));
+  return need;
 }
 
 TrackEntry* find_tracked(hpvm_ctx* ctx, const void* p, int64_t* offset) {
@@ -498,8 +674,8 @@ int check_device_pointer(const void* p, const char* name) {
 
 // Map a record pointer to the device: tracked host regions use their device
 // copy (copied in first when `read` and the device copy is stale).
-int map_pointer(hpvm_ctx* ctx, const void* p, bool read, cudaStream_t s, const char* name,
-                void** out, TrackEntry** entry, int64_t* h2d) {
+int map_pointer(hpvm_ctx* ctx, const void* p, bool read, cudaStream_t s, const char* name, void** out,
+                TrackEntry** entry, int64_t* h2d) {
   *entry = nullptr;
   *out = const_cast<void*>(p);
   if (!p) return HPVM_OK;
@@ -526,39 +702,161 @@ int map_pointer(hpvm_ctx* ctx, const void* p, bool read, cudaStream_t s, const c
   return HPVM_OK;
 }
 
-int ensure_workspace(hpvm_ctx* ctx, size_t need, void** ws) {
-  if (need == 0) {
-    *ws = ctx->ws;
-    return HPVM_OK;
+int grow_buffer(void** buf, size_t* have, size_t need, cudaStream_t sync_on) {
+  if (need == 0 || (*buf && *have >= need)) return HPVM_OK;
+  if (*buf) {
+    if (sync_on) cudaStreamSynchronize(sync_on);
+    else cudaDeviceSynchronize();
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
   }
-  if (ctx->ws && ctx->ws_bytes >= need) {
+  cudaError_t e = cudaMalloc(buf, need);
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    return fail(HPVM_ERR_OUT_OF_MEMORY, "workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+  }
+  *have = need;
+  return HPVM_OK;
+}
+
+int ensure_workspace(hpvm_ctx* ctx, size_t need, void** ws, size_t* ws_bytes) {
+  if (need == 0 || (ctx->ws && ctx->ws_bytes >= need)) {
     *ws = ctx->ws;
+    *ws_bytes = ctx->ws_bytes;
     return HPVM_OK;
   }
   if (ctx->ws && !ctx->ws_owned)
     return fail(HPVM_ERR_SHAPE, "the workspace set with hpvm_set_workspace has %zu bytes, this launch needs %zu",
                 ctx->ws_bytes, need);
-  if (ctx->ws) {
-    cudaDeviceSynchronize();
-    cudaFree(ctx->ws);
-    ctx->ws = nullptr;
-    ctx->ws_bytes = 0;
-  }
-  cudaError_t e = cudaMalloc(&ctx->ws, need);
-  if (e != cudaSuccess) {
-    ctx->ws = nullptr;
-    return fail(HPVM_ERR_OUT_OF_MEMORY, "workspace of %zu bytes: %s", need, cudaGetErrorString(e));
-  }
-  ctx->ws_bytes = need;
+  int rc = grow_buffer(&ctx->ws, &ctx->ws_bytes, need, nullptr);
+  if (rc != HPVM_OK) return rc;
   ctx->ws_owned = true;
   *ws = ctx->ws;
+  *ws_bytes = ctx->ws_bytes;
   return HPVM_OK;
 }
 
-size_t workspace_need(const Lowered& L, int tier) {
-  if (tier == HPVM_TIER_BF16X3 || tier == HPVM_TIER_BF16 || tier == HPVM_TIER_FP8)
-    return hpvm::tc_workspace_bytes(L.d, tier);
-  return 0;
+// Enqueue every stage of a lowered graph on stream s.
+int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t ws_bytes, hpvm_launch_info* inf) {
+  memset(inf, 0, sizeof *inf);
+  int64_t h2d = 0;
+  int rc;
+  bool first = true;
+  for (const Stage& S0 : P.stages) {
+    const int tier = record_i32(P, S0.rec, kTierOffset);
+    const int flags = record_i32(P, S0.rec, kFlagsOffset);
+    if ((rc = check_stage_tier(S0, tier)) != HPVM_OK) return rc;
+    Stage S = S0;
+    const bool work = S.d.M > 0 && S.d.N > 0;
+    void *A = nullptr, *B = nullptr, *C = nullptr, *H = nullptr;
+    TrackEntry *tA = nullptr, *tB = nullptr, *tC = nullptr, *tH = nullptr;
+    if (work && S.d.K > 0) {
+      if ((rc = map_pointer(ctx, S.d.A, true, s, "A", &A, &tA, &h2d)) != HPVM_OK) return rc;
+      if ((rc = map_pointer(ctx, S.d.B, true, s, "B", &B, &tB, &h2d)) != HPVM_OK) return rc;
+    }
+    if (work) {
+      if ((rc = map_pointer(ctx, S.d.C, S.d.beta != 0.f, s, "C", &C, &tC, &h2d)) != HPVM_OK) return rc;
+      if (S.epi.kind == 2 && (rc = map_pointer(ctx, S.epi.aux, true, s, "H", &H, &tH, &h2d)) != HPVM_OK) return rc;
+    }
+    S.d.A = static_cast<const float*>(A);
+    S.d.B = static_cast<const float*>(B);
+    S.d.C = static_cast<float*>(C);
+    if (S.epi.kind == 2) S.epi.aux = static_cast<const float*>(H);
+    hpvm::KernelReport rep;
+    if (work) {
+      std::string err;
+      hpvm::LaunchHooks hooks;
+      if (ctx->timing) {
+        if (cudaEventCreate(&hooks.main_begin) != cudaSuccess || cudaEventCreate(&hooks.main_end) != cudaSuccess)
+          return fail(HPVM_ERR_CUDA, "cannot create timing events");
+        ctx->timed.emplace_back(hooks.main_begin, hooks.main_end);
+      }
+      // MergeDependentNodes: the tensor-core leaves take the elementwise
+      // leaf into their epilogue; the FP32 leaves (or HPVM_LAUNCH_NO_FUSION)
+      // run it as its own kernel after the sgemm leaf.
+      const bool tensor = tier >= HPVM_TIER_BF16X3;
+      const bool fuse = tensor && !(flags & HPVM_LAUNCH_NO_FUSION);
+      hpvm::Epilogue none;
+      cudaError_t e;
+      switch (tier) {
+        case HPVM_TIER_FP32_DFG:
+          e = hpvm::launch_fp32_dfg(S.d, (int)S.block_x, (int)S.grid_x, (int)S.grid_y,
+                                    (size_t)(S.block_x * S.block_y * 4), s, &rep, &hooks);
+          break;
+        case HPVM_TIER_FP32:
+          e = hpvm::launch_fp32_tiled(S.d, s, &rep, &hooks);
+          break;
+        default:
+          e = hpvm::launch_tc(S.d, tier, ws, ws_bytes, ctx->status, s, &rep, &err, &hooks, fuse ? S.epi : none);
+          if (e == cudaErrorInvalidValue && !err.empty()) return fail(HPVM_ERR_SHAPE, "%s", err.c_str());
+          break;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+      if (S.epi.kind && !fuse) {
+        e = hpvm::launch_elementwise(S.d, S.epi, s);
+        if (e != cudaSuccess) return cuda_fail(e, "elementwise leaf launch");
+        rep.kernels += 1;
+      }
+    }
+    if (tC) {
+      tC->dev_valid = true;
+      tC->host_valid = false;
+    }
+    if (first) {  // the first stage describes the launch
+      inf->tier = tier;
+      inf->grid_x = rep.grid_x;
+      inf->grid_y = rep.grid_y;
+      inf->grid_z = rep.grid_z;
+      inf->block_threads = rep.block_threads;
+      inf->tile_m = rep.tile_m;
+      inf->tile_n = rep.tile_n;
+      inf->tile_k = rep.tile_k;
+      inf->smem_bytes = rep.smem_bytes;
+      inf->literal = rep.literal;
+      first = false;
+    }
+    inf->kernels += rep.kernels;
+    inf->workspace_bytes = std::max<int64_t>(inf->workspace_bytes, rep.workspace_bytes);
+  }
+  inf->h2d_bytes = h2d;
+  return HPVM_OK;
+}
+
+int wait_event(cudaEvent_t ev, int64_t timeout_ms) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return HPVM_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "waiting for the graph");
+    if (timeout_ms >= 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+      return fail(HPVM_ERR_TIMEOUT, "graph not finished after %lld ms", (long long)timeout_ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+int check_status(hpvm_ctx* ctx) {
+  if (!ctx->status.host) return HPVM_OK;
+  int st = *const_cast<volatile int*>(ctx->status.host);
+  if (st) {
+    *const_cast<volatile int*>(ctx->status.host) = 0;
+    return fail(HPVM_ERR_DEVICE_FAULT, "a kernel gave up a bounded wait (status bits 0x%x)", st);
+  }
+  return HPVM_OK;
+}
+
+void free_graph(hpvm_graph* g) {
+  if (g->done) cudaEventDestroy(g->done);
+  for (auto& it : g->items)
+    if (it.done) cudaEventDestroy(it.done);
+  for (size_t i = 0; i < g->slots.size(); ++i) {
+    if (g->slots[i]) {
+      cudaStreamSynchronize(g->slots[i]);
+      cudaStreamDestroy(g->slots[i]);
+    }
+    if (g->slot_ws[i]) cudaFree(g->slot_ws[i]);
+  }
+  delete g;
 }
 
 }  // namespace
@@ -568,7 +866,7 @@ size_t workspace_need(const Lowered& L, int tier) {
 extern "C" {
 
 const char* hpvm_last_error(void) { return g_last_error.c_str(); }
-int hpvm_version(void) { return 100; }
+int hpvm_version(void) { return 200; }
 
 int hpvm_init(int device, hpvm_ctx** out) {
   if (!out) return fail(HPVM_ERR_INVALID_ARG, "out is NULL");
@@ -606,10 +904,7 @@ int hpvm_cleanup(hpvm_ctx* ctx) {
   if (ctx->device >= 0) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    for (auto* g : ctx->graphs) {
-      if (g->done) cudaEventDestroy(g->done);
-      delete g;
-    }
+    for (auto* g : ctx->graphs) free_graph(g);
     for (auto& t : ctx->tracked)
       if (t.dev) cudaFree(t.dev);
     if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
@@ -627,7 +922,7 @@ int hpvm_create_node(hpvm_ctx* ctx, hpvm_node* parent, int kind, int ndims, cons
                      hpvm_node** out) {
   if (!ctx || !out) return fail(HPVM_ERR_INVALID_ARG, "ctx or out is NULL");
   *out = nullptr;
-  if (kind != HPVM_NODE_INTERNAL && kind != HPVM_NODE_ALLOCATION && kind != HPVM_NODE_SGEMM_LEAF)
+  if (kind < HPVM_NODE_INTERNAL || kind > HPVM_NODE_TANH_GRAD_LEAF)
     return fail(HPVM_ERR_INVALID_ARG, "unknown node kind %d", kind);
   if (ndims < 0 || ndims > 3) return fail(HPVM_ERR_INVALID_ARG, "ndims must be 0..3, got %d", ndims);
   if (ndims > 0 && !dims) return fail(HPVM_ERR_INVALID_ARG, "dims is NULL");
@@ -678,8 +973,7 @@ int hpvm_create_edge(hpvm_node* src, hpvm_node* dst, int repl, int sp, int dp, i
     for (int d = 0; same && d < src->ndims; ++d) same = src->dims[d] == dst->dims[d];
     if (!same) return fail(HPVM_ERR_INVALID_GRAPH, "a one-to-one edge needs identical grids");
   }
-  if (stream) return fail(HPVM_ERR_UNSUPPORTED, "streaming edges are not supported by this runtime");
-  auto e = std::make_unique<hpvm_edge>(hpvm_edge{src, dst, repl, sp, dp, stream});
+  auto e = std::make_unique<hpvm_edge>(hpvm_edge{src, dst, repl, sp, dp, stream != 0});
   hpvm_edge* raw = e.get();
   src->ctx->edges.push_back(std::move(e));
   src->parent->edges.push_back(raw);
@@ -694,8 +988,7 @@ int hpvm_bind_input(hpvm_node* child, int ip, int ic, int stream) {
     return fail(HPVM_ERR_INVALID_ARG, "parent input %d is out of range", ip);
   if (ic < 0 || ic >= in_arity(child))
     return fail(HPVM_ERR_INVALID_ARG, "input %d of %s is out of range", ic, node_label(child).c_str());
-  if (stream) return fail(HPVM_ERR_UNSUPPORTED, "streaming bindings are not supported by this runtime");
-  child->parent->in_binds.push_back(Bind{child, ip, ic, stream});
+  child->parent->in_binds.push_back(Bind{child, ip, ic, stream != 0});
   return ok();
 }
 
@@ -706,8 +999,9 @@ int hpvm_bind_output(hpvm_node* child, int oc, int op, int stream) {
     return fail(HPVM_ERR_INVALID_ARG, "output %d of %s is out of range", oc, node_label(child).c_str());
   if (op < 0 || op >= out_arity(child->parent))
     return fail(HPVM_ERR_INVALID_ARG, "parent output %d is out of range", op);
-  if (stream) return fail(HPVM_ERR_UNSUPPORTED, "streaming bindings are not supported by this runtime");
-  child->parent->out_binds.push_back(Bind{child, oc, op, stream});
+  for (auto& b : child->parent->out_binds)
+    if (b.outer == op) return fail(HPVM_ERR_INVALID_GRAPH, "parent output %d is already bound", op);
+  child->parent->out_binds.push_back(Bind{child, op, oc, stream != 0});
   return ok();
 }
 
@@ -762,12 +1056,10 @@ int hpvm_plan_sgemm(int tier, int64_t M, int64_t N, int64_t K, int32_t* block_x,
 
 int hpvm_workspace_size(hpvm_ctx* ctx, hpvm_node* root, const void* args, size_t args_size, size_t* out) {
   if (!ctx || !out) return fail(HPVM_ERR_INVALID_ARG, "ctx or out is NULL");
-  Lowered L;
-  int rc = lower_sgemm(root, args, args_size, &L);
+  Plan P;
+  int rc = lower_graph(root, args, args_size, &P);
   if (rc != HPVM_OK) return rc;
-  int32_t tier;
-  memcpy(&tier, static_cast<const uint8_t*>(args) + 104, 4);
-  *out = workspace_need(L, tier);
+  *out = plan_workspace(P);
   return ok();
 }
 
@@ -791,110 +1083,104 @@ int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args, size_t args_si
   if (out) *out = nullptr;
   if (!ctx || !out) return fail(HPVM_ERR_INVALID_ARG, "ctx or out is NULL");
   if (root && root->ctx != ctx) return fail(HPVM_ERR_INVALID_ARG, "root belongs to another context");
-  if (stream_graph) return fail(HPVM_ERR_UNSUPPORTED, "streaming graphs are not supported by this runtime");
-  Lowered L;
-  int rc = lower_sgemm(root, args, args_size, &L);
+  Plan P;
+  int rc = lower_graph(root, args, args_size, &P);
   if (rc != HPVM_OK) return rc;
-  int32_t tier, flags;
-  memcpy(&tier, static_cast<const uint8_t*>(args) + 104, 4);
-  memcpy(&flags, static_cast<const uint8_t*>(args) + 108, 4);
-  if (tier < HPVM_TIER_FP32_DFG || tier > HPVM_TIER_FP8) return fail(HPVM_ERR_INVALID_ARG, "unknown tier %d", tier);
-  if (tier == HPVM_TIER_FP32_DFG) {
-    if (L.block_x != L.block_y)
-      return fail(HPVM_ERR_UNSUPPORTED, "the FP32_DFG lowering needs a square leaf grid (got %lld x %lld)",
-                  (long long)L.block_x, (long long)L.block_y);
-    if (L.block_x * L.block_y > 1024)
-      return fail(HPVM_ERR_UNSUPPORTED, "the FP32_DFG lowering maps leaf instances to threads: at most 1024");
-    if (!L.has_a_tile)
-      return fail(HPVM_ERR_UNSUPPORTED, "the FP32_DFG lowering needs the Allocation's A tile (ports 14, 15)");
-    if (L.alloc_bx * L.alloc_by < L.block_x * L.block_y)
-      return fail(HPVM_ERR_SHAPE, "the Allocation tile (%lld x %lld) is smaller than the leaf grid",
-                  (long long)L.alloc_bx, (long long)L.alloc_by);
-  }
+  for (auto& S : P.stages)
+    if ((rc = check_stage_tier(S, record_i32(P, S.rec, kTierOffset))) != HPVM_OK) return rc;
   if (ctx->device < 0) return fail(HPVM_ERR_NO_DEVICE, "host-only context cannot launch");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-
-  // memory tracker: A and B are read; C is read unless beta == 0 and written
-  int64_t h2d = 0;
-  const bool work = L.d.M > 0 && L.d.N > 0;
-  const bool need_ab = work && L.d.K > 0;
-  void *A = nullptr, *B = nullptr, *C = nullptr;
-  TrackEntry *tA = nullptr, *tB = nullptr, *tC = nullptr;
-  if (need_ab) {
-    if ((rc = map_pointer(ctx, L.d.A, true, s, "A", &A, &tA, &h2d)) != HPVM_OK) return rc;
-    if ((rc = map_pointer(ctx, L.d.B, true, s, "B", &B, &tB, &h2d)) != HPVM_OK) return rc;
-  }
-  if (work) {
-    if ((rc = map_pointer(ctx, L.d.C, L.d.beta != 0.f, s, "C", &C, &tC, &h2d)) != HPVM_OK) return rc;
-  }
-  hpvm::SgemmDesc d = L.d;
-  d.A = static_cast<const float*>(A);
-  d.B = static_cast<const float*>(B);
-  d.C = static_cast<float*>(C);
-
-  hpvm::KernelReport rep;
-  if (work) {
-    void* ws = nullptr;
-    size_t need = workspace_need(L, tier);
-    if ((rc = ensure_workspace(ctx, need, &ws)) != HPVM_OK) return rc;
-    std::string err;
-    hpvm::LaunchHooks hooks;
-    if (ctx->timing) {
-      if (cudaEventCreate(&hooks.main_begin) != cudaSuccess || cudaEventCreate(&hooks.main_end) != cudaSuccess)
-        return fail(HPVM_ERR_CUDA, "cannot create timing events");
-      ctx->timed.emplace_back(hooks.main_begin, hooks.main_end);
-    }
-    switch (tier) {
-      case HPVM_TIER_FP32_DFG:
-        e = hpvm::launch_fp32_dfg(d, (int)L.block_x, (int)L.grid_x, (int)L.grid_y,
-                                  (size_t)(L.block_x * L.block_y * 4), s, &rep, &hooks);
-        break;
-      case HPVM_TIER_FP32:
-        e = hpvm::launch_fp32_tiled(d, s, &rep, &hooks);
-        break;
-      default:
-        e = hpvm::launch_tc(d, tier, ws, ctx->ws_bytes, ctx->status, s, &rep, &err, &hooks);
-        if (e == cudaErrorInvalidValue && !err.empty()) return fail(HPVM_ERR_SHAPE, "%s", err.c_str());
-        break;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-  }
-  if (tC) {
-    tC->dev_valid = true;
-    tC->host_valid = false;
-  }
   auto g = std::make_unique<hpvm_graph>();
   g->ctx = ctx;
   g->stream = s;
+  g->root = root;
+  if (stream_graph) {
+    // A streaming graph stays alive: nothing runs now; every hpvm_push runs
+    // one item on the next stream of the ring, after the work enqueued on
+    // the caller's stream before this launch.
+    g->streaming = true;
+    cudaEvent_t start;
+    if ((e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+    cudaEventRecord(start, s);
+    g->slots.assign(kStreamSlots, nullptr);
+    g->slot_ws.assign(kStreamSlots, nullptr);
+    g->slot_ws_bytes.assign(kStreamSlots, 0);
+    for (int i = 0; i < kStreamSlots; ++i) {
+      if ((e = cudaStreamCreateWithFlags(&g->slots[i], cudaStreamNonBlocking)) != cudaSuccess) {
+        cudaEventDestroy(start);
+        free_graph(g.release());
+        return cuda_fail(e, "cudaStreamCreate");
+      }
+      cudaStreamWaitEvent(g->slots[i], start, 0);
+    }
+    cudaEventDestroy(start);
+    *out = g.get();
+    ctx->graphs.insert(g.release());
+    return ok();
+  }
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  if ((rc = ensure_workspace(ctx, plan_workspace(P), &ws, &ws_bytes)) != HPVM_OK) return rc;
+  if ((rc = execute_plan(ctx, P, s, ws, ws_bytes, &g->info)) != HPVM_OK) return rc;
+  const int flags = record_i32(P, P.stages.front().rec, kFlagsOffset);
   if (!(flags & HPVM_LAUNCH_NO_EVENT)) {
     e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     e = cudaEventRecord(g->done, s);
     if (e != cudaSuccess) {
       cudaEventDestroy(g->done);
+      g->done = nullptr;
       return cuda_fail(e, "cudaEventRecord");
     }
   }
-  auto& inf = g->info;
-  inf.tier = tier;
-  inf.kernels = rep.kernels;
-  inf.grid_x = rep.grid_x;
-  inf.grid_y = rep.grid_y;
-  inf.grid_z = rep.grid_z;
-  inf.block_threads = rep.block_threads;
-  inf.tile_m = rep.tile_m;
-  inf.tile_n = rep.tile_n;
-  inf.tile_k = rep.tile_k;
-  inf.smem_bytes = rep.smem_bytes;
-  inf.literal = rep.literal;
-  inf.workspace_bytes = rep.workspace_bytes;
-  inf.h2d_bytes = h2d;
-  inf.d2h_bytes = 0;
   *out = g.get();
   ctx->graphs.insert(g.release());
   return ok();
+}
+
+int hpvm_push(hpvm_graph* g, const void* args, size_t args_size) {
+  if (!g || !args) return fail(HPVM_ERR_INVALID_ARG, "graph or args is NULL");
+  hpvm_ctx* ctx = g->ctx;
+  if (!ctx->graphs.count(g)) return fail(HPVM_ERR_INVALID_ARG, "unknown or finished graph handle");
+  if (!g->streaming) return fail(HPVM_ERR_INVALID_ARG, "push needs a graph launched as a streaming graph");
+  Plan P;
+  int rc = lower_graph(g->root, args, args_size, &P);
+  if (rc != HPVM_OK) return rc;
+  cudaSetDevice(ctx->device);
+  const int slot = (int)(g->pushed % g->slots.size());
+  cudaStream_t s = g->slots[slot];
+  if ((rc = grow_buffer(&g->slot_ws[slot], &g->slot_ws_bytes[slot], plan_workspace(P), s)) != HPVM_OK) return rc;
+  hpvm_launch_info inf;
+  if ((rc = execute_plan(ctx, P, s, g->slot_ws[slot], g->slot_ws_bytes[slot], &inf)) != HPVM_OK) return rc;
+  StreamItem it;
+  it.record.assign(static_cast<const uint8_t*>(args), static_cast<const uint8_t*>(args) + args_size);
+  cudaError_t e = cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  cudaEventRecord(it.done, s);
+  g->items.push_back(std::move(it));
+  g->info = inf;
+  g->pushed++;
+  return ok();
+}
+
+int hpvm_pop(hpvm_graph* g, void* out, size_t out_size, int64_t timeout_ms) {
+  if (!g) return fail(HPVM_ERR_INVALID_ARG, "graph is NULL");
+  hpvm_ctx* ctx = g->ctx;
+  if (!ctx->graphs.count(g)) return fail(HPVM_ERR_INVALID_ARG, "unknown or finished graph handle");
+  if (!g->streaming) return fail(HPVM_ERR_INVALID_ARG, "pop needs a graph launched as a streaming graph");
+  if (g->items.empty()) return fail(HPVM_ERR_INVALID_ARG, "pop on a stream with no pushed item");
+  cudaSetDevice(ctx->device);
+  StreamItem& it = g->items.front();
+  int rc = wait_event(it.done, timeout_ms);
+  if (rc == HPVM_ERR_TIMEOUT) return rc;  // the item stays queued
+  if (rc == HPVM_OK) rc = check_status(ctx);
+  if (out && out_size) memcpy(out, it.record.data(), std::min(out_size, it.record.size()));
+  cudaEventDestroy(it.done);
+  g->items.pop_front();
+  return rc == HPVM_OK ? ok() : rc;
 }
 
 int hpvm_wait(hpvm_graph* g, int64_t timeout_ms) {
@@ -902,32 +1188,23 @@ int hpvm_wait(hpvm_graph* g, int64_t timeout_ms) {
   hpvm_ctx* ctx = g->ctx;
   if (!ctx->graphs.count(g)) return fail(HPVM_ERR_INVALID_ARG, "unknown or already finished graph handle");
   cudaSetDevice(ctx->device);
-  cudaError_t e = cudaSuccess;
-  if (g->done) {
-    const auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-      e = cudaEventQuery(g->done);
-      if (e != cudaErrorNotReady) break;
-      if (timeout_ms >= 0 &&
-          std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
-        return fail(HPVM_ERR_TIMEOUT, "graph not finished after %lld ms", (long long)timeout_ms);
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
-    }
-  } else {
-    e = cudaStreamSynchronize(g->stream);
-  }
   int rc = HPVM_OK;
-  if (e != cudaSuccess) rc = cuda_fail(e, "waiting for the graph");
-  if (rc == HPVM_OK && ctx->status.host) {
-    int st = *const_cast<volatile int*>(ctx->status.host);
-    if (st) {
-      *const_cast<volatile int*>(ctx->status.host) = 0;
-      rc = fail(HPVM_ERR_DEVICE_FAULT, "a kernel gave up a bounded wait (status bits 0x%x)", st);
+  if (g->streaming) {
+    for (auto& it : g->items) {
+      rc = wait_event(it.done, timeout_ms);
+      if (rc == HPVM_ERR_TIMEOUT) return rc;
+      if (rc != HPVM_OK) break;
     }
+  } else if (g->done) {
+    rc = wait_event(g->done, timeout_ms);
+    if (rc == HPVM_ERR_TIMEOUT) return rc;
+  } else {
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "waiting for the graph");
   }
-  if (g->done) cudaEventDestroy(g->done);
+  if (rc == HPVM_OK) rc = check_status(ctx);
   ctx->graphs.erase(g);
-  delete g;
+  free_graph(g);
   return rc == HPVM_OK ? ok() : rc;
 }
 

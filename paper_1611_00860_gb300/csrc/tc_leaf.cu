@@ -88,6 +88,8 @@ struct TcParams {
   const float* scaleB;  // FP8: [ceil(N/128)][nkb] block scales of op(B)^T
   int nkb;              // FP8: ceil(K/128)
   int* status;
+  const float* aux;     // EPI 2: H, column-major with leading dimension ldaux
+  int64_t ldaux;
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -372,7 +374,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int MODE>
+// EPI: 0 none; 1 C = tanh(alpha*acc + beta*C); 2 C = (alpha*acc + beta*C)*(1 - H^2)
+// (the elementwise leaf merged into the sgemm leaf, MergeDependentNodes).
+template <int MODE, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
     sgemm_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -566,10 +570,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int u = 0; u < 8; ++u) old[u] = (u0 + u < ncols) ? __ldcs(cp + (int64_t)(u0 + u) * p.ldc) : 0.f;
           }
+          float hx[EPI == 2 ? 8 : 1];
+          if (EPI == 2) {
+            const float* hp = p.aux + row + (int64_t)col0 * p.ldaux;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) hx[u] = (u0 + u < ncols) ? __ldcs(hp + (int64_t)(u0 + u) * p.ldaux) : 0.f;
+          }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             if (u0 + u < ncols) {
-              const float v = (p.beta == 0.f) ? p.alpha * acc[u0 + u] : fmaf(p.alpha, acc[u0 + u], p.beta * old[u]);
+              float v = (p.beta == 0.f) ? p.alpha * acc[u0 + u] : fmaf(p.alpha, acc[u0 + u], p.beta * old[u]);
+              if (EPI == 1) v = tanhf(v);
+              if (EPI == 2) v = v * (1.f - hx[u] * hx[u]);
               __stcs(cp + (int64_t)(u0 + u) * p.ldc, v);
             }
           }
@@ -737,9 +749,23 @@ cudaError_t launch_quant(const float* X, int64_t ld, bool mmajor, int rows, int 
   return cudaGetLastError();
 }
 
+template <int MODE, int EPI>
+cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, dim3 grid, cudaStream_t s) {
+  using C_ = Cfg<MODE>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e =
+        cudaFuncSetAttribute(sgemm_tc<MODE, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  sgemm_tc<MODE, EPI><<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm);
+  return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStream_t s, KernelReport* rep,
-                   std::string* err, const LaunchHooks* hooks) {
+                   std::string* err, const LaunchHooks* hooks, const Epilogue& epi) {
   using C_ = Cfg<MODE>;
   constexpr int NPROD = MODE == 3 ? 3 : 1;
   const int M = (int)d.M, N = (int)d.N, K = (int)d.K;
@@ -784,19 +810,14 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
       maps[3] = maps[2];
     }
   }
-  static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(sgemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, st.dev};
+  TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, st.dev, epi.aux, epi.ldaux};
   const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   dim3 grid((unsigned)std::min(tiles, num_sms()));
   hook_begin(hooks, s);
-  sgemm_tc<MODE><<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm);
+  if (epi.kind == 1) e = launch_leaf<MODE, 1>(maps, prm, grid, s);
+  else if (epi.kind == 2) e = launch_leaf<MODE, 2>(maps, prm, grid, s);
+  else e = launch_leaf<MODE, 0>(maps, prm, grid, s);
   hook_end(hooks, s);
-  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   kernels += 1;
   if (rep) {
@@ -823,7 +844,8 @@ void tc_tile(int /*tier*/, int* tm, int* tn) {
 size_t tc_workspace_bytes(const SgemmDesc& d, int tier) { return ws_layout(d, mode_of_tier(tier)).total; }
 
 cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, const DeviceStatus& st,
-                      cudaStream_t s, KernelReport* rep, std::string* err, const LaunchHooks* hooks) {
+                      cudaStream_t s, KernelReport* rep, std::string* err, const LaunchHooks* hooks,
+                      const Epilogue& epi) {
   if (d.M > INT32_MAX / 2 || d.N > INT32_MAX / 2 || d.K > INT32_MAX / 2) {
     *err = "M, N and K must each fit in 30 bits for the tensor-core tiers";
     return cudaErrorInvalidValue;
@@ -832,9 +854,9 @@ cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, c
     *err = "workspace too small or not 256-byte aligned";
     return cudaErrorInvalidValue;
   }
-  if (tier == 2) return run_tc<3>(d, ws, st, s, rep, err, hooks);
-  if (tier == 4) return run_tc<8>(d, ws, st, s, rep, err, hooks);
-  return run_tc<1>(d, ws, st, s, rep, err, hooks);
+  if (tier == 2) return run_tc<3>(d, ws, st, s, rep, err, hooks, epi);
+  if (tier == 4) return run_tc<8>(d, ws, st, s, rep, err, hooks, epi);
+  return run_tc<1>(d, ws, st, s, rep, err, hooks, epi);
 }
 
 }  // namespace hpvm

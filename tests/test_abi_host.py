@@ -133,19 +133,45 @@ def test_ports_and_flags_checked(ctx):
     root = H.hpvm_create_node(ctx, None, H.HPVM_NODE_INTERNAL)
     a = H.hpvm_create_node(ctx, root, H.HPVM_NODE_ALLOCATION)
     l1 = H.hpvm_create_node(ctx, root, H.HPVM_NODE_SGEMM_LEAF, (2, 2))
-    for bad in [(a, l1, 1, 4, 12), (a, l1, 1, 0, 20), (a, l1, 2, 0, 12)]:
+    for bad in [(a, l1, 1, 4, 12), (a, l1, 1, 0, 20), (a, l1, 2, 0, 12), (l1, a, 1, 2, 0)]:
         with pytest.raises(H.HpvmError) as e:
             H.hpvm_create_edge(*bad)
         assert e.value.code == H.HPVM_ERR_INVALID_ARG
-    with pytest.raises(H.HpvmError) as e:
-        H.hpvm_create_edge(a, l1, H.HPVM_ALL_TO_ALL, 0, 12, stream=True)
-    assert e.value.code == H.HPVM_ERR_UNSUPPORTED
     with pytest.raises(H.HpvmError):
-        H.hpvm_bind_input(l1, 20, 0)  # the root has 20 inputs: 0..19
+        H.hpvm_bind_input(l1, 23 * 16, 0)  # the root has 16 records of 23 ports
     with pytest.raises(H.HpvmError):
         H.hpvm_bind_input(root, 0, 0)  # the root has no parent
     with pytest.raises(H.HpvmError):
-        H.hpvm_create_node(ctx, root, H.HPVM_NODE_SGEMM_LEAF, (H.HPVM_DIM_FROM_INPUT(20), 2))
+        H.hpvm_create_node(ctx, root, H.HPVM_NODE_SGEMM_LEAF, (H.HPVM_DIM_FROM_INPUT(23 * 16), 2))
+
+
+def test_streaming_edge_inside_a_tile_is_not_lowered(ctx):
+    nodes = build_sgemm_graph(ctx)
+    # a second, streaming Allocation -> leaf edge would feed port 12 twice;
+    # build a fresh tile node whose Allocation edge is streaming instead
+    root = H.hpvm_create_node(ctx, None, H.HPVM_NODE_INTERNAL)
+    inner = H.hpvm_create_node(ctx, root, H.HPVM_NODE_INTERNAL,
+                               (H.HPVM_DIM_FROM_INPUT(14), H.HPVM_DIM_FROM_INPUT(15)))
+    for p in range(20):
+        H.hpvm_bind_input(inner, p, p)
+    alloc = H.hpvm_create_node(ctx, inner, H.HPVM_NODE_ALLOCATION)
+    leaf = H.hpvm_create_node(ctx, inner, H.HPVM_NODE_SGEMM_LEAF,
+                              (H.HPVM_DIM_FROM_INPUT(12), H.HPVM_DIM_FROM_INPUT(13)))
+    for sp, dp in ((0, 12), (1, 13), (2, 14), (3, 15)):
+        H.hpvm_create_edge(alloc, leaf, H.HPVM_ALL_TO_ALL, sp, dp, stream=(sp == 0))
+    for p in range(12):
+        H.hpvm_bind_input(leaf, p, p)
+    for q in range(4):
+        H.hpvm_bind_input(leaf, 16 + q, 16 + q)
+    H.hpvm_bind_input(alloc, 12, 0)
+    H.hpvm_bind_input(alloc, 13, 1)
+    H.hpvm_validate(root)
+    a = make_args(128, 96, 160, 0x1000, 4 * 128 * 160, 128, 0x2000, 4 * 96 * 160, 96,
+                  0x3000, 4 * 128 * 96, 128, 1.5, 0.5, False, True, H.HPVM_TIER_BF16X3)
+    with pytest.raises(H.HpvmError) as e:
+        H.hpvm_workspace_size(ctx, root, a)
+    assert e.value.code == H.HPVM_ERR_UNSUPPORTED
+    del nodes
 
 
 def test_unfed_and_twice_fed_inputs(ctx):
@@ -250,3 +276,33 @@ def test_tracker_host_side(ctx):
     H.hpvm_untrack_mem(ctx, p)
     with pytest.raises(H.HpvmError):
         H.hpvm_untrack_mem(ctx, p)
+
+
+def test_chain_graph_lowers_on_host(ctx):
+    from paper_1611_00860_gb300.chain import build_chain_graph, build_single_stage_graph
+    root = build_chain_graph(ctx, 4)
+    w, rows = 64, 48
+    arr = (H.RootArgs * 4)()
+    for l in range(4):
+        arr[l] = make_args(w, rows, w, 0x1000, w * w * 4, w, 0 if l else 0x2000, rows * w * 4, w,
+                           0x3000 + 0x10000 * l, rows * w * 4, w, 1.0, 0.0, False, False,
+                           H.HPVM_TIER_BF16)
+    assert H.hpvm_workspace_size(ctx, root, arr) > 0
+    # fewer records than stages: stage 3 reads a record that was not passed
+    short = (H.RootArgs * 3)(*arr[:3])
+    with pytest.raises(H.HpvmError) as e:
+        H.hpvm_workspace_size(ctx, root, short)
+    assert e.value.code == H.HPVM_ERR_INVALID_ARG
+    g = build_single_stage_graph(ctx, H.HPVM_NODE_TANH_GRAD_LEAF)
+    a = make_args(w, rows, w, 0x1000, w * w * 4, w, 0x2000, rows * w * 4, w, 0x3000, rows * w * 4, w,
+                  1.0, 0.0, True, False, H.HPVM_TIER_BF16)
+    with pytest.raises(H.HpvmError) as e:  # the tanh adjoint needs H
+        H.hpvm_workspace_size(ctx, g, a)
+    assert e.value.code == H.HPVM_ERR_SHAPE
+    a.aux, a.bytesAux, a.ldaux = 0x4000, rows * w * 4, w
+    assert H.hpvm_workspace_size(ctx, g, a) > 0
+
+
+def test_push_pop_need_a_streaming_graph(ctx):
+    with pytest.raises(H.HpvmError):
+        H.hpvm_pop(0)

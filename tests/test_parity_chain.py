@@ -1,0 +1,156 @@
+"""The streamed differentiable chain on the GPU, through the C-ABI.
+
+* MergeDependentNodes: a stage whose tanh leaf is merged into the sgemm
+  epilogue equals the same stage with the tanh leaf run as its own kernel,
+  bit for bit (both evaluate tanhf on the same FP32 value).
+* Forward (one launch of the chain graph, and items pushed through it as a
+  streaming graph) against the FP64 chain definition of the oracle.
+* Gradients of sum(Y * G) from torch.autograd through ChainFunction (the
+  adjoint sgemm and tanh leaves, activations recomputed) against the
+  oracle's FP64 gradients, which finite differences pin.
+
+Tolerances (normwise relative): plain BF16 operands 1e-2 (the BF16 tier's
+bound). For BF16x3 operands each product carries the tier's 5e-6, and an
+output of the chain composes up to 2L - 1 = 7 products (recomputed forward
+and adjoint) plus tanh evaluations, so the bound used is 7 x 5e-6 ~ 4e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint as J
+from oracle import sgemm as O
+from paper_1611_00860_gb300 import _lib as H
+from paper_1611_00860_gb300.chain import ChainEngine, chain_apply, _rm_product_args
+
+pytestmark = pytest.mark.gpu
+
+TOL = {H.HPVM_TIER_BF16: 1e-2, H.HPVM_TIER_BF16X3: 4e-5}
+
+
+def _inputs(items, rows, w, layers, seed):
+    g = torch.Generator().manual_seed(seed)
+    X = torch.randn(items, rows, w, generator=g)
+    Ws = [torch.randn(w, w, generator=g) / w ** 0.5 for _ in range(layers)]
+    G = torch.randn(items, rows, w, generator=g)
+    return X, Ws, G
+
+
+@pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
+@pytest.mark.parametrize("kind", [H.HPVM_NODE_TANH_LEAF, H.HPVM_NODE_TANH_GRAD_LEAF])
+def test_merged_equals_unmerged(cuda_device, tier, kind):
+    fused = ChainEngine(1, tier=tier, fuse=True)
+    plain = ChainEngine(1, tier=tier, fuse=False)
+    try:
+        g = torch.Generator().manual_seed(1)
+        Hm = torch.randn(300, 160, generator=g).cuda()
+        W = (torch.randn(160, 200, generator=g) / 12).cuda()
+        Haux = torch.tanh(torch.randn(300, 200, generator=g)).cuda()
+        outs = []
+        for eng in (fused, plain):
+            out = torch.empty(300, 200, device="cuda")
+            a = _rm_product_args(out, Hm, W, tier, eng.flags)
+            if kind == H.HPVM_NODE_TANH_GRAD_LEAF:
+                a.aux, a.bytesAux, a.ldaux = Haux.data_ptr(), Haux.numel() * 4, 200
+                eng._run(eng.stage_dtanh, a)
+            else:
+                eng._run(eng.stage_tanh, a)
+            outs.append(out.cpu())
+        assert torch.equal(outs[0], outs[1])
+        # and both are the elementwise leaf applied to the product
+        ref = Hm.double().cpu() @ W.double().cpu()
+        ref = torch.tanh(ref) if kind == H.HPVM_NODE_TANH_LEAF else ref * (1 - Haux.double().cpu() ** 2)
+        assert O.normwise_rel_err(outs[0].double().numpy(), ref.numpy()) <= TOL[tier]
+    finally:
+        fused.close()
+        plain.close()
+
+
+@pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
+@pytest.mark.parametrize("items,rows,w,layers", [(3, 24, 16, 4), (2, 300, 256, 4), (1, 7, 5, 2)])
+def test_forward_and_streaming_match_oracle(cuda_device, tier, items, rows, w, layers):
+    X, Ws, _ = _inputs(items, rows, w, layers, seed=rows + w)
+    eng = ChainEngine(layers, tier=tier)
+    try:
+        Xd = X.cuda()
+        Wd = [W.cuda() for W in Ws]
+        Y = eng.forward(Xd.reshape(-1, w), Wd).reshape(items, rows, w).cpu()
+        streamed = eng.stream_forward([Xd[i] for i in range(items)], Wd)
+        for i in range(items):
+            _, _, ref = J.chain_forward(X[i].double().numpy(), [W.double().numpy() for W in Ws])
+            assert O.normwise_rel_err(Y[i].double().numpy(), ref) <= TOL[tier]
+            # an item pushed alone through the streaming graph gives the
+            # result of the same rows in the batched launch
+            assert O.normwise_rel_err(streamed[i].cpu().double().numpy(), Y[i].double().numpy()) <= 1e-6
+    finally:
+        eng.close()
+
+
+@pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
+@pytest.mark.parametrize("items,rows,w", [(1, 24, 16), (2, 64, 128)])
+def test_gradients_match_oracle(cuda_device, tier, items, rows, w):
+    layers = 4
+    X, Ws, G = _inputs(items, rows, w, layers, seed=7 * rows + w)
+    eng = ChainEngine(layers, tier=tier)
+    try:
+        Xd = X.cuda().requires_grad_(True)
+        Wd = [W.cuda().requires_grad_(True) for W in Ws]
+        Y = chain_apply(eng, Xd, Wd)
+        (Y * G.cuda()).sum().backward()
+        Xf = X.reshape(-1, w).double().numpy()
+        dX, dW = J.chain_backward(Xf, [W.double().numpy() for W in Ws], G.reshape(-1, w).double().numpy())
+        assert O.normwise_rel_err(Xd.grad.reshape(-1, w).double().cpu().numpy(), dX) <= TOL[tier]
+        for l in range(layers):
+            assert O.normwise_rel_err(Wd[l].grad.double().cpu().numpy(), dW[l]) <= TOL[tier]
+    finally:
+        eng.close()
+
+
+def test_pop_without_push_and_push_without_stream(cuda_device):
+    eng = ChainEngine(2)
+    try:
+        X = torch.randn(8, 16, device="cuda")
+        Ws = [torch.randn(16, 16, device="cuda") for _ in range(2)]
+        outs = [torch.empty(8, 16, device="cuda") for _ in range(2)]
+        rec = eng.chain_records(X, Ws, outs)
+        g = H.hpvm_launch(eng.ctx, eng.chain, rec, True, 0)
+        with pytest.raises(H.HpvmError) as e:
+            H.hpvm_pop(g, None, 1000)
+        assert e.value.code == H.HPVM_ERR_INVALID_ARG
+        H.hpvm_push(g, rec)
+        H.hpvm_pop(g, None, 60000)
+        H.hpvm_wait(g, 60000)
+        g2 = H.hpvm_launch(eng.ctx, eng.chain, rec, False, 0)
+        with pytest.raises(H.HpvmError):
+            H.hpvm_push(g2, rec)
+        H.hpvm_wait(g2, 60000)
+        torch.cuda.synchronize()
+        _, _, ref = J.chain_forward(X.double().cpu().numpy(), [W.double().cpu().numpy() for W in Ws])
+        assert O.normwise_rel_err(outs[-1].double().cpu().numpy(), ref) <= 1e-2
+    finally:
+        eng.close()
+
+
+@pytest.mark.slow
+def test_chain_workload_sampled_rows(cuda_device):
+    # the chain workload: 64 items of 256 x 4096, four 4096 x 4096 weights,
+    # BF16 operands; rows are independent, so the oracle checks the forward
+    # output and the input gradient of 32 sampled rows of one item
+    import workloads as W
+    X, Ws, G = W.chain_inputs()
+    eng = ChainEngine(4, tier=H.HPVM_TIER_BF16)
+    try:
+        Xd = X.cuda().requires_grad_(True)
+        Wd = [w.cuda().requires_grad_(True) for w in Ws]
+        Y = chain_apply(eng, Xd, Wd)
+        (Y * G.cuda()).sum().backward()
+        rows = torch.arange(0, 256, 8)
+        Xs = X[5, rows].double().numpy()
+        Wn = [w.double().numpy() for w in Ws]
+        _, _, ref = J.chain_forward(Xs, Wn)
+        assert O.normwise_rel_err(Y[5, rows].double().detach().cpu().numpy(), ref) <= 1e-2
+        dX, _ = J.chain_backward(Xs, Wn, G[5, rows].double().numpy())
+        assert O.normwise_rel_err(Xd.grad[5, rows].double().cpu().numpy(), dX) <= 1e-2
+        assert np.isfinite(Wd[0].grad.cpu().numpy()).all()
+    finally:
+        eng.close()
