@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp8", action="store_true", help="skip the 16384 FP8 workload section")
     ap.add_argument("--fp8-n", type=int, default=16384)
+    ap.add_argument("--no-chain", action="store_true", help="skip the streamed chain section")
     return ap.parse_args()
 
 
@@ -260,6 +261,68 @@ def fp8_section(args, dfg, H, W, torch, local, peaks, world, rank, barrier):
     return out
 
 
+def chain_section(args, H, W, torch, local, world, barrier):
+    """The streamed chain: 64 items of 256 x 4096 through four 4096 x 4096
+    weights with tanh between (BF16 operands, FP32 accumulate).
+    (a) a training step of the whole batch through ChainFunction: forward
+        chain launch, recomputed activations, adjoint leaves;
+    (b) the forward of the 64 items pushed one by one through the chain
+        launched as a streaming graph (hpvm_push / hpvm_pop)."""
+    from paper_1611_00860_gb300.chain import ChainEngine, chain_apply
+    X, Ws, G = W.chain_inputs()
+    items, rows, w = X.shape
+    L = len(Ws)
+    dev = f"cuda:{local}"
+    Xd, Gd = X.to(dev), G.to(dev)
+    Wd = [x.to(dev).requires_grad_(True) for x in Ws]
+    eng = ChainEngine(L, device=local, tier=H.HPVM_TIER_BF16)
+    stream = torch.cuda.current_stream(local)
+    n = items * rows
+    prod = 2.0 * n * w * w                      # one stage's product
+    fwd, bwd, recompute = L * prod, 2 * L * prod, (L - 1) * prod
+    out = {"workload": f"{items} items x {rows} x {w}, {L} weights {w}x{w} ~ N(0,1/{w}), tanh between, "
+                       "BF16 operands, FP32 accumulate, seed 3", "unit": "TFLOP/s"}
+
+    def step():
+        Xr = Xd.requires_grad_(True)
+        Y = chain_apply(eng, Xr, Wd)
+        (Y * Gd).sum().backward()
+        Xd.grad = None
+        for x in Wd:
+            x.grad = None
+
+    steps = 5
+    step()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / steps
+    out["train_step"] = {"value": (fwd + bwd) * world / (ms * 1e-3) / 1e12, "ms_per_step": ms, "steps": steps,
+                         "executed_tflop_per_step": (fwd + bwd + recompute) / 1e12,
+                         "executed_rate": (fwd + bwd + recompute) * world / (ms * 1e-3) / 1e12,
+                         "note": "value counts forward + backward products; the recomputed forward "
+                                 "of the activations is in executed_rate"}
+    with torch.no_grad():
+        Wn = [x.detach() for x in Wd]
+        xs = [Xd[i] for i in range(items)]
+        eng.stream_forward(xs, Wn)
+        barrier()
+        t0 = time.perf_counter()
+        eng.stream_forward(xs, Wn)
+        barrier()
+        dt = time.perf_counter() - t0
+    out["streamed_forward"] = {"value": fwd * world / dt / 1e12, "ms_per_batch": dt * 1e3,
+                               "items": items, "path": "hpvm_launch(stream_graph=1) + 64 x hpvm_push + 64 x hpvm_pop"}
+    eng.close()
+    del Xd, Gd, Wd
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -430,7 +493,12 @@ def main():
                "blocks": len(refs), "metric": "normwise ||C-C_ref||_F/||C_ref||_F over sampled blocks",
                "tolerance": 5e-6}
 
-    # 6) the FP8 workload: M = N = K = 16384, per-row log-normal(0,2)
+    # 6) the streamed chain (training step and streamed forward)
+    chain = None
+    if not args.no_chain:
+        chain = chain_section(args, H, W, torch, local, world, barrier)
+
+    # 7) the FP8 workload: M = N = K = 16384, per-row log-normal(0,2)
     # magnitudes, beta = 0; FP8 block-scaled leaf vs BF16x3 vs plain FP32 on
     # the same inputs and GPU
     fp8 = None
@@ -450,7 +518,7 @@ def main():
                        "l2": "inputs larger than L2 (768 MiB FP32 operands + 512 MiB split planes); no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "rel_err": err, "fp32_cuda_core": fp32,
-            "fp8_workload": fp8,
+            "fp8_workload": fp8, "chain_workload": chain,
         }
         print(json.dumps(line), flush=True)
     dfg.close()

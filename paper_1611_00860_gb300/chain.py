@@ -126,6 +126,7 @@ class ChainEngine:
         self.stage_dtanh = build_single_stage_graph(self.ctx, H.HPVM_NODE_TANH_GRAD_LEAF)
         self.stage_plain = build_single_stage_graph(self.ctx, None)
         self._ws = None
+        self._pending: list = []
 
     def close(self):
         if self.ctx:
@@ -143,12 +144,20 @@ class ChainEngine:
         return torch.cuda.current_stream(self.device).cuda_stream
 
     def _run(self, root: int, args) -> None:
+        """Launch asynchronously on the current stream; launches of one
+        forward or backward share the workspace in stream order and are
+        waited for together (``_drain``)."""
         need = H.hpvm_workspace_size(self.ctx, root, args)
         if need and (self._ws is None or self._ws.numel() < need):
+            self._drain()
             self._ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
             H.hpvm_set_workspace(self.ctx, self._ws.data_ptr(), self._ws.numel())
-        g = H.hpvm_launch(self.ctx, root, args, False, self._stream())
-        H.hpvm_wait(g, 600000)
+        self._pending.append(H.hpvm_launch(self.ctx, root, args, False, self._stream()))
+
+    def _drain(self, timeout_ms: int = 600000) -> None:
+        pending, self._pending = self._pending, []
+        for g in pending:
+            H.hpvm_wait(g, timeout_ms)
 
     def chain_records(self, X: torch.Tensor, Ws, outs):
         """Records of the chain graph: stage l computes outs[l] = act(in_l) W_l."""
@@ -167,6 +176,7 @@ class ChainEngine:
         H_1..H_{L-1} (the tanh outputs, the chain's intermediate buffers)."""
         outs = [torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws]
         self._run(self.chain, self.chain_records(X, Ws, outs))
+        self._drain()
         return (outs[-1], outs[:-1]) if keep else outs[-1]
 
     def recompute(self, X: torch.Tensor, Ws):
@@ -210,6 +220,7 @@ class ChainEngine:
             else:
                 self._run(self.stage_plain, a)
                 dX = dH
+        self._drain()
         return dX, dWs
 
     # -- streaming -----------------------------------------------------------------

@@ -55,6 +55,7 @@ def test_merged_equals_unmerged(cuda_device, tier, kind):
                 eng._run(eng.stage_dtanh, a)
             else:
                 eng._run(eng.stage_tanh, a)
+            eng._drain()
             outs.append(out.cpu())
         assert torch.equal(outs[0], outs[1])
         # and both are the elementwise leaf applied to the product
