@@ -350,6 +350,48 @@ HPVM_API int hpvm_sgemm_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, float al
                                        float beta, float* C, int64_t ldc, int transA, int transB,
                                        int* dev_status, void* cuda_stream);
 
+/* ---- batches of independent DFG instances -----------------------------
+ * No paper counterpart: many instances of one single-stage sgemm graph
+ * (records[i] = instance i's argument records, record_bytes apart), run by
+ * one split pre-pass launch and one persistent launch of the grouped leaf
+ * over every output tile of every instance, longest tiles first.
+ * Instances take the BF16X3 or BF16 tier (the same for all) and device
+ * pointers. Each instance's tile width (its leaf grid, block_y = 64, 128 or
+ * 256 columns per internal instance) comes from a policy:
+ *   0: 256 for all; 1: 128 for all; 2, 3: per instance, the width that
+ *   minimises tiles x (width x padded K + overhead), overhead light (2) or
+ *   heavy (3); -1: the policy hpvm_batch_autotune found for a batch of the
+ *   same shapes in this context, else 2.
+ * prepare allocates the batch's operand planes and tables on the device
+ * (runtime-owned, freed by hpvm_batch_free or hpvm_cleanup) and sets kernel
+ * attributes; run only enqueues the two kernels, so it can be captured in
+ * a CUDA graph. A batch reads the pointers of its records at every run. */
+typedef struct hpvm_batch hpvm_batch;
+typedef struct hpvm_batch_stats {
+  int32_t count, tier, policy;
+  int32_t tiles;        /* output tiles of the leaf launch */
+  int32_t split_tiles;  /* 64 x 64 tiles of the pre-pass launch */
+  int32_t grid;         /* persistent CTAs */
+  int32_t tile_width_count[3]; /* instances with 64, 128, 256 columns */
+  int32_t reserved;
+  int64_t workspace_bytes;
+} hpvm_batch_stats;
+HPVM_API int hpvm_batch_prepare(hpvm_ctx* ctx, hpvm_node* root, const void* records, size_t record_bytes,
+                                int count, int policy, hpvm_batch** out);
+HPVM_API int hpvm_batch_run(hpvm_batch* batch, void* cuda_stream);
+/* Time each policy (reps runs after one warm-up, CUDA events on
+ * cuda_stream), keep the fastest for this batch and for later batches of
+ * the same shapes in the context. Results of the timed runs are valid. */
+HPVM_API int hpvm_batch_autotune(hpvm_batch* batch, void* cuda_stream, int reps, int* best_policy,
+                                 double* best_ms);
+HPVM_API int hpvm_batch_info(hpvm_batch* batch, hpvm_batch_stats* out);
+HPVM_API int hpvm_batch_free(hpvm_batch* batch);
+/* Host-only: the tile widths a policy (0..3) picks for instances of the
+ * given shapes, and the leaf's tile schedule, 4 ints per tile (instance,
+ * m0, n0, 0) in launch order; tiles may be NULL to query num_tiles. */
+HPVM_API int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, const int64_t* K, int policy,
+                             int32_t* bn, int32_t* tiles, int64_t tile_cap, int64_t* num_tiles);
+
 /* Thread-local message of the last failed call ("" if none). */
 HPVM_API const char* hpvm_last_error(void);
 /* ABI version (major * 100 + minor). */

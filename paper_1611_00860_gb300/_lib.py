@@ -95,6 +95,20 @@ class LaunchInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int32), ("tier", ctypes.c_int32), ("policy", ctypes.c_int32),
+        ("tiles", ctypes.c_int32), ("split_tiles", ctypes.c_int32), ("grid", ctypes.c_int32),
+        ("tile_width_count", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32),
+        ("workspace_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d["tile_width_count"] = list(self.tile_width_count)
+        return d
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -131,6 +145,14 @@ def _load() -> ctypes.CDLL:
         "hpvm_quant_fp8": (I, [P, I64, I, I64, I64, P, P, P]),
         "hpvm_sgemm_bf16x3_noalloc": (I, [I64, I64, I64, ctypes.c_float, P, I64, P, I64,
                                           ctypes.c_float, P, I64, I, I, P, P]),
+        "hpvm_batch_prepare": (I, [P, P, P, SZ, I, I, PP]),
+        "hpvm_batch_run": (I, [P, P]),
+        "hpvm_batch_autotune": (I, [P, P, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+        "hpvm_batch_info": (I, [P, ctypes.POINTER(BatchInfo)]),
+        "hpvm_batch_free": (I, [P]),
+        "hpvm_batch_plan": (I, [I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                ctypes.POINTER(ctypes.c_int64), I, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int32), I64, ctypes.POINTER(ctypes.c_int64)]),
         "hpvm_last_error": (ctypes.c_char_p, []),
         "hpvm_version": (I, []),
     }
@@ -302,6 +324,48 @@ def hpvm_sgemm_bf16x3_noalloc(M: int, N: int, K: int, alpha: float, A: int, lda:
     _check(LIB.hpvm_sgemm_bf16x3_noalloc(int(M), int(N), int(K), float(alpha), A, int(lda), B,
                                          int(ldb), float(beta), C, int(ldc), int(bool(transA)),
                                          int(bool(transB)), dev_status, cuda_stream or None))
+
+
+def hpvm_batch_prepare(ctx: int, root: int, records, count: int, policy: int = -1) -> int:
+    """``records``: a ctypes array of ``count`` RootArgs (one per instance)."""
+    out = ctypes.c_void_p()
+    _check(LIB.hpvm_batch_prepare(ctx, root, ctypes.byref(records), ctypes.sizeof(RootArgs), int(count),
+                                  int(policy), ctypes.byref(out)))
+    return out.value
+
+
+def hpvm_batch_run(batch: int, cuda_stream: int = 0) -> None:
+    _check(LIB.hpvm_batch_run(batch, cuda_stream or None))
+
+
+def hpvm_batch_autotune(batch: int, cuda_stream: int = 0, reps: int = 3) -> tuple[int, float]:
+    best = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(LIB.hpvm_batch_autotune(batch, cuda_stream or None, int(reps), ctypes.byref(best), ctypes.byref(ms)))
+    return best.value, ms.value
+
+
+def hpvm_batch_info(batch: int) -> BatchInfo:
+    info = BatchInfo()
+    _check(LIB.hpvm_batch_info(batch, ctypes.byref(info)))
+    return info
+
+
+def hpvm_batch_free(batch: int) -> None:
+    _check(LIB.hpvm_batch_free(batch))
+
+
+def hpvm_batch_plan(M, N, K, policy: int):
+    """Tile widths and the tile schedule (list of (instance, m0, n0))."""
+    n = len(M)
+    arr = lambda v: (ctypes.c_int64 * max(n, 1))(*[int(x) for x in v])
+    Ma, Na, Ka = arr(M), arr(N), arr(K)
+    bn = (ctypes.c_int32 * max(n, 1))()
+    cnt = ctypes.c_int64()
+    _check(LIB.hpvm_batch_plan(n, Ma, Na, Ka, int(policy), bn, None, 0, ctypes.byref(cnt)))
+    tiles = (ctypes.c_int32 * max(4 * cnt.value, 1))()
+    _check(LIB.hpvm_batch_plan(n, Ma, Na, Ka, int(policy), bn, tiles, cnt.value, ctypes.byref(cnt)))
+    return list(bn)[:n], [tuple(tiles[4 * i:4 * i + 3]) for i in range(cnt.value)]
 
 
 def hpvm_last_error() -> str:

@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 namespace hpvm {
 
@@ -86,6 +87,35 @@ cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes,
                       KernelReport* rep, std::string* err,
                       const LaunchHooks* hooks, const Epilogue& epi = Epilogue());
 void tc_tile(int tier, int* tm, int* tn);
+
+// ---- batches of independent instances (tc_leaf.cu) ------------------------
+// One batch of sgemm instances run by the grouped persistent leaf: the split
+// pre-pass of every operand in one launch, then every output tile of every
+// instance in one launch (tiles in decreasing cost, round robin over CTAs).
+struct TcBatch {
+  int tier = 2;
+  std::vector<SgemmDesc> d;
+  std::vector<int> bn;  // tile width of each instance (the policy's choice)
+  int policy = 2;       // 0: 256, 1: 128, 2/3: cost model (light/heavy tile overhead)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<size_t> plane_off;
+  void* d_ops = nullptr;
+  void* d_split_tiles = nullptr;
+  int num_split_tiles = 0;
+  void* d_insts = nullptr;
+  void* d_tiles = nullptr;
+  int num_tiles = 0;
+  int grid = 0;
+};
+std::vector<int> batch_choose_bn(const std::vector<SgemmDesc>& d, int policy);
+// tiles: 4 ints per tile (instance, m0, n0, 0) in schedule order
+void batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, std::vector<int>* tiles);
+int tc_batch_build(TcBatch* b, std::string* err);
+cudaError_t tc_batch_run(const TcBatch& b, const DeviceStatus& st, cudaStream_t s, const LaunchHooks* hooks);
+int tc_batch_autotune(TcBatch* b, const DeviceStatus& st, cudaStream_t s, int reps, int* best_policy,
+                      double* best_ms, std::string* err);
+void tc_batch_free(TcBatch* b);
 
 // Sets the calling thread's hpvm_last_error() message (cleared for HPVM_OK)
 // and returns `code` (runtime.cpp).

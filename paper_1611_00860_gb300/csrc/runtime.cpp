@@ -165,6 +165,12 @@ struct hpvm_graph {
   uint64_t pushed = 0;
 };
 
+struct hpvm_batch {
+  hpvm_ctx* ctx = nullptr;
+  hpvm::TcBatch tb;
+  uint64_t signature = 0;
+};
+
 struct hpvm_ctx {
   int device = -1;
   int next_id = 0;
@@ -178,6 +184,8 @@ struct hpvm_ctx {
   hpvm::DeviceStatus status;
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed;  // main-kernel events
+  std::set<hpvm_batch*> batches;
+  std::vector<std::pair<uint64_t, int>> tuned;  // batch shape signature -> best policy
 };
 
 // ---------------------------------------------------------------------------
@@ -913,6 +921,10 @@ int hpvm_cleanup(hpvm_ctx* ctx) {
       cudaEventDestroy(pr.first);
       cudaEventDestroy(pr.second);
     }
+    for (auto* b : ctx->batches) {
+      hpvm::tc_batch_free(&b->tb);
+      delete b;
+    }
   }
   delete ctx;
   return ok();
@@ -1302,6 +1314,160 @@ int hpvm_untrack_mem(hpvm_ctx* ctx, void* p) {
     }
   }
   return fail(HPVM_ERR_INVALID_ARG, "pointer is not the start of a tracked region");
+}
+
+// ---- batches -----------------------------------------------------------------
+namespace {
+uint64_t batch_signature(const std::vector<hpvm::SgemmDesc>& d, int tier) {
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)tier;
+  auto mix = [&](uint64_t v) {
+    h ^= v;
+    h *= 1099511628211ull;
+  };
+  for (auto& x : d) {
+    mix((uint64_t)x.M);
+    mix((uint64_t)x.N);
+    mix((uint64_t)x.K);
+    mix((uint64_t)(x.transA * 2 + x.transB));
+  }
+  return h;
+}
+}  // namespace
+
+int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, const int64_t* K, int policy, int32_t* bn,
+                    int32_t* tiles, int64_t tile_cap, int64_t* num_tiles) {
+  if (count < 0 || (count > 0 && (!M || !N || !K)) || !num_tiles)
+    return fail(HPVM_ERR_INVALID_ARG, "bad arguments");
+  if (policy < 0 || policy > 3) return fail(HPVM_ERR_INVALID_ARG, "policy must be 0..3");
+  std::vector<hpvm::SgemmDesc> d(count);
+  for (int i = 0; i < count; ++i) {
+    if (M[i] < 0 || N[i] < 0 || K[i] < 0) return fail(HPVM_ERR_SHAPE, "negative extent in instance %d", i);
+    d[i].M = M[i];
+    d[i].N = N[i];
+    d[i].K = K[i];
+  }
+  auto w = hpvm::batch_choose_bn(d, policy);
+  std::vector<int> t;
+  hpvm::batch_schedule(d, w, &t);
+  if (bn)
+    for (int i = 0; i < count; ++i) bn[i] = w[i];
+  *num_tiles = (int64_t)(t.size() / 4);
+  if (tiles) {
+    if (tile_cap < *num_tiles) return fail(HPVM_ERR_SHAPE, "tile buffer holds %lld tiles, %lld needed",
+                                           (long long)tile_cap, (long long)*num_tiles);
+    for (size_t i = 0; i < t.size(); ++i) tiles[i] = t[i];
+  }
+  return ok();
+}
+
+int hpvm_batch_prepare(hpvm_ctx* ctx, hpvm_node* root, const void* records, size_t record_bytes, int count,
+                       int policy, hpvm_batch** out) {
+  if (out) *out = nullptr;
+  if (!ctx || !out || !records || count <= 0) return fail(HPVM_ERR_INVALID_ARG, "bad arguments");
+  if (policy < -1 || policy > 3) return fail(HPVM_ERR_INVALID_ARG, "policy must be -1 (tuned) or 0..3");
+  if (ctx->device < 0) return fail(HPVM_ERR_NO_DEVICE, "host-only context");
+  cudaSetDevice(ctx->device);
+  std::vector<hpvm::SgemmDesc> d(count);
+  int tier = -1, rc;
+  for (int i = 0; i < count; ++i) {
+    Plan P;
+    const uint8_t* rec = static_cast<const uint8_t*>(records) + (size_t)i * record_bytes;
+    if ((rc = lower_graph(root, rec, record_bytes, &P)) != HPVM_OK) return rc;
+    if (P.stages.size() != 1 || P.stages[0].epi.kind)
+      return fail(HPVM_ERR_UNSUPPORTED, "a batch runs single-stage sgemm graphs without elementwise leaves");
+    const int t = record_i32(P, P.stages[0].rec, kTierOffset);
+    if (t != HPVM_TIER_BF16X3 && t != HPVM_TIER_BF16)
+      return fail(HPVM_ERR_UNSUPPORTED, "a batch runs the BF16X3 or BF16 tier (instance %d has tier %d)", i, t);
+    if (tier >= 0 && t != tier) return fail(HPVM_ERR_UNSUPPORTED, "all instances of a batch need the same tier");
+    tier = t;
+    d[i] = P.stages[0].d;
+    if (d[i].M > 0 && d[i].N > 0) {
+      if ((rc = check_device_pointer(d[i].C, "C")) != HPVM_OK) return rc;
+      if (d[i].K > 0 && ((rc = check_device_pointer(d[i].A, "A")) != HPVM_OK ||
+                         (rc = check_device_pointer(d[i].B, "B")) != HPVM_OK))
+        return rc;
+    }
+    if (d[i].M > INT32_MAX / 2 || d[i].N > INT32_MAX / 2 || d[i].K > INT32_MAX / 2)
+      return fail(HPVM_ERR_SHAPE, "instance %d is too large for a batch", i);
+  }
+  auto b = std::make_unique<hpvm_batch>();
+  b->ctx = ctx;
+  b->tb.tier = tier;
+  b->tb.d = d;
+  b->signature = batch_signature(d, tier);
+  int pol = policy;
+  if (pol < 0) {
+    pol = 2;
+    for (auto& kv : ctx->tuned)
+      if (kv.first == b->signature) pol = kv.second;
+  }
+  b->tb.policy = pol;
+  std::string err;
+  if (hpvm::tc_batch_build(&b->tb, &err)) {
+    hpvm::tc_batch_free(&b->tb);
+    return fail(HPVM_ERR_CUDA, "batch preparation: %s", err.c_str());
+  }
+  *out = b.get();
+  ctx->batches.insert(b.release());
+  return ok();
+}
+
+int hpvm_batch_run(hpvm_batch* b, void* cuda_stream) {
+  if (!b || !b->ctx->batches.count(b)) return fail(HPVM_ERR_INVALID_ARG, "unknown batch");
+  hpvm_ctx* ctx = b->ctx;
+  hpvm::LaunchHooks hooks;
+  if (ctx->timing) {
+    if (cudaEventCreate(&hooks.main_begin) != cudaSuccess || cudaEventCreate(&hooks.main_end) != cudaSuccess)
+      return fail(HPVM_ERR_CUDA, "cannot create timing events");
+    ctx->timed.emplace_back(hooks.main_begin, hooks.main_end);
+  }
+  cudaError_t e = hpvm::tc_batch_run(b->tb, ctx->status, static_cast<cudaStream_t>(cuda_stream), &hooks);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  return ok();
+}
+
+int hpvm_batch_autotune(hpvm_batch* b, void* cuda_stream, int reps, int* best_policy, double* best_ms) {
+  if (!b || !b->ctx->batches.count(b)) return fail(HPVM_ERR_INVALID_ARG, "unknown batch");
+  int best = -1;
+  double ms = 0;
+  std::string err;
+  if (hpvm::tc_batch_autotune(&b->tb, b->ctx->status, static_cast<cudaStream_t>(cuda_stream), reps < 1 ? 1 : reps,
+                              &best, &ms, &err))
+    return fail(HPVM_ERR_CUDA, "autotuning: %s", err.c_str());
+  bool found = false;
+  for (auto& kv : b->ctx->tuned)
+    if (kv.first == b->signature) {
+      kv.second = best;
+      found = true;
+    }
+  if (!found) b->ctx->tuned.emplace_back(b->signature, best);
+  if (best_policy) *best_policy = best;
+  if (best_ms) *best_ms = ms;
+  return check_status(b->ctx) == HPVM_OK ? ok() : HPVM_ERR_DEVICE_FAULT;
+}
+
+int hpvm_batch_info(hpvm_batch* b, hpvm_batch_stats* out) {
+  if (!b || !out || !b->ctx->batches.count(b)) return fail(HPVM_ERR_INVALID_ARG, "unknown batch or NULL out");
+  memset(out, 0, sizeof *out);
+  out->count = (int32_t)b->tb.d.size();
+  out->tier = b->tb.tier;
+  out->policy = b->tb.policy;
+  out->tiles = b->tb.num_tiles;
+  out->split_tiles = b->tb.num_split_tiles;
+  out->grid = b->tb.grid;
+  out->workspace_bytes = (int64_t)b->tb.ws_bytes;
+  for (int w : b->tb.bn) out->tile_width_count[w == 64 ? 0 : w == 128 ? 1 : 2]++;
+  return ok();
+}
+
+int hpvm_batch_free(hpvm_batch* b) {
+  if (!b || !b->ctx->batches.count(b)) return fail(HPVM_ERR_INVALID_ARG, "unknown batch");
+  cudaSetDevice(b->ctx->device);
+  cudaDeviceSynchronize();
+  hpvm::tc_batch_free(&b->tb);
+  b->ctx->batches.erase(b);
+  delete b;
+  return ok();
 }
 
 }  // extern "C"

@@ -229,14 +229,15 @@ __device__ __forceinline__ void split_pair(float x, __nv_bfloat16& h, __nv_bfloa
   l = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// X "m-major": element (r, k) at X[r + k*ld] (rows contiguous). 64 x 64 tiles.
+// X "m-major": element (r, k) at X[r + k*ld] (rows contiguous). One 64 x 64
+// tile (rows r0.., K k0..) per CTA of 256 threads, transposed through
+// shared memory so both the FP32 read and the BF16 writes are coalesced.
 template <int NPROD>
-__global__ void __launch_bounds__(256) split_mmajor(const float* __restrict__ X, int64_t ld, int rows, int K,
-                                                    int Kp, __nv_bfloat16* __restrict__ hi,
-                                                    __nv_bfloat16* __restrict__ lo) {
+__device__ __forceinline__ void split_tile_m(const float* __restrict__ X, int64_t ld, int rows, int K, int Kp,
+                                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                             int64_t r0, int64_t k0) {
   __shared__ float t[64][65];
   const int tid = threadIdx.x;
-  const int64_t r0 = (int64_t)blockIdx.x * 64, k0 = (int64_t)blockIdx.y * 64;
 #pragma unroll 4
   for (int it = 0; it < 16; ++it) {
     int e = tid + it * 256;
@@ -258,6 +259,56 @@ __global__ void __launch_bounds__(256) split_mmajor(const float* __restrict__ X,
     *reinterpret_cast<uint4*>(hi + gr * Kp + gk) = *reinterpret_cast<const uint4*>(h);
     if (NPROD == 3) *reinterpret_cast<uint4*>(lo + gr * Kp + gk) = *reinterpret_cast<const uint4*>(l);
   }
+}
+
+// X "k-major": element (r, k) at X[k + r*ld] (K contiguous); one 64 x 64
+// tile per CTA, eight consecutive K elements per thread and pass.
+template <int NPROD>
+__device__ __forceinline__ void split_tile_k(const float* __restrict__ X, int64_t ld, int rows, int K, int Kp,
+                                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                             int64_t r0, int64_t k0) {
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int e = threadIdx.x + it * 256;
+    const int64_t r = r0 + (e >> 3), k = k0 + (e & 7) * 8;
+    if (r >= rows || k >= Kp) continue;
+    const float* src = X + r * ld + k;
+    __align__(16) __nv_bfloat16 h[8];
+    __align__(16) __nv_bfloat16 l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) split_pair((k + u < K) ? src[u] : 0.f, h[u], l[u]);
+    *reinterpret_cast<uint4*>(hi + r * Kp + k) = *reinterpret_cast<const uint4*>(h);
+    if (NPROD == 3) *reinterpret_cast<uint4*>(lo + r * Kp + k) = *reinterpret_cast<const uint4*>(l);
+  }
+}
+
+template <int NPROD>
+__global__ void __launch_bounds__(256) split_mmajor(const float* __restrict__ X, int64_t ld, int rows, int K,
+                                                    int Kp, __nv_bfloat16* __restrict__ hi,
+                                                    __nv_bfloat16* __restrict__ lo) {
+  split_tile_m<NPROD>(X, ld, rows, K, Kp, hi, lo, (int64_t)blockIdx.x * 64, (int64_t)blockIdx.y * 64);
+}
+
+// One operand of a batch and its planes; one 64 x 64 tile of one operand.
+struct SplitOp {
+  const float* X;
+  int64_t ld;
+  int mmajor, rows, K, Kp;
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+};
+struct SplitTile {
+  int op, r0, k0, pad;
+};
+
+// The pre-pass of a whole batch in one launch: CTA i splits tile i.
+template <int NPROD>
+__global__ void __launch_bounds__(256) split_batch(const SplitOp* __restrict__ ops,
+                                                   const SplitTile* __restrict__ tiles) {
+  const SplitTile t = tiles[blockIdx.x];
+  const SplitOp o = ops[t.op];
+  if (o.mmajor) split_tile_m<NPROD>(o.X, o.ld, o.rows, o.K, o.Kp, o.hi, o.lo, t.r0, t.k0);
+  else split_tile_k<NPROD>(o.X, o.ld, o.rows, o.K, o.Kp, o.hi, o.lo, t.r0, t.k0);
 }
 
 // X "k-major": element (r, k) at X[k + r*ld] (K contiguous).
@@ -374,13 +425,46 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// One instance of a batch of independent sgemm DFGs (device memory): its
+// four operand-plane tensor maps (64-byte aligned), its result, and the tile
+// width bn (64, 128 or 256 columns) its schedule chose.
+struct GroupInst {
+  CUtensorMap tm[4];  // A hi, A lo, B hi, B lo
+  float* C;
+  int64_t ldc;
+  int M, N, K, bn;
+  float alpha, beta;
+  int pad[10];
+};
+static_assert(sizeof(GroupInst) % 64 == 0, "tensor maps stay 64-byte aligned in an array");
+// One output tile of the batch's schedule.
+struct GroupTile {
+  int inst, m0, n0, pad;
+};
+struct GroupParams {
+  const GroupInst* insts;
+  const GroupTile* tiles;
+  int num_tiles;
+};
+
+// What one tile needs: its instance's operands and result, and where it sits.
+struct TileView {
+  const CUtensorMap* tm[4];
+  float* C;
+  int64_t ldc;
+  int M, N, K, bn, m0, n0;
+  float alpha, beta;
+};
+
 // EPI: 0 none; 1 C = tanh(alpha*acc + beta*C); 2 C = (alpha*acc + beta*C)*(1 - H^2)
 // (the elementwise leaf merged into the sgemm leaf, MergeDependentNodes).
-template <int MODE, int EPI>
+// GROUPED: the persistent CTAs walk the tile list of a batch of instances
+// (gp) instead of the tiles of the one instance of the kernel parameters.
+template <int MODE, int EPI, bool GROUPED>
 __global__ void __launch_bounds__(THREADS, 1)
     sgemm_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
-             TcParams p) {
+             TcParams p, GroupParams gp) {
   using C_ = Cfg<MODE>;
   constexpr int S = C_::STAGES;
   constexpr int NPROD = MODE == 3 ? 3 : 1;
@@ -395,10 +479,42 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int num_kb = (p.K + BK - 1) / BK;
-  const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
   const int tiles_m = (p.M + BM - 1) / BM, tiles_n = (p.N + BN - 1) / BN;
-  const int num_tiles = tiles_m * tiles_n;
+  const int num_tiles = GROUPED ? gp.num_tiles : tiles_m * tiles_n;
+
+  auto view = [&](int t) {
+    TileView v;
+    if constexpr (GROUPED) {
+      const GroupTile gt = gp.tiles[t];
+      const GroupInst* in = gp.insts + gt.inst;
+      for (int i = 0; i < 4; ++i) v.tm[i] = &in->tm[i];
+      v.C = in->C;
+      v.ldc = in->ldc;
+      v.M = in->M;
+      v.N = in->N;
+      v.K = in->K;
+      v.bn = in->bn;
+      v.alpha = in->alpha;
+      v.beta = in->beta;
+      v.m0 = gt.m0;
+      v.n0 = gt.n0;
+    } else {
+      v.tm[0] = &tmA_hi;
+      v.tm[1] = &tmA_lo;
+      v.tm[2] = &tmB_hi;
+      v.tm[3] = &tmB_lo;
+      v.C = p.C;
+      v.ldc = p.ldc;
+      v.M = p.M;
+      v.N = p.N;
+      v.K = p.K;
+      v.bn = BN;
+      v.alpha = p.alpha;
+      v.beta = p.beta;
+      tile_coords(t, tiles_m, tiles_n, &v.m0, &v.n0);
+    }
+    return v;
+  };
 
   // stage s: [A hi][A lo][B hi][B lo] (lo planes only for NPROD == 3)
   auto a_hi = [&](int s) { return smem + s * C_::STAGE_BYTES; };
@@ -433,17 +549,19 @@ __global__ void __launch_bounds__(THREADS, 1)
   // bookkeeping for the drain after an abort
   int issued = 0;     // producer: slabs requested (ring position)
   int committed = 0;  // MMA: slabs whose MMAs were committed (ring position)
-  int chunks_committed = 0;
 
   if (warp == 0 && lane == 0) {
     // ---- producer: TMA loads of the operand slabs into the ring
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA_hi)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
+    if (!GROUPED) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA_hi)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
+    }
     int it = 0;
     bool go = true;
     for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
-      int m0, n0;
-      tile_coords(t, tiles_m, tiles_n, &m0, &n0);
+      const TileView v = view(t);
+      const int num_kb = (v.K + BK - 1) / BK;
+      const uint32_t bytes = C_::PLANES * (A_SLAB + (uint32_t)v.bn * SLAB_ROW_BYTES);
       for (int kb = 0; kb < num_kb; ++kb, ++it) {
         const int s = it % S;
         const uint32_t ph = (it / S) & 1;
@@ -451,22 +569,25 @@ __global__ void __launch_bounds__(THREADS, 1)
           go = false;
           break;
         }
-        mbar_expect_tx(&full[s], C_::STAGE_BYTES);
+        mbar_expect_tx(&full[s], bytes);
         const int k = kb * BK;
-        tma_load_2d(&tmA_hi, &full[s], a_hi(s), k, m0);
-        if (NPROD == 3) tma_load_2d(&tmA_lo, &full[s], a_lo(s), k, m0);
-        tma_load_2d(&tmB_hi, &full[s], b_hi(s), k, n0);
-        if (NPROD == 3) tma_load_2d(&tmB_lo, &full[s], b_lo(s), k, n0);
+        tma_load_2d(v.tm[0], &full[s], a_hi(s), k, v.m0);
+        if (NPROD == 3) tma_load_2d(v.tm[1], &full[s], a_lo(s), k, v.m0);
+        tma_load_2d(v.tm[2], &full[s], b_hi(s), k, v.n0);
+        if (NPROD == 3) tma_load_2d(v.tm[3], &full[s], b_lo(s), k, v.n0);
         issued = it + 1;
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: per K chunk, a fresh accumulation in tensor-memory
     // buffer (chunk parity); three (or one) BF16 products per 16-wide K step
-    constexpr uint32_t idesc = C_::FP8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
     int it = 0, g = 0;
     bool go = true;
     for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
+      const TileView v = view(t);
+      const int num_kb = (v.K + BK - 1) / BK;
+      const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
+      const uint32_t idesc = C_::FP8 ? idesc_e4m3(BM, GROUPED ? v.bn : BN) : idesc_bf16(BM, GROUPED ? v.bn : BN);
       for (int c = 0; go && c < num_chunks; ++c, ++g) {
         const int buf = g & 1;
         const uint32_t use = (uint32_t)(g >> 1);
@@ -506,19 +627,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (!go) break;
         umma_commit(&tfull[buf]);  // chunk complete in buffer buf
-        chunks_committed = g + 1;
       }
     }
   } else if (warp >= 2) {
     // ---- epilogue: every chunk, tensor memory -> FP32 registers (round to
     // nearest); at the end of a tile, registers -> C, coalesced per column
     const int q = warp & 3;          // TMEM lane quarter this warp may access
-    const int h = (warp - 2) >> 2;   // which half of the BN columns
+    const int h = (warp - 2) >> 2;   // which half of the tile's columns
     int g = 0;
     bool go = true;
     for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
-      int m0, n0;
-      tile_coords(t, tiles_m, tiles_n, &m0, &n0);
+      const TileView v = view(t);
+      const int num_kb = (v.K + BK - 1) / BK;
+      const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
+      const int half = GROUPED ? v.bn / 2 : BN / 2;  // columns this warp owns
       float acc[BN / 2];
 #pragma unroll
       for (int u = 0; u < BN / 2; ++u) acc[u] = 0.f;
@@ -527,10 +649,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       const float* sa = nullptr;
       const float* sb = nullptr;
       if (C_::FP8) {
-        sa = p.scaleA + (int64_t)(m0 / FP8_BLOCK) * p.nkb;
-        sb = p.scaleB + (int64_t)((n0 + h * (BN / 2)) / FP8_BLOCK) * p.nkb;
+        sa = p.scaleA + (int64_t)(v.m0 / FP8_BLOCK) * p.nkb;
+        sb = p.scaleB + (int64_t)((v.n0 + h * (BN / 2)) / FP8_BLOCK) * p.nkb;
       }
-      const bool cols_live = n0 + h * (BN / 2) < p.N;
+      const bool cols_live = v.n0 + h * half < v.N;
       for (int c = 0; c < num_chunks; ++c, ++g) {
         const int buf = g & 1;
         const uint32_t use = (uint32_t)(g >> 1);
@@ -542,33 +664,35 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc_fence_after();
         __syncwarp();
-        const uint32_t src = tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * BN + h * (BN / 2);
+        const uint32_t src = tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * BN + h * half;
 #pragma unroll
         for (int i = 0; i < BN / 64; ++i) {
-          uint32_t r[32];
-          tmem_ld_x32(src + i * 32, r);
+          if (i * 32 < half) {
+            uint32_t r[32];
+            tmem_ld_x32(src + i * 32, r);
 #pragma unroll
-          for (int u = 0; u < 32; u += 2) ffma2(acc[i * 32 + u], acc[i * 32 + u + 1], scale, r[u], r[u + 1]);
+            for (int u = 0; u < 32; u += 2) ffma2(acc[i * 32 + u], acc[i * 32 + u + 1], scale, r[u], r[u + 1]);
+          }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
       }
       if (!go) break;
-      const int row = m0 + q * 32 + lane;
-      const int col0 = n0 + h * (BN / 2);
-      if (row < p.M) {
+      const int row = v.m0 + q * 32 + lane;
+      const int col0 = v.n0 + h * half;
+      if (row < v.M) {
         // C in groups of 8 columns: all loads of old C values first, so
         // their DRAM round trips overlap, then the stores (streaming hints:
         // C is touched once and should not displace operand panels in L2)
-        float* cp = p.C + row + (int64_t)col0 * p.ldc;
-        const int ncols = min(BN / 2, p.N - col0);
+        float* cp = v.C + row + (int64_t)col0 * v.ldc;
+        const int ncols = min(half, v.N - col0);
 #pragma unroll
         for (int u0 = 0; u0 < BN / 2; u0 += 8) {
           float old[8];
-          if (p.beta != 0.f) {
+          if (v.beta != 0.f) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) old[u] = (u0 + u < ncols) ? __ldcs(cp + (int64_t)(u0 + u) * p.ldc) : 0.f;
+            for (int u = 0; u < 8; ++u) old[u] = (u0 + u < ncols) ? __ldcs(cp + (int64_t)(u0 + u) * v.ldc) : 0.f;
           }
           float hx[EPI == 2 ? 8 : 1];
           if (EPI == 2) {
@@ -579,10 +703,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             if (u0 + u < ncols) {
-              float v = (p.beta == 0.f) ? p.alpha * acc[u0 + u] : fmaf(p.alpha, acc[u0 + u], p.beta * old[u]);
-              if (EPI == 1) v = tanhf(v);
-              if (EPI == 2) v = v * (1.f - hx[u] * hx[u]);
-              __stcs(cp + (int64_t)(u0 + u) * p.ldc, v);
+              float x = (v.beta == 0.f) ? v.alpha * acc[u0 + u] : fmaf(v.alpha, acc[u0 + u], v.beta * old[u]);
+              if (EPI == 1) x = tanhf(x);
+              if (EPI == 2) x = x * (1.f - hx[u] * hx[u]);
+              __stcs(cp + (int64_t)(u0 + u) * v.ldc, x);
             }
           }
         }
@@ -618,7 +742,6 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
     }
-    (void)chunks_committed;
     __syncthreads();
   }
   if (warp == 1) {
@@ -754,12 +877,13 @@ cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, dim3 grid,
   using C_ = Cfg<MODE>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e =
-        cudaFuncSetAttribute(sgemm_tc<MODE, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(sgemm_tc<MODE, EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C_::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  sgemm_tc<MODE, EPI><<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm);
+  sgemm_tc<MODE, EPI, false><<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm,
+                                                                    GroupParams{nullptr, nullptr, 0});
   return cudaGetLastError();
 }
 
@@ -833,6 +957,250 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
 }
 
 int mode_of_tier(int tier) { return tier == 2 ? 3 : tier == 4 ? 8 : 1; }
+
+// ---- batches of independent instances ----------------------------------------
+template <int MODE>
+cudaError_t launch_batch_kernels(const TcBatch& b, const DeviceStatus& st, cudaStream_t s,
+                                 const LaunchHooks* hooks) {
+  using C_ = Cfg<MODE>;
+  constexpr int NPROD = MODE == 3 ? 3 : 1;
+  if (b.num_split_tiles > 0) {
+    split_batch<NPROD><<<b.num_split_tiles, 256, 0, s>>>(static_cast<const SplitOp*>(b.d_ops),
+                                                         static_cast<const SplitTile*>(b.d_split_tiles));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (b.num_tiles == 0) return cudaSuccess;
+  alignas(64) CUtensorMap unused[4];
+  memset(unused, 0, sizeof unused);
+  TcParams prm{};
+  prm.status = st.dev;
+  GroupParams gp{static_cast<const GroupInst*>(b.d_insts), static_cast<const GroupTile*>(b.d_tiles), b.num_tiles};
+  hook_begin(hooks, s);
+  sgemm_tc<MODE, 0, true><<<b.grid, THREADS, C_::SMEM_BYTES, s>>>(unused[0], unused[1], unused[2], unused[3], prm, gp);
+  hook_end(hooks, s);
+  return cudaGetLastError();
+}
+
+void free_dev(void** p) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+}
+
+template <class T>
+int upload(void** dst, const std::vector<T>& v, std::string* err) {
+  free_dev(dst);
+  if (v.empty()) return 0;
+  if (cudaMalloc(dst, v.size() * sizeof(T)) != cudaSuccess ||
+      cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    *err = "cannot upload a batch table to the device";
+    free_dev(dst);
+    return -1;
+  }
+  return 0;
+}
+
+}  // namespace
+
+std::vector<int> batch_choose_bn(const std::vector<SgemmDesc>& d, int policy) {
+  std::vector<int> bn(d.size(), BN);
+  if (policy == 0) return bn;
+  if (policy == 1) {
+    std::fill(bn.begin(), bn.end(), 128);
+    return bn;
+  }
+  // Model policies: for each instance pick the tile width that minimises
+  // tiles x (columns x padded K + per-tile overhead), the overhead counted
+  // in the same column-K units (policy 2: light, 3: heavy).
+  const double overhead = policy == 2 ? 8192.0 : 65536.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    const double kp = (double)((d[i].K + 127) / 128 * 128);
+    double best = -1;
+    for (int w : {64, 128, 256}) {
+      const double tiles = (double)((d[i].M + BM - 1) / BM) * (double)((d[i].N + w - 1) / w);
+      const double cost = tiles * (w * kp + overhead);
+      if (best < 0 || cost < best - 1e-9) {
+        best = cost;
+        bn[i] = w;
+      }
+    }
+  }
+  return bn;
+}
+
+void batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, std::vector<int>* tiles) {
+  // every output tile of every instance, in decreasing cost (longest first:
+  // the persistent CTAs take them round robin, which balances them)
+  struct T {
+    int64_t cost;
+    int inst, m0, n0;
+  };
+  std::vector<T> v;
+  for (size_t i = 0; i < d.size(); ++i) {
+    if (d[i].M <= 0 || d[i].N <= 0) continue;
+    const int64_t kp = (d[i].K + 127) / 128 * 128;
+    for (int64_t n0 = 0; n0 < d[i].N; n0 += bn[i])
+      for (int64_t m0 = 0; m0 < d[i].M; m0 += BM) v.push_back({kp * bn[i] + 4096, (int)i, (int)m0, (int)n0});
+  }
+  std::stable_sort(v.begin(), v.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
+  tiles->clear();
+  for (auto& t : v) {
+    tiles->push_back(t.inst);
+    tiles->push_back(t.m0);
+    tiles->push_back(t.n0);
+    tiles->push_back(0);
+  }
+}
+
+int tc_batch_build(TcBatch* b, std::string* err) {
+  const int mode = mode_of_tier(b->tier);
+  const int count = (int)b->d.size();
+  if (mode == 8) {
+    *err = "batches run the BF16x3 and BF16 tiers";
+    return -1;
+  }
+  // workspace: each instance's planes, 256-byte aligned, laid end to end
+  if (!b->ws) {
+    b->plane_off.assign(count, 0);
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+      b->plane_off[i] = off;
+      off += ws_layout(b->d[i], mode).total;
+      off = align256(off);
+    }
+    b->ws_bytes = std::max<size_t>(off, 256);
+    if (cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess) {
+      b->ws = nullptr;
+      *err = "cannot allocate the batch's operand planes";
+      return -1;
+    }
+    // split pre-pass tables (independent of the tile widths)
+    std::vector<SplitOp> ops;
+    std::vector<SplitTile> st;
+    for (int i = 0; i < count; ++i) {
+      const SgemmDesc& d = b->d[i];
+      if (d.M <= 0 || d.N <= 0 || d.K <= 0) continue;
+      const WsLayout L = ws_layout(d, mode);
+      uint8_t* w = static_cast<uint8_t*>(b->ws) + b->plane_off[i];
+      const SplitOp a{d.A, d.lda, d.transA ? 0 : 1, (int)d.M, (int)d.K, (int)L.Kp,
+                      reinterpret_cast<__nv_bfloat16*>(w + L.a_hi), reinterpret_cast<__nv_bfloat16*>(w + L.a_lo)};
+      const SplitOp bb{d.B, d.ldb, d.transB ? 1 : 0, (int)d.N, (int)d.K, (int)L.Kp,
+                       reinterpret_cast<__nv_bfloat16*>(w + L.b_hi), reinterpret_cast<__nv_bfloat16*>(w + L.b_lo)};
+      for (const SplitOp& o : {a, bb}) {
+        const int id = (int)ops.size();
+        ops.push_back(o);
+        for (int r0 = 0; r0 < o.rows; r0 += 64)
+          for (int k0 = 0; k0 < o.Kp; k0 += 64) st.push_back({id, r0, k0, 0});
+      }
+    }
+    if (upload(&b->d_ops, ops, err) || upload(&b->d_split_tiles, st, err)) return -1;
+    b->num_split_tiles = (int)st.size();
+  }
+  // tile widths, tensor maps and the tile schedule of the current policy
+  b->bn = batch_choose_bn(b->d, b->policy);
+  std::vector<GroupInst> insts(count);
+  for (int i = 0; i < count; ++i) {
+    const SgemmDesc& d = b->d[i];
+    GroupInst& g = insts[i];
+    memset(&g, 0, sizeof g);
+    g.C = d.C;
+    g.ldc = d.ldc;
+    g.M = (int)d.M;
+    g.N = (int)d.N;
+    g.K = (int)d.K;
+    g.bn = b->bn[i];
+    g.alpha = d.alpha;
+    g.beta = d.beta;
+    if (d.M <= 0 || d.N <= 0 || d.K <= 0) continue;
+    const WsLayout L = ws_layout(d, mode);
+    uint8_t* w = static_cast<uint8_t*>(b->ws) + b->plane_off[i];
+    if (!encode_plane(&g.tm[0], w + L.a_hi, (int)d.M, (int)d.K, (int)L.Kp, BM, 2, err) ||
+        !encode_plane(&g.tm[2], w + L.b_hi, (int)d.N, (int)d.K, (int)L.Kp, g.bn, 2, err))
+      return -1;
+    if (mode == 3) {
+      if (!encode_plane(&g.tm[1], w + L.a_lo, (int)d.M, (int)d.K, (int)L.Kp, BM, 2, err) ||
+          !encode_plane(&g.tm[3], w + L.b_lo, (int)d.N, (int)d.K, (int)L.Kp, g.bn, 2, err))
+        return -1;
+    } else {
+      g.tm[1] = g.tm[0];
+      g.tm[3] = g.tm[2];
+    }
+  }
+  std::vector<int> tiles;
+  batch_schedule(b->d, b->bn, &tiles);
+  std::vector<GroupTile> gt(tiles.size() / 4);
+  for (size_t t = 0; t < gt.size(); ++t) gt[t] = GroupTile{tiles[4 * t], tiles[4 * t + 1], tiles[4 * t + 2], 0};
+  if (upload(&b->d_insts, insts, err) || upload(&b->d_tiles, gt, err)) return -1;
+  b->num_tiles = (int)gt.size();
+  b->grid = std::max(1, std::min(b->num_tiles, num_sms()));
+  // kernel attributes now, so a run can be captured into a CUDA graph
+  cudaError_t e;
+  if (mode == 3)
+    e = cudaFuncSetAttribute(sgemm_tc<3, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<3>::SMEM_BYTES);
+  else
+    e = cudaFuncSetAttribute(sgemm_tc<1, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<1>::SMEM_BYTES);
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return -1;
+  }
+  return 0;
+}
+
+cudaError_t tc_batch_run(const TcBatch& b, const DeviceStatus& st, cudaStream_t s, const LaunchHooks* hooks) {
+  if (mode_of_tier(b.tier) == 3) return launch_batch_kernels<3>(b, st, s, hooks);
+  return launch_batch_kernels<1>(b, st, s, hooks);
+}
+
+int tc_batch_autotune(TcBatch* b, const DeviceStatus& st, cudaStream_t s, int reps, int* best_policy,
+                      double* best_ms, std::string* err) {
+  int best = -1;
+  double best_t = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int pol = 0; pol < 4; ++pol) {
+    b->policy = pol;
+    if (tc_batch_build(b, err)) break;
+    if (tc_batch_run(*b, st, s, nullptr) != cudaSuccess) break;  // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) tc_batch_run(*b, st, s, nullptr);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      *err = "a timed batch run failed";
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double t = ms / std::max(1, reps);
+    if (best < 0 || t < best_t) {
+      best = pol;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) {
+    if (err->empty()) *err = "autotuning failed";
+    return -1;
+  }
+  b->policy = best;
+  if (tc_batch_build(b, err)) return -1;
+  *best_policy = best;
+  *best_ms = best_t;
+  return 0;
+}
+
+void tc_batch_free(TcBatch* b) {
+  free_dev(&b->ws);
+  free_dev(&b->d_ops);
+  free_dev(&b->d_split_tiles);
+  free_dev(&b->d_insts);
+  free_dev(&b->d_tiles);
+}
+
+namespace {
 
 }  // namespace
 

@@ -1,0 +1,51 @@
+"""The batch schedule and tile-width policies on the host (no GPU)."""
+import pytest
+
+import workloads as W
+from paper_1611_00860_gb300 import _lib as H
+
+
+def _grid(M, N, bn):
+    return {(m0, n0) for m0 in range(0, M, 128) for n0 in range(0, N, bn)}
+
+
+@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+def test_schedule_covers_every_tile_once(policy):
+    shapes = W.batched_shapes(64, seed=5)
+    M, N, K = zip(*shapes)
+    bn, tiles = H.hpvm_batch_plan(M, N, K, policy)
+    assert len(tiles) == len(set(tiles))
+    for i, (m, n, _k) in enumerate(shapes):
+        got = {(t[1], t[2]) for t in tiles if t[0] == i}
+        assert got == _grid(m, n, bn[i])
+    # longest tiles first: cost (padded K x width) never increases
+    cost = [((K[t[0]] + 127) // 128 * 128) * bn[t[0]] for t in tiles]
+    assert all(a >= b for a, b in zip(cost, cost[1:]))
+
+
+def test_policies():
+    M, N, K = [300, 300, 2048], [40, 1000, 100], [512, 512, 64]
+    assert H.hpvm_batch_plan(M, N, K, 0)[0] == [256, 256, 256]
+    assert H.hpvm_batch_plan(M, N, K, 1)[0] == [128, 128, 128]
+    bn2 = H.hpvm_batch_plan(M, N, K, 2)[0]
+    assert bn2[0] == 64   # 40 columns: the narrowest tile wastes the least
+    assert bn2[1] == 256  # 1000 columns: wide tiles
+    # a heavier per-tile overhead never asks for more tiles than a lighter one
+    bn3 = H.hpvm_batch_plan(M, N, K, 3)[0]
+    assert all(b3 >= b2 for b2, b3 in zip(bn2, bn3))
+
+
+def test_batched_workload_plan():
+    shapes = W.batched_shapes()  # 512 instances, M, N, K log-uniform in [32, 2048]
+    assert len(shapes) == 512
+    assert all(32 <= x <= 2048 for s in shapes for x in s)
+    M, N, K = zip(*shapes)
+    _, tiles = H.hpvm_batch_plan(M, N, K, 2)
+    assert len(tiles) == sum(len(_grid(m, n, b)) for (m, n, _), b in zip(shapes, H.hpvm_batch_plan(M, N, K, 2)[0]))
+
+
+def test_bad_policy_and_shapes():
+    with pytest.raises(H.HpvmError):
+        H.hpvm_batch_plan([1], [1], [1], 7)
+    with pytest.raises(H.HpvmError):
+        H.hpvm_batch_plan([-1], [1], [1], 0)
