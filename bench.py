@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--n", type=int, default=N_SIZE, help="M = N = K")
+    ap.add_argument("--size", type=int, default=N_SIZE, help="M = N = K of the headline workload")
     ap.add_argument("--fp32-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-fp8", action="store_true", help="skip the 16384 FP8 workload section")
     ap.add_argument("--fp8-n", type=int, default=16384)
     ap.add_argument("--no-chain", action="store_true", help="skip the streamed chain section")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances section")
     return ap.parse_args()
 
 
@@ -68,6 +69,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(ms: float, device: str) -> float:
+    """The slowest rank's time (every rank gets it); the local time when the
+    job has one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(flop_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job TFLOP/s: the work of all ranks over the slowest rank's time
+    (weak scaling: every rank runs its own replica)."""
+    return flop_per_rank * world / (ms * 1e-3) / 1e12
 
 
 def load_peaks() -> dict:
@@ -323,13 +342,88 @@ def chain_section(args, H, W, torch, local, world, barrier):
     return out
 
 
+def batch_section(args, H, W, torch, local, world, rank, barrier):
+    """512 independent sgemm DFG instances (M, N, K log-uniform in [32, 2048],
+    BF16x3 leaves): one autotuned batch (batched split pre-pass + grouped
+    persistent leaf) replayed from a CUDA graph, against one hpvm_launch per
+    instance on the same inputs."""
+    from paper_1611_00860_gb300.batch import BatchDFG
+    from paper_1611_00860_gb300.sgemm import SgemmDFG
+    shapes = W.batched_shapes()
+    probs = [W.sgemm_problem(m, n, k, seed=20000 + i, alpha=1.0, beta=0.0) for i, (m, n, k) in enumerate(shapes)]
+    flop = sum(2.0 * m * n * k for m, n, k in shapes)
+    dev = [tuple(t.to(f"cuda:{local}") for t in (p.A, p.B, p.C)) for p in probs]
+    stream = torch.cuda.current_stream(local)
+    b = BatchDFG(local)
+    b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=-1)
+    best, tuned_ms = b.autotune(3)
+    graph = b.capture()
+    reps = 20
+    graph.replay()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        graph.replay()
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / reps
+    out = {"workload": "512 sgemm DFG instances, M,N,K log-uniform in [32,2048] (seed 2), N(0,1), "
+                       "alpha=1, beta=0, BF16x3 leaves", "unit": "TFLOP/s",
+           "useful_tflop": flop / 1e12, "batch": {
+               "value": flop * world / (ms * 1e-3) / 1e12, "ms_per_batch": ms,
+               "launches": 2, "path": "hpvm_batch_prepare + hpvm_batch_autotune, hpvm_batch_run captured "
+                                      "in a CUDA graph, replayed",
+               "autotuned_policy": best, "info": b.info()}}
+    # one launch per instance (each: split of A, split of B, leaf)
+    s = SgemmDFG(local)
+    args_list = [s.args_for(p.M, p.N, p.K, A, p.lda, B, p.ldb, C, p.ldc, p.alpha, p.beta, p.transA,
+                            p.transB, tier=H.HPVM_TIER_BF16X3) for p, (A, B, C) in zip(probs, dev)]
+    for a in args_list:
+        s.ensure_workspace(a)
+    for a in args_list:
+        s.wait(s.launch(a))
+    barrier()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    gs = [s.launch(a) for a in args_list]
+    ev1.record(stream)
+    barrier()
+    wall = (time.perf_counter() - t0) * 1e3
+    for g in gs:
+        s.wait(g)
+    ms1 = ev0.elapsed_time(ev1)
+    out["one_launch_per_instance"] = {"value": flop * world / (ms1 * 1e-3) / 1e12, "ms_per_batch": ms1,
+                                      "host_ms": wall, "launches": 3 * len(probs)}
+    out["speedup"] = ms1 / ms
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import sgemm as O
+        # error of the batch on the 32 smallest instances (the oracle computes them whole)
+        order = sorted(range(len(probs)), key=lambda i: probs[i].M * probs[i].N * probs[i].K)[:32]
+        for (_, _, C) in dev:
+            C.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        worst = 0.0
+        for i in order:
+            p = probs[i]
+            got = W.col_major(dev[i][2].cpu(), p.M, p.N, p.ldc).double().numpy()
+            worst = max(worst, O.normwise_rel_err(got, O.sgemm_f64(p)))
+        out["rel_err_worst_of_32_smallest"] = worst
+    s.close()
+    b.close()
+    del dev
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import workloads as W
     from oracle import sgemm as O
-    p = W.large_dfg_problem(args.n)
+    p = W.large_dfg_problem(args.size)
     blocks = W.sample_blocks(p.M, p.N, bs=TILE_BLOCK, count=max(16, args.steps + args.warmup))
     seq = [blocks[i % len(blocks)] for i in range(args.steps + args.warmup)]
     for (i0, j0) in seq[:args.warmup]:
@@ -373,7 +467,7 @@ def main():
     from paper_1611_00860_gb300.sgemm import SgemmDFG
 
     peaks = load_peaks()
-    n = args.n
+    n = args.size
     p = W.large_dfg_problem(n)
     flop = 2.0 * p.M * p.N * p.K
     A, B, C0 = (t.to(f"cuda:{local}") for t in (p.A, p.B, p.C))
@@ -416,10 +510,7 @@ def main():
             dfg.wait(g)
         clk = sampler.stop() if sampler else None
         ms = ev0.elapsed_time(ev1)
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), kms / max(1, klaunch), kernels, clk
+        return max_over_ranks(ms, f"cuda:{local}"), kms / max(1, klaunch), kernels, clk
 
     # 1) correctness run of both tiers on a fresh C (checked below against the oracle)
     C_bf = C0.clone()
@@ -430,7 +521,7 @@ def main():
     # 2) timed split-BF16x3 DFG (headline)
     ms_total, kern_ms, launches, clocks = timed(H.HPVM_TIER_BF16X3, args.steps, args.warmup, C, True)
     ms_step = ms_total / args.steps
-    value = flop * world * args.steps / (ms_total * 1e-3) / 1e12
+    value = job_rate(flop * args.steps, world, ms_total)
     tensor_flop = 3 * flop
     achieved = tensor_flop / (kern_ms * 1e-3) / 1e12
     src_hash = kernel_source_hash()
@@ -493,7 +584,10 @@ def main():
                "blocks": len(refs), "metric": "normwise ||C-C_ref||_F/||C_ref||_F over sampled blocks",
                "tolerance": 5e-6}
 
-    # 6) the streamed chain (training step and streamed forward)
+    # 6) batches of independent instances, and the streamed chain
+    batch = None
+    if not args.no_batch:
+        batch = batch_section(args, H, W, torch, local, world, rank, barrier)
     chain = None
     if not args.no_chain:
         chain = chain_section(args, H, W, torch, local, world, barrier)
@@ -518,7 +612,7 @@ def main():
                        "l2": "inputs larger than L2 (768 MiB FP32 operands + 512 MiB split planes); no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "rel_err": err, "fp32_cuda_core": fp32,
-            "fp8_workload": fp8, "chain_workload": chain,
+            "fp8_workload": fp8, "chain_workload": chain, "batched_workload": batch,
         }
         print(json.dumps(line), flush=True)
     dfg.close()

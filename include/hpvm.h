@@ -392,6 +392,15 @@ HPVM_API int hpvm_batch_free(hpvm_batch* batch);
 HPVM_API int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, const int64_t* K, int policy,
                              int32_t* bn, int32_t* tiles, int64_t tile_cap, int64_t* num_tiles);
 
+/* ---- failure detection self-test ---------------------------------------
+ * No paper counterpart. Runs one kernel whose single mbarrier wait nothing
+ * ever satisfies, through the same bounded wait the leaf kernels use, with
+ * a limit of limit_ms (1..10000). The wait gives up, the kernel records it
+ * in the context's status word and returns; this call waits for it and
+ * returns what a graph's hpvm_wait would: HPVM_ERR_DEVICE_FAULT. No copy,
+ * MMA or tensor memory is involved and the context stays usable. */
+HPVM_API int hpvm_selftest_wait_timeout(hpvm_ctx* ctx, int64_t limit_ms, void* cuda_stream);
+
 /* Thread-local message of the last failed call ("" if none). */
 HPVM_API const char* hpvm_last_error(void);
 /* ABI version (major * 100 + minor). */

@@ -153,6 +153,7 @@ def _load() -> ctypes.CDLL:
         "hpvm_batch_plan": (I, [I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64), I, ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_int32), I64, ctypes.POINTER(ctypes.c_int64)]),
+        "hpvm_selftest_wait_timeout": (I, [P, I64, P]),
         "hpvm_last_error": (ctypes.c_char_p, []),
         "hpvm_version": (I, []),
     }
@@ -366,6 +367,11 @@ def hpvm_batch_plan(M, N, K, policy: int):
     tiles = (ctypes.c_int32 * max(4 * cnt.value, 1))()
     _check(LIB.hpvm_batch_plan(n, Ma, Na, Ka, int(policy), bn, tiles, cnt.value, ctypes.byref(cnt)))
     return list(bn)[:n], [tuple(tiles[4 * i:4 * i + 3]) for i in range(cnt.value)]
+
+
+def hpvm_selftest_wait_timeout(ctx: int, limit_ms: int, cuda_stream: int = 0) -> None:
+    """Raises HpvmError(HPVM_ERR_DEVICE_FAULT) when the bounded wait gave up, as it must."""
+    _check(LIB.hpvm_selftest_wait_timeout(ctx, int(limit_ms), cuda_stream or None))
 
 
 def hpvm_last_error() -> str:

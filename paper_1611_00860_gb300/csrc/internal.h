@@ -116,6 +116,8 @@ cudaError_t tc_batch_run(const TcBatch& b, const DeviceStatus& st, cudaStream_t 
 int tc_batch_autotune(TcBatch* b, const DeviceStatus& st, cudaStream_t s, int reps, int* best_policy,
                       double* best_ms, std::string* err);
 void tc_batch_free(TcBatch* b);
+// One kernel whose single bounded wait can never be satisfied (tc_leaf.cu).
+cudaError_t launch_wait_selftest(const DeviceStatus& st, uint64_t limit_ns, cudaStream_t s);
 
 // Sets the calling thread's hpvm_last_error() message (cleared for HPVM_OK)
 // and returns `code` (runtime.cpp).

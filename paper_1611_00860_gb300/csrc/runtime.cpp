@@ -1316,6 +1316,20 @@ int hpvm_untrack_mem(hpvm_ctx* ctx, void* p) {
   return fail(HPVM_ERR_INVALID_ARG, "pointer is not the start of a tracked region");
 }
 
+int hpvm_selftest_wait_timeout(hpvm_ctx* ctx, int64_t limit_ms, void* cuda_stream) {
+  if (!ctx) return fail(HPVM_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->device < 0) return fail(HPVM_ERR_NO_DEVICE, "host-only context");
+  if (limit_ms < 1 || limit_ms > 10000) return fail(HPVM_ERR_INVALID_ARG, "limit must be 1..10000 ms");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = hpvm::launch_wait_selftest(ctx->status, (uint64_t)limit_ms * 1000000ull, s);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test wait");
+  int rc = check_status(ctx);
+  return rc == HPVM_OK ? ok() : rc;
+}
+
 // ---- batches -----------------------------------------------------------------
 namespace {
 uint64_t batch_signature(const std::vector<hpvm::SgemmDesc>& d, int tier) {

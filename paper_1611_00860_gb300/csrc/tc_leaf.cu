@@ -55,7 +55,7 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per bounded wait
 constexpr int FP8_BLOCK = 128;      // FP8 scale block (rows x K) of each operand
 
 // status bits (DeviceStatus word)
-constexpr int ST_PRODUCER = 1, ST_MMA = 2, ST_EPILOGUE = 4, ST_DRAIN = 8;
+constexpr int ST_PRODUCER = 1, ST_MMA = 2, ST_EPILOGUE = 4, ST_DRAIN = 8, ST_SELFTEST = 16;
 
 // Leaf modes: 3 = BF16x3 split (hi*hi + hi*lo + lo*hi), 1 = BF16, 8 = FP8
 // E4M3 with one FP32 scale per 128 x 128 block of each operand.
@@ -123,14 +123,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // false) when another role raised the abort flag or after WAIT_LIMIT_NS, in
 // which case it records `code` in the status word and raises the flag.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* status, int code) {
+                                          int* status, int code, uint64_t limit_ns = WAIT_LIMIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t n = 1;; ++n) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((n & 63u) == 0) {
       if (*abort_flag) return false;
-      if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+      if (globaltimer() - t0 > limit_ns) {
         if (status) atomicOr_system(status, code);
         *abort_flag = 1;
         return false;
@@ -750,6 +750,22 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// A wait that nothing satisfies: the bounded wait the leaf kernels use must
+// give up after limit_ns, record ST_SELFTEST in the status word and let the
+// kernel return (no copy, MMA or tensor memory is involved).
+__global__ void wait_selftest(int* status, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0, &abort_flag, status, ST_SELFTEST, limit_ns);
+  __syncthreads();
+}
+
 // ---- host side ---------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1190,6 +1206,11 @@ int tc_batch_autotune(TcBatch* b, const DeviceStatus& st, cudaStream_t s, int re
   *best_policy = best;
   *best_ms = best_t;
   return 0;
+}
+
+cudaError_t launch_wait_selftest(const DeviceStatus& st, uint64_t limit_ns, cudaStream_t s) {
+  wait_selftest<<<1, 32, 0, s>>>(st.dev, limit_ns);
+  return cudaGetLastError();
 }
 
 void tc_batch_free(TcBatch* b) {

@@ -179,3 +179,31 @@ def test_wait_timeout_leaves_handle_valid(dfg):
     if not finished_early:
         H.hpvm_wait(g, 120000)
     torch.cuda.synchronize()
+
+
+def test_bounded_wait_gives_up_and_context_survives(cuda_device):
+    # a wait nothing satisfies: the bounded wait must expire after ~200 ms,
+    # be reported as a device fault, and leave the context usable
+    import time
+    ctx = H.hpvm_init(0)
+    try:
+        t0 = time.perf_counter()
+        with pytest.raises(H.HpvmError) as e:
+            H.hpvm_selftest_wait_timeout(ctx, 200)
+        dt = time.perf_counter() - t0
+        assert e.value.code == H.HPVM_ERR_DEVICE_FAULT
+        assert 0.19 <= dt < 10.0
+        # the status word was cleared by the report: a real launch now succeeds
+        nodes = build_sgemm_graph(ctx)
+        p = W.sgemm_problem(64, 48, 32, seed=3)
+        A, B, C = (t.cuda() for t in (p.A, p.B, p.C))
+        a = make_args(p.M, p.N, p.K, A.data_ptr(), A.numel() * 4, p.lda, B.data_ptr(), B.numel() * 4, p.ldb,
+                      C.data_ptr(), C.numel() * 4, p.ldc, p.alpha, p.beta, p.transA, p.transB,
+                      H.HPVM_TIER_BF16X3)
+        ws = torch.empty(H.hpvm_workspace_size(ctx, nodes["root"], a), dtype=torch.uint8, device="cuda")
+        H.hpvm_set_workspace(ctx, ws.data_ptr(), ws.numel())
+        H.hpvm_wait(H.hpvm_launch(ctx, nodes["root"], a), 60000)
+        got = W.col_major(C.cpu(), p.M, p.N, p.ldc).double().numpy()
+        assert O.normwise_rel_err(got, O.sgemm_f64(p)) <= 5e-6
+    finally:
+        H.hpvm_cleanup(ctx)
