@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--fp8-n", type=int, default=16384)
     ap.add_argument("--no-chain", action="store_true", help="skip the streamed chain section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances section")
+    ap.add_argument("--only", choices=["chain", "batch", "fp8"], default=None,
+                    help="run one workload section alone and print its JSON (for profiling); "
+                         "no headline line")
     return ap.parse_args()
 
 
@@ -467,6 +470,28 @@ def main():
     from paper_1611_00860_gb300.sgemm import SgemmDFG
 
     peaks = load_peaks()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(local)
+
+    if args.only:
+        out = None
+        if args.only == "chain":
+            out = chain_section(args, H, W, torch, local, world, barrier)
+        elif args.only == "batch":
+            out = batch_section(args, H, W, torch, local, world, rank, barrier)
+        else:
+            dfg = SgemmDFG(local)
+            out = fp8_section(args, dfg, H, W, torch, local, peaks, world, rank, barrier)
+            dfg.close()
+        if rank == 0:
+            print(json.dumps({"section": args.only, **out}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     n = args.size
     p = W.large_dfg_problem(n)
     flop = 2.0 * p.M * p.N * p.K
@@ -478,11 +503,6 @@ def main():
     def launch_args(tier, Cbuf):
         return dfg.args_for(p.M, p.N, p.K, A, p.lda, B, p.ldb, Cbuf, p.ldc, p.alpha, p.beta,
                             p.transA, p.transB, tier=tier)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(local)
 
     def timed(tier, steps, warmup, Cbuf, clocks=False):
         a = launch_args(tier, Cbuf)

@@ -45,7 +45,17 @@ constexpr int BM = 128;             // tile rows (M) = tensor-memory lanes
 constexpr int BN = 256;             // tile columns (N) = accumulator columns
 constexpr int SLAB_ROW_BYTES = 64;  // one K slab row: 64 bytes (64-byte swizzle)
 constexpr int EPI_WARPS = 8;        // two per tensor-memory lane quarter
-constexpr int THREADS = 64 + EPI_WARPS * 32;  // producer, MMA, epilogue warps
+constexpr int EPI_WARP0 = 4;        // warpgroup 0: producer, MMA, two idle warps
+constexpr int THREADS = EPI_WARP0 * 32 + EPI_WARPS * 32;  // 3 warpgroups
+// Register split (setmaxnreg): the block is launched with THREADS x
+// LAUNCH_REGS registers (the cap __launch_bounds__(THREADS, 1) gives); the
+// control warpgroup gives registers back and the two epilogue warpgroups,
+// which hold a 128-column FP32 running sum per thread, take them.
+constexpr int LAUNCH_REGS = 168;
+constexpr int CTRL_REGS = 56;
+constexpr int EPI_REGS = 224;
+static_assert(EPI_WARP0 * 32 * CTRL_REGS + EPI_WARPS * 32 * EPI_REGS <= THREADS * LAUNCH_REGS,
+              "register split exceeds the launch's registers");
 constexpr uint32_t TMEM_COLS = 2 * BN;        // two FP32 BM x BN chunk buffers
 constexpr int GROUP_N = 8;          // column tiles per rasterisation group
 constexpr uint32_t A_SLAB = BM * SLAB_ROW_BYTES;  // bytes of one A plane slab
@@ -68,15 +78,18 @@ struct Cfg {
   static constexpr int MMA_K = 32 / ELEM_BYTES;           // K per tcgen05.mma
   // K chunk accumulated afresh in tensor memory and then added to FP32
   // registers with round-to-nearest (the tensor-core accumulation
-  // truncates): 128 elements; for FP8 this is exactly one scale block, and
-  // the chunk is multiplied by its two block scales when it is added.
-  static constexpr int KC_SLABS = 128 / BK;
+  // truncates): 128 elements for BF16x3, whose 5e-6 bound the truncation
+  // over a long K would break; for FP8 this is exactly one scale block, and
+  // the chunk is multiplied by its two block scales when it is added. Plain
+  // BF16 (bound 1e-2) accumulates all of K in tensor memory: one chunk per
+  // tile, read out once.
+  static constexpr int KC_SLABS = MODE == 1 ? (1 << 24) : 128 / BK;
   static constexpr uint32_t STAGE_BYTES = PLANES * (A_SLAB + B_SLAB);
   static constexpr int STAGES = (int)((SMEM_BUDGET - 2048) / STAGE_BYTES) > 8
                                     ? 8 : (int)((SMEM_BUDGET - 2048) / STAGE_BYTES);
   static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
   static_assert(2 * STAGES * 8 + 4 * 8 + 8 <= 512, "barrier area");
-  static_assert(KC_SLABS * BK == 128, "chunk of 128 K elements");
+  static_assert(MODE == 1 || KC_SLABS * BK == 128, "chunk of 128 K elements");
 };
 
 struct TcParams {
@@ -220,6 +233,38 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
         "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// All THREADS threads of the CTA, arriving from different branches: a
+// named barrier without .aligned, which may be reached from divergent code.
+__device__ __forceinline__ void cta_barrier_all() {
+  asm volatile("barrier.sync 1, %0;" ::"n"(THREADS) : "memory");
+}
+
+// Two 32-column tensor-memory loads in flight before one wait.
+__device__ __forceinline__ void tmem_ld_2x32(uint32_t taddr0, uint32_t taddr1, uint32_t (&r)[32],
+                                             uint32_t (&s)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr0));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]),
+        "=r"(s[8]), "=r"(s[9]), "=r"(s[10]), "=r"(s[11]), "=r"(s[12]), "=r"(s[13]), "=r"(s[14]),
+        "=r"(s[15]), "=r"(s[16]), "=r"(s[17]), "=r"(s[18]), "=r"(s[19]), "=r"(s[20]), "=r"(s[21]),
+        "=r"(s[22]), "=r"(s[23]), "=r"(s[24]), "=r"(s[25]), "=r"(s[26]), "=r"(s[27]), "=r"(s[28]),
+        "=r"(s[29]), "=r"(s[30]), "=r"(s[31])
+      : "r"(taddr1));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -545,95 +590,135 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
   // bookkeeping for the drain after an abort
   int issued = 0;     // producer: slabs requested (ring position)
   int committed = 0;  // MMA: slabs whose MMAs were committed (ring position)
 
-  if (warp == 0 && lane == 0) {
-    // ---- producer: TMA loads of the operand slabs into the ring
-    if (!GROUPED) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA_hi)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
-    }
-    int it = 0;
-    bool go = true;
-    for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
-      const TileView v = view(t);
-      const int num_kb = (v.K + BK - 1) / BK;
-      const uint32_t bytes = C_::PLANES * (A_SLAB + (uint32_t)v.bn * SLAB_ROW_BYTES);
-      for (int kb = 0; kb < num_kb; ++kb, ++it) {
-        const int s = it % S;
-        const uint32_t ph = (it / S) & 1;
-        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, p.status, ST_PRODUCER)) {
-          go = false;
-          break;
-        }
-        mbar_expect_tx(&full[s], bytes);
-        const int k = kb * BK;
-        tma_load_2d(v.tm[0], &full[s], a_hi(s), k, v.m0);
-        if (NPROD == 3) tma_load_2d(v.tm[1], &full[s], a_lo(s), k, v.m0);
-        tma_load_2d(v.tm[2], &full[s], b_hi(s), k, v.n0);
-        if (NPROD == 3) tma_load_2d(v.tm[3], &full[s], b_lo(s), k, v.n0);
-        issued = it + 1;
+  if (warp < EPI_WARP0) {
+    // control warpgroup: its registers go to the epilogue warpgroups
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(CTRL_REGS));
+    if (warp == 0 && lane == 0) {
+      // ---- producer: TMA loads of the operand slabs into the ring
+      if (!GROUPED) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA_hi)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
       }
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: per K chunk, a fresh accumulation in tensor-memory
-    // buffer (chunk parity); three (or one) BF16 products per 16-wide K step
-    int it = 0, g = 0;
-    bool go = true;
-    for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
-      const TileView v = view(t);
-      const int num_kb = (v.K + BK - 1) / BK;
-      const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
-      const uint32_t idesc = C_::FP8 ? idesc_e4m3(BM, GROUPED ? v.bn : BN) : idesc_bf16(BM, GROUPED ? v.bn : BN);
-      for (int c = 0; go && c < num_chunks; ++c, ++g) {
-        const int buf = g & 1;
-        const uint32_t use = (uint32_t)(g >> 1);
-        if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag, p.status, ST_MMA)) {
-          go = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dst = tmem + buf * BN;
-        const int kb_end = min(num_kb, (c + 1) * KC_SLABS);
-        for (int kb = c * KC_SLABS; kb < kb_end; ++kb, ++it) {
+      int it = 0;
+      bool go = true;
+      for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
+        const TileView v = view(t);
+        const int num_kb = (v.K + BK - 1) / BK;
+        const uint32_t bytes = C_::PLANES * (A_SLAB + (uint32_t)v.bn * SLAB_ROW_BYTES);
+        for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1;
-          if (!mbar_wait(&full[s], ph, abort_flag, p.status, ST_MMA)) {
+          if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, p.status, ST_PRODUCER)) {
+            go = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], bytes);
+          const int k = kb * BK;
+          tma_load_2d(v.tm[0], &full[s], a_hi(s), k, v.m0);
+          if (NPROD == 3) tma_load_2d(v.tm[1], &full[s], a_lo(s), k, v.m0);
+          tma_load_2d(v.tm[2], &full[s], b_hi(s), k, v.n0);
+          if (NPROD == 3) tma_load_2d(v.tm[3], &full[s], b_lo(s), k, v.n0);
+          issued = it + 1;
+        }
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ---- MMA issuer: per K chunk, a fresh accumulation in tensor-memory
+      // buffer (chunk parity); three (or one) BF16 products per 16-wide K step
+      int it = 0, g = 0;
+      bool go = true;
+      for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
+        const TileView v = view(t);
+        const int num_kb = (v.K + BK - 1) / BK;
+        const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
+        const uint32_t idesc = C_::FP8 ? idesc_e4m3(BM, GROUPED ? v.bn : BN) : idesc_bf16(BM, GROUPED ? v.bn : BN);
+        for (int c = 0; go && c < num_chunks; ++c, ++g) {
+          const int buf = g & 1;
+          const uint32_t use = (uint32_t)(g >> 1);
+          if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag, p.status, ST_MMA)) {
             go = false;
             break;
           }
           tc_fence_after();
-          const uint32_t ah = smem_u32(a_hi(s)), al = smem_u32(a_lo(s));
-          const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_lo(s));
-#pragma unroll
-          for (int kk = 0; kk < BK / MMA_K; ++kk) {
-            const uint32_t off = kk * MMA_K * C_::ELEM_BYTES;  // bytes along the 64-byte row
-            const uint32_t acc = (kb == c * KC_SLABS && kk == 0) ? 0u : 1u;
-            if (C_::FP8) {
-              umma_e4m3(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, acc);
-            } else if (NPROD == 3) {
-              umma_bf16(dst, sdesc_k_sw64(al + off), sdesc_k_sw64(bh + off), idesc, acc);
-              umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bl + off), idesc, 1u);
-              umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, 1u);
-            } else {
-              umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, acc);
+          const uint32_t dst = tmem + buf * BN;
+          const int kb_end = min(num_kb, (c + 1) * KC_SLABS);
+          for (int kb = c * KC_SLABS; kb < kb_end; ++kb, ++it) {
+            const int s = it % S;
+            const uint32_t ph = (it / S) & 1;
+            if (!mbar_wait(&full[s], ph, abort_flag, p.status, ST_MMA)) {
+              go = false;
+              break;
             }
+            tc_fence_after();
+            const uint32_t ah = smem_u32(a_hi(s)), al = smem_u32(a_lo(s));
+            const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_lo(s));
+  #pragma unroll
+            for (int kk = 0; kk < BK / MMA_K; ++kk) {
+              const uint32_t off = kk * MMA_K * C_::ELEM_BYTES;  // bytes along the 64-byte row
+              const uint32_t acc = (kb == c * KC_SLABS && kk == 0) ? 0u : 1u;
+              if (C_::FP8) {
+                umma_e4m3(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, acc);
+              } else if (NPROD == 3) {
+                umma_bf16(dst, sdesc_k_sw64(al + off), sdesc_k_sw64(bh + off), idesc, acc);
+                umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bl + off), idesc, 1u);
+                umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, 1u);
+              } else {
+                umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, acc);
+              }
+            }
+            umma_commit(&empty[s]);  // frees the slab once these MMAs have read it
+            committed = it + 1;
           }
-          umma_commit(&empty[s]);  // frees the slab once these MMAs have read it
-          committed = it + 1;
+          if (!go) break;
+          umma_commit(&tfull[buf]);  // chunk complete in buffer buf
         }
-        if (!go) break;
-        umma_commit(&tfull[buf]);  // chunk complete in buffer buf
       }
     }
-  } else if (warp >= 2) {
+    __syncwarp();
+    tc_fence_before();
+    cta_barrier_all();  // every role is done
+    tc_fence_after();
+    if (*abort_flag) {
+      // Drain what this CTA itself started before returning (bounded waits):
+      // TMA loads not yet consumed, and the MMAs of the last commit.
+      if (warp == 0 && lane == 0) {
+        for (int it = (issued > S ? issued - S : 0); it < issued; ++it) {
+          const int s = it % S;
+          const uint64_t t0 = globaltimer();
+          while (!mbar_try_wait(&full[s], (it / S) & 1)) {
+            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+              if (p.status) atomicOr_system(p.status, ST_DRAIN);
+              break;
+            }
+          }
+        }
+      }
+      if (warp == 1 && lane == 0 && committed > 0) {
+        const int it = committed - 1;
+        const int s = it % S;
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&empty[s], (it / S) & 1)) {
+          if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+            if (p.status) atomicOr_system(p.status, ST_DRAIN);
+            break;
+          }
+        }
+      }
+    }
+    __syncwarp();  // warp 1: the drain of lane 0 ends before the dealloc
+    if (warp == 1) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(EPI_REGS));
     // ---- epilogue: every chunk, tensor memory -> FP32 registers (round to
     // nearest); at the end of a tile, registers -> C, coalesced per column
     const int q = warp & 3;          // TMEM lane quarter this warp may access
-    const int h = (warp - 2) >> 2;   // which half of the tile's columns
+    const int h = (warp - EPI_WARP0) >> 2;  // which half of the tile's columns
     int g = 0;
     bool go = true;
     for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
@@ -666,8 +751,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
         const uint32_t src = tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * BN + h * half;
 #pragma unroll
-        for (int i = 0; i < BN / 64; ++i) {
-          if (i * 32 < half) {
+        for (int i = 0; i < BN / 64; i += 2) {
+          // 64 columns per step, two loads in flight (half is a multiple of 32;
+          // a 32-wide half of a 64-column tile takes the single-load path)
+          if (i * 32 + 32 < half) {
+            uint32_t r[32], r2[32];
+            tmem_ld_2x32(src + i * 32, src + i * 32 + 32, r, r2);
+#pragma unroll
+            for (int u = 0; u < 32; u += 2) ffma2(acc[i * 32 + u], acc[i * 32 + u + 1], scale, r[u], r[u + 1]);
+#pragma unroll
+            for (int u = 0; u < 32; u += 2)
+              ffma2(acc[i * 32 + 32 + u], acc[i * 32 + 33 + u], scale, r2[u], r2[u + 1]);
+          } else if (i * 32 < half) {
             uint32_t r[32];
             tmem_ld_x32(src + i * 32, r);
 #pragma unroll
@@ -682,26 +777,27 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int row = v.m0 + q * 32 + lane;
       const int col0 = v.n0 + h * half;
       if (row < v.M) {
-        // C in groups of 8 columns: all loads of old C values first, so
+        // C in groups of CG columns: all loads of old C values first, so
         // their DRAM round trips overlap, then the stores (streaming hints:
         // C is touched once and should not displace operand panels in L2)
         float* cp = v.C + row + (int64_t)col0 * v.ldc;
         const int ncols = min(half, v.N - col0);
+        constexpr int CG = EPI == 2 ? 4 : 8;  // the tanh adjoint also reads H
 #pragma unroll
-        for (int u0 = 0; u0 < BN / 2; u0 += 8) {
-          float old[8];
+        for (int u0 = 0; u0 < BN / 2; u0 += CG) {
+          float old[CG];
           if (v.beta != 0.f) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) old[u] = (u0 + u < ncols) ? __ldcs(cp + (int64_t)(u0 + u) * v.ldc) : 0.f;
+            for (int u = 0; u < CG; ++u) old[u] = (u0 + u < ncols) ? __ldcs(cp + (int64_t)(u0 + u) * v.ldc) : 0.f;
           }
-          float hx[EPI == 2 ? 8 : 1];
+          float hx[EPI == 2 ? CG : 1];
           if (EPI == 2) {
             const float* hp = p.aux + row + (int64_t)col0 * p.ldaux;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) hx[u] = (u0 + u < ncols) ? __ldcs(hp + (int64_t)(u0 + u) * p.ldaux) : 0.f;
+            for (int u = 0; u < CG; ++u) hx[u] = (u0 + u < ncols) ? __ldcs(hp + (int64_t)(u0 + u) * p.ldaux) : 0.f;
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < CG; ++u) {
             if (u0 + u < ncols) {
               float x = (v.beta == 0.f) ? v.alpha * acc[u0 + u] : fmaf(v.alpha, acc[u0 + u], v.beta * old[u]);
               if (EPI == 1) x = tanhf(x);
@@ -712,41 +808,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
     }
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  if (*abort_flag) {
-    // Drain what this CTA itself started before returning (bounded waits):
-    // TMA loads not yet consumed, and the MMAs of the last commit.
-    if (warp == 0 && lane == 0) {
-      for (int it = (issued > S ? issued - S : 0); it < issued; ++it) {
-        const int s = it % S;
-        const uint64_t t0 = globaltimer();
-        while (!mbar_try_wait(&full[s], (it / S) & 1)) {
-          if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-            if (p.status) atomicOr_system(p.status, ST_DRAIN);
-            break;
-          }
-        }
-      }
-    }
-    if (warp == 1 && lane == 0 && committed > 0) {
-      const int it = committed - 1;
-      const int s = it % S;
-      const uint64_t t0 = globaltimer();
-      while (!mbar_try_wait(&empty[s], (it / S) & 1)) {
-        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-          if (p.status) atomicOr_system(p.status, ST_DRAIN);
-          break;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    tc_fence_before();
+    cta_barrier_all();
   }
 }
 
@@ -888,6 +951,19 @@ cudaError_t launch_quant(const float* X, int64_t ld, bool mmajor, int rows, int 
   return cudaGetLastError();
 }
 
+// The leaf's register split (setmaxnreg) moves registers between the
+// warpgroups of a block; it only balances when the block was launched with
+// LAUNCH_REGS registers per thread. A build that gave the kernel fewer would
+// make setmaxnreg.inc wait for registers that never come, so it is refused.
+template <typename Kern>
+cudaError_t check_register_split(Kern* kernel) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  if (a.numRegs < LAUNCH_REGS || a.maxThreadsPerBlock < THREADS) return cudaErrorInvalidConfiguration;
+  return cudaSuccess;
+}
+
 template <int MODE, int EPI>
 cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, dim3 grid, cudaStream_t s) {
   using C_ = Cfg<MODE>;
@@ -895,6 +971,7 @@ cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, dim3 grid,
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(sgemm_tc<MODE, EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C_::SMEM_BYTES);
+    if (e == cudaSuccess) e = check_register_split(sgemm_tc<MODE, EPI, false>);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -1151,12 +1228,15 @@ int tc_batch_build(TcBatch* b, std::string* err) {
   b->grid = std::max(1, std::min(b->num_tiles, num_sms()));
   // kernel attributes now, so a run can be captured into a CUDA graph
   cudaError_t e;
-  if (mode == 3)
+  if (mode == 3) {
     e = cudaFuncSetAttribute(sgemm_tc<3, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg<3>::SMEM_BYTES);
-  else
+    if (e == cudaSuccess) e = check_register_split(sgemm_tc<3, 0, true>);
+  } else {
     e = cudaFuncSetAttribute(sgemm_tc<1, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg<1>::SMEM_BYTES);
+    if (e == cudaSuccess) e = check_register_split(sgemm_tc<1, 0, true>);
+  }
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
     return -1;
