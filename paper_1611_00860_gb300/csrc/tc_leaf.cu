@@ -43,7 +43,6 @@ namespace {
 
 constexpr int BM = 128;             // tile rows (M) = tensor-memory lanes
 constexpr int BN = 256;             // tile columns (N) = accumulator columns
-constexpr int SLAB_ROW_BYTES = 64;  // one K slab row: 64 bytes (64-byte swizzle)
 constexpr int EPI_WARPS = 8;        // two per tensor-memory lane quarter
 constexpr int EPI_WARP0 = 4;        // warpgroup 0: producer, MMA, two idle warps
 constexpr int THREADS = EPI_WARP0 * 32 + EPI_WARPS * 32;  // 3 warpgroups
@@ -58,8 +57,6 @@ static_assert(EPI_WARP0 * 32 * CTRL_REGS + EPI_WARPS * 32 * EPI_REGS <= THREADS 
               "register split exceeds the launch's registers");
 constexpr uint32_t TMEM_COLS = 2 * BN;        // two FP32 BM x BN chunk buffers
 constexpr int GROUP_N = 8;          // column tiles per rasterisation group
-constexpr uint32_t A_SLAB = BM * SLAB_ROW_BYTES;  // bytes of one A plane slab
-constexpr uint32_t B_SLAB = BN * SLAB_ROW_BYTES;  // bytes of one B plane slab
 constexpr uint32_t SMEM_BUDGET = 200 * 1024;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per bounded wait
 constexpr int FP8_BLOCK = 128;      // FP8 scale block (rows x K) of each operand
@@ -74,7 +71,14 @@ struct Cfg {
   static constexpr bool FP8 = MODE == 8;
   static constexpr int PLANES = MODE == 3 ? 2 : 1;
   static constexpr int ELEM_BYTES = FP8 ? 1 : 2;
-  static constexpr int BK = SLAB_ROW_BYTES / ELEM_BYTES;  // K elements per slab
+  // One K slab row in shared memory: 128 bytes (128-byte swizzle) for BF16
+  // and FP8, so a slab carries 4 MMAs and the per-slab handshake is paid
+  // once per 4; 64 bytes (64-byte swizzle) for BF16x3, whose 3 products
+  // already give 6 MMAs per slab and whose 4 planes need the smaller stages.
+  static constexpr int ROW_BYTES = MODE == 3 ? 64 : 128;
+  static constexpr uint32_t A_SLAB = BM * ROW_BYTES;  // bytes of one A plane slab
+  static constexpr uint32_t B_SLAB = BN * ROW_BYTES;  // bytes of one B plane slab
+  static constexpr int BK = ROW_BYTES / ELEM_BYTES;   // K elements per slab
   static constexpr int MMA_K = 32 / ELEM_BYTES;           // K per tcgen05.mma
   // K chunk accumulated afresh in tensor memory and then added to FP32
   // registers with round-to-nearest (the tensor-core accumulation
@@ -167,13 +171,15 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // used by swizzled K-major layouts), stride byte offset >> 4 in 32-45 (the
 // distance between groups of 8 rows: 8 * 64 bytes), descriptor version 1 in
 // bits 46-47, swizzle mode in bits 61-63 (4 = 64-byte swizzle).
-__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
+template <int ROW_BYTES>
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr) {
+  static_assert(ROW_BYTES == 64 || ROW_BYTES == 128, "64- or 128-byte swizzle");
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
   d |= static_cast<uint64_t>(1) << 16;
-  d |= static_cast<uint64_t>(512 >> 4) << 32;
+  d |= static_cast<uint64_t>((8 * ROW_BYTES) >> 4) << 32;      // 8-row group stride
   d |= static_cast<uint64_t>(1) << 46;
-  d |= static_cast<uint64_t>(4) << 61;
+  d |= static_cast<uint64_t>(ROW_BYTES == 128 ? 2 : 4) << 61;  // 128B / 64B swizzle
   return d;
 }
 // Instruction descriptor of tcgen05.mma kind::f16: D format F32 (bits 4-5 =
@@ -563,9 +569,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   // stage s: [A hi][A lo][B hi][B lo] (lo planes only for NPROD == 3)
   auto a_hi = [&](int s) { return smem + s * C_::STAGE_BYTES; };
-  auto a_lo = [&](int s) { return smem + s * C_::STAGE_BYTES + A_SLAB; };
-  auto b_hi = [&](int s) { return smem + s * C_::STAGE_BYTES + C_::PLANES * A_SLAB; };
-  auto b_lo = [&](int s) { return smem + s * C_::STAGE_BYTES + C_::PLANES * A_SLAB + B_SLAB; };
+  auto a_lo = [&](int s) { return smem + s * C_::STAGE_BYTES + C_::A_SLAB; };
+  auto b_hi = [&](int s) { return smem + s * C_::STAGE_BYTES + C_::PLANES * C_::A_SLAB; };
+  auto b_lo = [&](int s) { return smem + s * C_::STAGE_BYTES + C_::PLANES * C_::A_SLAB + C_::B_SLAB; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -608,7 +614,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
         const TileView v = view(t);
         const int num_kb = (v.K + BK - 1) / BK;
-        const uint32_t bytes = C_::PLANES * (A_SLAB + (uint32_t)v.bn * SLAB_ROW_BYTES);
+        const uint32_t bytes = C_::PLANES * (C_::A_SLAB + (uint32_t)v.bn * C_::ROW_BYTES);
         for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1;
@@ -660,13 +666,13 @@ __global__ void __launch_bounds__(THREADS, 1)
               const uint32_t off = kk * MMA_K * C_::ELEM_BYTES;  // bytes along the 64-byte row
               const uint32_t acc = (kb == c * KC_SLABS && kk == 0) ? 0u : 1u;
               if (C_::FP8) {
-                umma_e4m3(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, acc);
+                umma_e4m3(dst, sdesc_k<C_::ROW_BYTES>(ah + off), sdesc_k<C_::ROW_BYTES>(bh + off), idesc, acc);
               } else if (NPROD == 3) {
-                umma_bf16(dst, sdesc_k_sw64(al + off), sdesc_k_sw64(bh + off), idesc, acc);
-                umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bl + off), idesc, 1u);
-                umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, 1u);
+                umma_bf16(dst, sdesc_k<C_::ROW_BYTES>(al + off), sdesc_k<C_::ROW_BYTES>(bh + off), idesc, acc);
+                umma_bf16(dst, sdesc_k<C_::ROW_BYTES>(ah + off), sdesc_k<C_::ROW_BYTES>(bl + off), idesc, 1u);
+                umma_bf16(dst, sdesc_k<C_::ROW_BYTES>(ah + off), sdesc_k<C_::ROW_BYTES>(bh + off), idesc, 1u);
               } else {
-                umma_bf16(dst, sdesc_k_sw64(ah + off), sdesc_k_sw64(bh + off), idesc, acc);
+                umma_bf16(dst, sdesc_k<C_::ROW_BYTES>(ah + off), sdesc_k<C_::ROW_BYTES>(bh + off), idesc, acc);
               }
             }
             umma_commit(&empty[s]);  // frees the slab once these MMAs have read it
@@ -847,7 +853,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
 // K-major operand plane: rows x K elements of `elem_bytes` bytes, row stride
 // Kp elements; TMA box of one 64-byte slab row width x box_rows rows.
 bool encode_plane(CUtensorMap* map, const void* base, int rows, int K, int Kp, int box_rows, int elem_bytes,
-                  std::string* err) {
+                  int row_bytes, std::string* err) {
   auto enc = get_encoder();
   if (!enc) {
     *err = "cuTensorMapEncodeTiled is not available from the driver";
@@ -855,11 +861,12 @@ bool encode_plane(CUtensorMap* map, const void* base, int rows, int K, int Kp, i
   }
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)Kp * elem_bytes};
-  cuuint32_t box[2] = {(cuuint32_t)(SLAB_ROW_BYTES / elem_bytes), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)(row_bytes / elem_bytes), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   const CUtensorMapDataType dt = elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     char buf[160];
     snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for a %d x %d plane", (int)r, rows, K);
@@ -1016,11 +1023,12 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
   alignas(64) CUtensorMap maps[4];
   memset(maps, 0, sizeof maps);
   if (K > 0) {
-    if (!encode_plane(&maps[0], ah, M, K, Kp, BM, C_::ELEM_BYTES, err) ||
-        !encode_plane(&maps[2], bh, N, K, Kp, BN, C_::ELEM_BYTES, err))
+    if (!encode_plane(&maps[0], ah, M, K, Kp, BM, C_::ELEM_BYTES, C_::ROW_BYTES, err) ||
+        !encode_plane(&maps[2], bh, N, K, Kp, BN, C_::ELEM_BYTES, C_::ROW_BYTES, err))
       return cudaErrorInvalidValue;
     if (NPROD == 3) {
-      if (!encode_plane(&maps[1], al, M, K, Kp, BM, 2, err) || !encode_plane(&maps[3], bl, N, K, Kp, BN, 2, err))
+      if (!encode_plane(&maps[1], al, M, K, Kp, BM, 2, C_::ROW_BYTES, err) ||
+          !encode_plane(&maps[3], bl, N, K, Kp, BN, 2, C_::ROW_BYTES, err))
         return cudaErrorInvalidValue;
     } else {
       maps[1] = maps[0];
@@ -1207,12 +1215,13 @@ int tc_batch_build(TcBatch* b, std::string* err) {
     if (d.M <= 0 || d.N <= 0 || d.K <= 0) continue;
     const WsLayout L = ws_layout(d, mode);
     uint8_t* w = static_cast<uint8_t*>(b->ws) + b->plane_off[i];
-    if (!encode_plane(&g.tm[0], w + L.a_hi, (int)d.M, (int)d.K, (int)L.Kp, BM, 2, err) ||
-        !encode_plane(&g.tm[2], w + L.b_hi, (int)d.N, (int)d.K, (int)L.Kp, g.bn, 2, err))
+    const int rb = mode == 3 ? Cfg<3>::ROW_BYTES : Cfg<1>::ROW_BYTES;
+    if (!encode_plane(&g.tm[0], w + L.a_hi, (int)d.M, (int)d.K, (int)L.Kp, BM, 2, rb, err) ||
+        !encode_plane(&g.tm[2], w + L.b_hi, (int)d.N, (int)d.K, (int)L.Kp, g.bn, 2, rb, err))
       return -1;
     if (mode == 3) {
-      if (!encode_plane(&g.tm[1], w + L.a_lo, (int)d.M, (int)d.K, (int)L.Kp, BM, 2, err) ||
-          !encode_plane(&g.tm[3], w + L.b_lo, (int)d.N, (int)d.K, (int)L.Kp, g.bn, 2, err))
+      if (!encode_plane(&g.tm[1], w + L.a_lo, (int)d.M, (int)d.K, (int)L.Kp, BM, 2, rb, err) ||
+          !encode_plane(&g.tm[3], w + L.b_lo, (int)d.N, (int)d.K, (int)L.Kp, g.bn, 2, rb, err))
         return -1;
     } else {
       g.tm[1] = g.tm[0];
