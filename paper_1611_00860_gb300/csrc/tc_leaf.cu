@@ -51,22 +51,26 @@ constexpr int THREADS = EPI_WARP0 * 32 + EPI_WARPS * 32;  // 3 warpgroups
 // control warpgroup gives registers back and the two epilogue warpgroups,
 // which hold a 128-column FP32 running sum per thread, take them.
 constexpr int LAUNCH_REGS = 168;
-constexpr int CTRL_REGS = 56;
-constexpr int EPI_REGS = 224;
+constexpr int CTRL_REGS = 40;
+constexpr int EPI_REGS = 232;
 static_assert(EPI_WARP0 * 32 * CTRL_REGS + EPI_WARPS * 32 * EPI_REGS <= THREADS * LAUNCH_REGS,
               "register split exceeds the launch's registers");
 constexpr uint32_t TMEM_COLS = 2 * BN;        // two FP32 BM x BN chunk buffers
 constexpr int GROUP_N = 8;          // column tiles per rasterisation group
-constexpr uint32_t SMEM_BUDGET = 200 * 1024;
+constexpr uint32_t SMEM_BUDGET = 226 * 1024;  // of the 227 KB a block may have
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per bounded wait
 constexpr int FP8_BLOCK = 128;      // FP8 scale block (rows x K) of each operand
 
 // status bits (DeviceStatus word)
-constexpr int ST_PRODUCER = 1, ST_MMA = 2, ST_EPILOGUE = 4, ST_DRAIN = 8, ST_SELFTEST = 16;
+constexpr int ST_PRODUCER = 1, ST_MMA = 2, ST_EPILOGUE = 4, ST_DRAIN = 8, ST_SELFTEST = 16, ST_CONFIG = 32;
 
 // Leaf modes: 3 = BF16x3 split (hi*hi + hi*lo + lo*hi), 1 = BF16, 8 = FP8
 // E4M3 with one FP32 scale per 128 x 128 block of each operand.
-template <int MODE>
+// PAIR: two CTAs of a cluster share one 256 x 256 tile (tcgen05 cta_group::2):
+// each stages its own 128 rows of A and 128 of the tile's 256 rows of B, so
+// per CTA a stage holds a third less and the operand traffic from L2 and the
+// shared-memory reads of the MMAs drop by the same third.
+template <int MODE, bool PAIR = false>
 struct Cfg {
   static constexpr bool FP8 = MODE == 8;
   static constexpr int PLANES = MODE == 3 ? 2 : 1;
@@ -77,7 +81,8 @@ struct Cfg {
   // already give 6 MMAs per slab and whose 4 planes need the smaller stages.
   static constexpr int ROW_BYTES = MODE == 3 ? 64 : 128;
   static constexpr uint32_t A_SLAB = BM * ROW_BYTES;  // bytes of one A plane slab
-  static constexpr uint32_t B_SLAB = BN * ROW_BYTES;  // bytes of one B plane slab
+  static constexpr int B_ROWS = PAIR ? BN / 2 : BN;     // rows of B this CTA stages
+  static constexpr uint32_t B_SLAB = B_ROWS * ROW_BYTES;  // bytes of one B plane slab
   static constexpr int BK = ROW_BYTES / ELEM_BYTES;   // K elements per slab
   static constexpr int MMA_K = 32 / ELEM_BYTES;           // K per tcgen05.mma
   // K chunk accumulated afresh in tensor memory and then added to FP32
@@ -89,8 +94,8 @@ struct Cfg {
   // tile, read out once.
   static constexpr int KC_SLABS = MODE == 1 ? (1 << 24) : 128 / BK;
   static constexpr uint32_t STAGE_BYTES = PLANES * (A_SLAB + B_SLAB);
-  static constexpr int STAGES = (int)((SMEM_BUDGET - 2048) / STAGE_BYTES) > 8
-                                    ? 8 : (int)((SMEM_BUDGET - 2048) / STAGE_BYTES);
+  static constexpr int STAGES = (int)((SMEM_BUDGET - 1536) / STAGE_BYTES) > 8
+                                    ? 8 : (int)((SMEM_BUDGET - 1536) / STAGE_BYTES);
   static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
   static_assert(2 * STAGES * 8 + 4 * 8 + 8 <= 512, "barrier area");
   static_assert(MODE == 1 || KC_SLABS * BK == 128, "chunk of 128 K elements");
@@ -125,31 +130,52 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+// CLUSTER: acquire at cluster scope, for barriers that threads of the peer
+// CTA of a pair arrive on.
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
+  if constexpr (CLUSTER) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  }
   return ok != 0;
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
 }
 // Wait for the phase of `bar` with the given parity. Gives up (returns
 // false) when another role raised the abort flag or after WAIT_LIMIT_NS, in
 // which case it records `code` in the status word and raises the flag.
+// peer_abort: shared::cluster address of the peer CTA's abort flag (a pair
+// of CTAs on one tile), raised too so the peer stops waiting; 0 for none.
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* status, int code, uint64_t limit_ns = WAIT_LIMIT_NS) {
-  if (mbar_try_wait(bar, parity)) return true;
+                                          int* status, int code, uint64_t limit_ns = WAIT_LIMIT_NS,
+                                          uint32_t peer_abort = 0) {
+  if (mbar_try_wait<CLUSTER>(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t n = 1;; ++n) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait<CLUSTER>(bar, parity)) return true;
     if ((n & 63u) == 0) {
       if (*abort_flag) return false;
       if (globaltimer() - t0 > limit_ns) {
         if (status) atomicOr_system(status, code);
         *abort_flag = 1;
+        if (peer_abort) st_cluster_u32(peer_abort, 1);
         return false;
       }
     }
@@ -162,6 +188,40 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
       "[%2];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
       : "memory");
+}
+// The same load for one CTA of a pair (.cta_group::2): the mbarrier may be
+// the peer's (a shared::cluster address), so both CTAs' loads of a stage
+// complete on the leader CTA's barrier.
+__device__ __forceinline__ void tma_load_2d_pair(const CUtensorMap* map, uint32_t bar_cluster, void* dst, int c0,
+                                                 int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the object at shared address a in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// Every thread of both CTAs of the cluster (reachable from divergent code).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -189,33 +249,68 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
          (static_cast<uint32_t>(m >> 4) << 24);
 }
+// CG: 1 = this CTA's tensor core; 2 = the pair's (issued by the leader CTA:
+// A's 256 rows are 128 in each CTA's shared memory, B's N rows N/2 in each,
+// at the same offsets; D's rows 0-127 land in the leader's tensor memory and
+// rows 128-255 in the peer's)
+template <int CG>
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if constexpr (CG == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
 }
 // Instruction descriptor of tcgen05.mma kind::f8f6f4 with E4M3 A and B
 // (format 0 in bits 7-9 and 10-12), F32 D, K-major, N >> 3, M >> 4.
 __host__ __device__ constexpr uint32_t idesc_e4m3(int m, int n) {
   return (1u << 4) | (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
 }
+template <int CG>
 __device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if constexpr (CG == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
 }
+// Arrive on `bar` once every MMA issued before has completed; CG 2 arrives on
+// the barrier at the same offset in both CTAs of the pair.
+template <int CG>
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
+  if constexpr (CG == 2) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+  } else {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+  }
 }
 // (a0, a1) <- (s*v0 + a0, s*v1 + a1), one rounding each (packed FP32 FMA).
 __device__ __forceinline__ void ffma2(float& a0, float& a1, float s, uint32_t v0, uint32_t v1) {
@@ -463,12 +558,12 @@ __global__ void __launch_bounds__(QTHREADS) quant_fp8(const float* __restrict__ 
 // Persistent: CTA b handles tiles b, b + gridDim.x, ... in a grouped order
 // (GROUP_N column tiles at a time, M fastest) so CTAs that run together share
 // operand panels in L2.
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int* m0, int* n0) {
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int tile_rows, int* m0, int* n0) {
   const int group = GROUP_N * tiles_m;
   const int g = t / group, r = t % group;
   const int first_n = g * GROUP_N;
   const int gn = min(GROUP_N, tiles_n - first_n);
-  *m0 = (r / gn) * BM;
+  *m0 = (r / gn) * tile_rows;
   *n0 = (first_n + r % gn) * BN;
 }
 
@@ -511,15 +606,30 @@ struct TileView {
 // (the elementwise leaf merged into the sgemm leaf, MergeDependentNodes).
 // GROUPED: the persistent CTAs walk the tile list of a batch of instances
 // (gp) instead of the tiles of the one instance of the kernel parameters.
-template <int MODE, int EPI, bool GROUPED>
+// PAIR: launched in clusters of 2 CTAs; each cluster takes 256 x 256 tiles
+// (the internal node's instance maps to a CTA pair) and the leader CTA
+// (rank 0) issues the pair's MMAs. Roles per CTA:
+//   warp 0      TMA producer (both CTAs: each loads its own half)
+//   warp 1      tensor-memory allocation; MMA issuer (leader only)
+//   warps 2, 3  idle (they complete the control warpgroup)
+//   warps 4-11  epilogue (both CTAs: each drains its own 128 rows)
+template <int MODE, int EPI, bool GROUPED, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1)
     sgemm_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
              TcParams p, GroupParams gp) {
-  using C_ = Cfg<MODE>;
+  static_assert(!(GROUPED && PAIR), "batches run on single CTAs");
+  using C_ = Cfg<MODE, PAIR>;
+  constexpr int CG = PAIR ? 2 : 1;
+  constexpr int TM = PAIR ? 2 * BM : BM;  // tile rows (one CTA, or the pair)
   constexpr int S = C_::STAGES;
   constexpr int NPROD = MODE == 3 ? 3 : 1;
   constexpr int BK = C_::BK, MMA_K = C_::MMA_K, KC_SLABS = C_::KC_SLABS;
+  if (PAIR && cluster_nctarank() != 2) {
+    // launched without its cluster: nothing was set up yet, so just report
+    if (threadIdx.x == 0 && p.status) atomicOr_system(p.status, ST_CONFIG);
+    return;
+  }
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * C_::STAGE_BYTES);
@@ -530,7 +640,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles_m = (p.M + BM - 1) / BM, tiles_n = (p.N + BN - 1) / BN;
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;  // CTA within the pair
+  const bool leader = rank == 0;
+  const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;  // CTA or pair index
+  const int num_units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  // the peer's abort flag (raised with ours, so it stops waiting for us)
+  const uint32_t peer_abort = PAIR ? mapa_rank(smem_u32((const void*)abort_flag), rank ^ 1u) : 0u;
+  const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + BN - 1) / BN;
   const int num_tiles = GROUPED ? gp.num_tiles : tiles_m * tiles_n;
 
   auto view = [&](int t) {
@@ -562,7 +678,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       v.bn = BN;
       v.alpha = p.alpha;
       v.beta = p.beta;
-      tile_coords(t, tiles_m, tiles_n, &v.m0, &v.n0);
+      tile_coords(t, tiles_m, tiles_n, TM, &v.m0, &v.n0);
     }
     return v;
   };
@@ -580,20 +696,31 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], EPI_WARPS);
+      mbar_init(&tempty[b], PAIR ? 2 * EPI_WARPS : EPI_WARPS);  // PAIR: both CTAs' epilogues
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    // PAIR: one warp of each CTA of the pair allocates, collectively
+    if constexpr (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR)
+    cluster_sync_all();  // both CTAs' barriers exist before either signals the other's
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   // bookkeeping for the drain after an abort
@@ -604,47 +731,63 @@ __global__ void __launch_bounds__(THREADS, 1)
     // control warpgroup: its registers go to the epilogue warpgroups
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(CTRL_REGS));
     if (warp == 0 && lane == 0) {
-      // ---- producer: TMA loads of the operand slabs into the ring
+      // ---- producer: TMA loads of the operand slabs into the ring. PAIR:
+      // this CTA's 128 rows of A and its half of B's rows; both CTAs' loads
+      // complete on the leader's barrier, which expects the pair's bytes.
       if (!GROUPED) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA_hi)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
       }
       int it = 0;
       bool go = true;
-      for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
+      for (int t = unit; go && t < num_tiles; t += num_units) {
         const TileView v = view(t);
         const int num_kb = (v.K + BK - 1) / BK;
-        const uint32_t bytes = C_::PLANES * (C_::A_SLAB + (uint32_t)v.bn * C_::ROW_BYTES);
+        const uint32_t b_rows = PAIR ? (uint32_t)C_::B_ROWS : (uint32_t)v.bn;
+        const uint32_t bytes = C_::PLANES * (C_::A_SLAB + b_rows * C_::ROW_BYTES);
+        const int ma = v.m0 + (int)rank * BM;
+        const int nb = v.n0 + (int)rank * C_::B_ROWS;
         for (int kb = 0; kb < num_kb; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1;
-          if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, p.status, ST_PRODUCER)) {
+          if (!mbar_wait<PAIR>(&empty[s], ph ^ 1, abort_flag, p.status, ST_PRODUCER, WAIT_LIMIT_NS, peer_abort)) {
             go = false;
             break;
           }
-          mbar_expect_tx(&full[s], bytes);
           const int k = kb * BK;
-          tma_load_2d(v.tm[0], &full[s], a_hi(s), k, v.m0);
-          if (NPROD == 3) tma_load_2d(v.tm[1], &full[s], a_lo(s), k, v.m0);
-          tma_load_2d(v.tm[2], &full[s], b_hi(s), k, v.n0);
-          if (NPROD == 3) tma_load_2d(v.tm[3], &full[s], b_lo(s), k, v.n0);
+          if constexpr (PAIR) {
+            if (leader) mbar_expect_tx(&full[s], 2 * bytes);
+            const uint32_t bar = mapa_rank(smem_u32(&full[s]), 0);
+            tma_load_2d_pair(v.tm[0], bar, a_hi(s), k, ma);
+            if (NPROD == 3) tma_load_2d_pair(v.tm[1], bar, a_lo(s), k, ma);
+            tma_load_2d_pair(v.tm[2], bar, b_hi(s), k, nb);
+            if (NPROD == 3) tma_load_2d_pair(v.tm[3], bar, b_lo(s), k, nb);
+          } else {
+            mbar_expect_tx(&full[s], bytes);
+            tma_load_2d(v.tm[0], &full[s], a_hi(s), k, ma);
+            if (NPROD == 3) tma_load_2d(v.tm[1], &full[s], a_lo(s), k, ma);
+            tma_load_2d(v.tm[2], &full[s], b_hi(s), k, nb);
+            if (NPROD == 3) tma_load_2d(v.tm[3], &full[s], b_lo(s), k, nb);
+          }
           issued = it + 1;
         }
       }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1 && lane == 0 && leader) {
       // ---- MMA issuer: per K chunk, a fresh accumulation in tensor-memory
-      // buffer (chunk parity); three (or one) BF16 products per 16-wide K step
+      // buffer (chunk parity); three (or one) products per K step
       int it = 0, g = 0;
       bool go = true;
-      for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
+      for (int t = unit; go && t < num_tiles; t += num_units) {
         const TileView v = view(t);
         const int num_kb = (v.K + BK - 1) / BK;
         const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
-        const uint32_t idesc = C_::FP8 ? idesc_e4m3(BM, GROUPED ? v.bn : BN) : idesc_bf16(BM, GROUPED ? v.bn : BN);
+        const int n_mma = GROUPED ? v.bn : BN;
+        const uint32_t idesc = C_::FP8 ? idesc_e4m3(TM, n_mma) : idesc_bf16(TM, n_mma);
         for (int c = 0; go && c < num_chunks; ++c, ++g) {
           const int buf = g & 1;
           const uint32_t use = (uint32_t)(g >> 1);
-          if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag, p.status, ST_MMA)) {
+          if (!mbar_wait<PAIR>(&tempty[buf], (use & 1) ^ 1, abort_flag, p.status, ST_MMA, WAIT_LIMIT_NS,
+                               peer_abort)) {
             go = false;
             break;
           }
@@ -654,47 +797,50 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int kb = c * KC_SLABS; kb < kb_end; ++kb, ++it) {
             const int s = it % S;
             const uint32_t ph = (it / S) & 1;
-            if (!mbar_wait(&full[s], ph, abort_flag, p.status, ST_MMA)) {
+            if (!mbar_wait<PAIR>(&full[s], ph, abort_flag, p.status, ST_MMA, WAIT_LIMIT_NS, peer_abort)) {
               go = false;
               break;
             }
             tc_fence_after();
             const uint32_t ah = smem_u32(a_hi(s)), al = smem_u32(a_lo(s));
             const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_lo(s));
-  #pragma unroll
+#pragma unroll
             for (int kk = 0; kk < BK / MMA_K; ++kk) {
-              const uint32_t off = kk * MMA_K * C_::ELEM_BYTES;  // bytes along the 64-byte row
+              const uint32_t off = kk * MMA_K * C_::ELEM_BYTES;  // bytes along the slab row
               const uint32_t acc = (kb == c * KC_SLABS && kk == 0) ? 0u : 1u;
+              constexpr int RB = C_::ROW_BYTES;
               if (C_::FP8) {
-                umma_e4m3(dst, sdesc_k<C_::ROW_BYTES>(ah + off), sdesc_k<C_::ROW_BYTES>(bh + off), idesc, acc);
+                umma_e4m3<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, acc);
               } else if (NPROD == 3) {
-                umma_bf16(dst, sdesc_k<C_::ROW_BYTES>(al + off), sdesc_k<C_::ROW_BYTES>(bh + off), idesc, acc);
-                umma_bf16(dst, sdesc_k<C_::ROW_BYTES>(ah + off), sdesc_k<C_::ROW_BYTES>(bl + off), idesc, 1u);
-                umma_bf16(dst, sdesc_k<C_::ROW_BYTES>(ah + off), sdesc_k<C_::ROW_BYTES>(bh + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_k<RB>(al + off), sdesc_k<RB>(bh + off), idesc, acc);
+                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bl + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, 1u);
               } else {
-                umma_bf16(dst, sdesc_k<C_::ROW_BYTES>(ah + off), sdesc_k<C_::ROW_BYTES>(bh + off), idesc, acc);
+                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, acc);
               }
             }
-            umma_commit(&empty[s]);  // frees the slab once these MMAs have read it
+            umma_commit<CG>(&empty[s]);  // frees the slab (in both CTAs) once read
             committed = it + 1;
           }
           if (!go) break;
-          umma_commit(&tfull[buf]);  // chunk complete in buffer buf
+          umma_commit<CG>(&tfull[buf]);  // chunk complete in buffer buf (both CTAs)
         }
       }
     }
     __syncwarp();
     tc_fence_before();
-    cta_barrier_all();  // every role is done
+    cta_barrier_all();  // every role of this CTA is done
     tc_fence_after();
     if (*abort_flag) {
-      // Drain what this CTA itself started before returning (bounded waits):
-      // TMA loads not yet consumed, and the MMAs of the last commit.
-      if (warp == 0 && lane == 0) {
+      // Drain what this CTA started before returning (bounded waits): TMA
+      // loads not yet consumed and the MMAs of the last commit. PAIR: the
+      // loads of both CTAs complete on the leader's barriers, so the leader
+      // drains them; the cluster barrier below keeps the peer until then.
+      if (warp == 0 && lane == 0 && leader) {
         for (int it = (issued > S ? issued - S : 0); it < issued; ++it) {
           const int s = it % S;
           const uint64_t t0 = globaltimer();
-          while (!mbar_try_wait(&full[s], (it / S) & 1)) {
+          while (!mbar_try_wait<PAIR>(&full[s], (it / S) & 1)) {
             if (globaltimer() - t0 > WAIT_LIMIT_NS) {
               if (p.status) atomicOr_system(p.status, ST_DRAIN);
               break;
@@ -706,7 +852,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int it = committed - 1;
         const int s = it % S;
         const uint64_t t0 = globaltimer();
-        while (!mbar_try_wait(&empty[s], (it / S) & 1)) {
+        while (!mbar_try_wait<PAIR>(&empty[s], (it / S) & 1)) {
           if (globaltimer() - t0 > WAIT_LIMIT_NS) {
             if (p.status) atomicOr_system(p.status, ST_DRAIN);
             break;
@@ -715,20 +861,30 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
     __syncwarp();  // warp 1: the drain of lane 0 ends before the dealloc
+    // PAIR: neither CTA leaves (or frees tensor memory) while the other may
+    // still arrive on its barriers or the leader's MMAs may read its stages
+    if constexpr (PAIR) cluster_sync_all();
     if (warp == 1) {
       tc_fence_after();
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+      if constexpr (PAIR)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+      else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
     }
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(EPI_REGS));
     // ---- epilogue: every chunk, tensor memory -> FP32 registers (round to
-    // nearest); at the end of a tile, registers -> C, coalesced per column
-    const int q = warp & 3;          // TMEM lane quarter this warp may access
+    // nearest); at the end of a tile, registers -> C, coalesced per column.
+    // PAIR: this CTA's tensor memory holds rows rank*128 .. +127 of the tile.
+    const int q = warp & 3;                 // TMEM lane quarter this warp may access
     const int h = (warp - EPI_WARP0) >> 2;  // which half of the tile's columns
     int g = 0;
     bool go = true;
-    for (int t = blockIdx.x; go && t < num_tiles; t += gridDim.x) {
+    for (int t = unit; go && t < num_tiles; t += num_units) {
       const TileView v = view(t);
+      const int m_cta = v.m0 + (int)rank * BM;  // first row of this CTA's half
       const int num_kb = (v.K + BK - 1) / BK;
       const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
       const int half = GROUPED ? v.bn / 2 : BN / 2;  // columns this warp owns
@@ -736,20 +892,32 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int u = 0; u < BN / 2; ++u) acc[u] = 0.f;
       // FP8: this warp's 128 columns are exactly one 128-wide block of
-      // op(B)^T rows and its tile rows one block of op(A) rows
+      // op(B)^T rows and this CTA's tile rows one block of op(A) rows
       const float* sa = nullptr;
       const float* sb = nullptr;
       if (C_::FP8) {
-        sa = p.scaleA + (int64_t)(v.m0 / FP8_BLOCK) * p.nkb;
+        sa = p.scaleA + (int64_t)(m_cta / FP8_BLOCK) * p.nkb;
         sb = p.scaleB + (int64_t)((v.n0 + h * (BN / 2)) / FP8_BLOCK) * p.nkb;
       }
-      const bool cols_live = v.n0 + h * half < v.N;
+      const bool live = v.n0 + h * half < v.N && m_cta < v.M;
+      // FP8: the block scales of chunks c and c + 1, loaded two chunks ahead
+      // so their L2 round trips stay off the chunk-to-chunk critical path
+      float sa0 = 0.f, sb0 = 0.f, sa1 = 0.f, sb1 = 0.f;
+      if (C_::FP8 && live) {
+        if (num_chunks > 0) sa0 = __ldg(sa), sb0 = __ldg(sb);
+        if (num_chunks > 1) sa1 = __ldg(sa + 1), sb1 = __ldg(sb + 1);
+      }
       for (int c = 0; c < num_chunks; ++c, ++g) {
         const int buf = g & 1;
         const uint32_t use = (uint32_t)(g >> 1);
         float scale = 1.f;
-        if (C_::FP8) scale = cols_live ? __ldg(sa + c) * __ldg(sb + c) : 0.f;
-        if (!mbar_wait(&tfull[buf], use & 1, abort_flag, p.status, ST_EPILOGUE)) {
+        if (C_::FP8) {
+          scale = sa0 * sb0;
+          sa0 = sa1;
+          sb0 = sb1;
+          if (live && c + 2 < num_chunks) sa1 = __ldg(sa + c + 2), sb1 = __ldg(sb + c + 2);
+        }
+        if (!mbar_wait<PAIR>(&tfull[buf], use & 1, abort_flag, p.status, ST_EPILOGUE, WAIT_LIMIT_NS, peer_abort)) {
           go = false;
           break;
         }
@@ -777,33 +945,38 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
+        if (lane == 0) {
+          if constexpr (PAIR)
+            mbar_arrive_cluster(mapa_rank(smem_u32(&tempty[buf]), 0));  // the leader's barrier
+          else
+            mbar_arrive(&tempty[buf]);
+        }
       }
       if (!go) break;
-      const int row = v.m0 + q * 32 + lane;
+      const int row = m_cta + q * 32 + lane;
       const int col0 = v.n0 + h * half;
       if (row < v.M) {
-        // C in groups of CG columns: all loads of old C values first, so
+        // C in groups of CGRP columns: all loads of old C values first, so
         // their DRAM round trips overlap, then the stores (streaming hints:
         // C is touched once and should not displace operand panels in L2)
         float* cp = v.C + row + (int64_t)col0 * v.ldc;
         const int ncols = min(half, v.N - col0);
-        constexpr int CG = EPI == 2 ? 4 : 8;  // the tanh adjoint also reads H
+        constexpr int CGRP = EPI == 2 ? 4 : 8;  // the tanh adjoint also reads H
 #pragma unroll
-        for (int u0 = 0; u0 < BN / 2; u0 += CG) {
-          float old[CG];
+        for (int u0 = 0; u0 < BN / 2; u0 += CGRP) {
+          float old[CGRP];
           if (v.beta != 0.f) {
 #pragma unroll
-            for (int u = 0; u < CG; ++u) old[u] = (u0 + u < ncols) ? __ldcs(cp + (int64_t)(u0 + u) * v.ldc) : 0.f;
+            for (int u = 0; u < CGRP; ++u) old[u] = (u0 + u < ncols) ? __ldcs(cp + (int64_t)(u0 + u) * v.ldc) : 0.f;
           }
-          float hx[EPI == 2 ? CG : 1];
+          float hx[EPI == 2 ? CGRP : 1];
           if (EPI == 2) {
             const float* hp = p.aux + row + (int64_t)col0 * p.ldaux;
 #pragma unroll
-            for (int u = 0; u < CG; ++u) hx[u] = (u0 + u < ncols) ? __ldcs(hp + (int64_t)(u0 + u) * p.ldaux) : 0.f;
+            for (int u = 0; u < CGRP; ++u) hx[u] = (u0 + u < ncols) ? __ldcs(hp + (int64_t)(u0 + u) * p.ldaux) : 0.f;
           }
 #pragma unroll
-          for (int u = 0; u < CG; ++u) {
+          for (int u = 0; u < CGRP; ++u) {
             if (u0 + u < ncols) {
               float x = (v.beta == 0.f) ? v.alpha * acc[u0 + u] : fmaf(v.alpha, acc[u0 + u], v.beta * old[u]);
               if (EPI == 1) x = tanhf(x);
@@ -816,6 +989,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     tc_fence_before();
     cta_barrier_all();
+    if constexpr (PAIR) cluster_sync_all();
   }
 }
 
@@ -971,26 +1145,71 @@ cudaError_t check_register_split(Kern* kernel) {
   return cudaSuccess;
 }
 
-template <int MODE, int EPI>
-cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, dim3 grid, cudaStream_t s) {
-  using C_ = Cfg<MODE>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sgemm_tc<MODE, EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C_::SMEM_BYTES);
-    if (e == cudaSuccess) e = check_register_split(sgemm_tc<MODE, EPI, false>);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+// Which leaves of a single instance run on CTA pairs (256 x 256 tiles,
+// cta_group::2) rather than on single CTAs (128 x 256 tiles). Measured at
+// M = N = K = 8192 and 16384: pairs make plain BF16 (one accumulation per
+// tile) 5-10% faster; BF16x3 runs the same either way; FP8, which hands a
+// tensor-memory buffer between the MMA and epilogue warps every 128 K, runs
+// 2.3x slower, its hand-offs now crossing CTAs. So only BF16 pairs.
+constexpr bool pair_for_mode(int mode) { return mode == 1; }
+
+// The single-instance leaf, persistent: PAIR runs clusters of 2, one cluster
+// per 256 x 256 tile at a time, as many clusters as fit on the GPU at once;
+// otherwise one CTA per SM. *grid_ctas returns the CTAs launched.
+template <int MODE, int EPI, bool PAIR>
+cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, int tiles, cudaStream_t s, int* grid_ctas) {
+  using C_ = Cfg<MODE, PAIR>;
+  auto kernel = sgemm_tc<MODE, EPI, false, PAIR>;
+  if constexpr (!PAIR) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
+      if (e == cudaSuccess) e = check_register_split(kernel);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    const int grid = std::max(1, std::min(tiles, num_sms()));
+    *grid_ctas = grid;
+    kernel<<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm,
+                                                  GroupParams{nullptr, nullptr, 0});
+    return cudaGetLastError();
   }
-  sgemm_tc<MODE, EPI, false><<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm,
-                                                                    GroupParams{nullptr, nullptr, 0});
-  return cudaGetLastError();
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = C_::SMEM_BYTES;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  static int max_clusters = 0;
+  if (max_clusters == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
+    if (e == cudaSuccess) e = check_register_split(kernel);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(2 * num_sms());
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    max_clusters = n;
+  }
+  const int clusters = std::max(1, std::min(tiles, max_clusters));
+  cfg.gridDim = dim3(2 * clusters);
+  *grid_ctas = 2 * clusters;
+  return cudaLaunchKernelEx(&cfg, kernel, maps[0], maps[1], maps[2], maps[3], prm,
+                            GroupParams{nullptr, nullptr, 0});
 }
 
 template <int MODE>
 cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStream_t s, KernelReport* rep,
                    std::string* err, const LaunchHooks* hooks, const Epilogue& epi) {
-  using C_ = Cfg<MODE>;
+  constexpr bool PAIR = pair_for_mode(MODE);
+  constexpr int TM = PAIR ? 2 * BM : BM;
+  using C_ = Cfg<MODE, PAIR>;
   constexpr int NPROD = MODE == 3 ? 3 : 1;
   const int M = (int)d.M, N = (int)d.N, K = (int)d.K;
   const WsLayout L = ws_layout(d, MODE);
@@ -1023,12 +1242,13 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
   alignas(64) CUtensorMap maps[4];
   memset(maps, 0, sizeof maps);
   if (K > 0) {
+    // a CTA loads 128 rows of A and B_ROWS of B (PAIR: 128 of the tile's 256)
     if (!encode_plane(&maps[0], ah, M, K, Kp, BM, C_::ELEM_BYTES, C_::ROW_BYTES, err) ||
-        !encode_plane(&maps[2], bh, N, K, Kp, BN, C_::ELEM_BYTES, C_::ROW_BYTES, err))
+        !encode_plane(&maps[2], bh, N, K, Kp, C_::B_ROWS, C_::ELEM_BYTES, C_::ROW_BYTES, err))
       return cudaErrorInvalidValue;
     if (NPROD == 3) {
       if (!encode_plane(&maps[1], al, M, K, Kp, BM, 2, C_::ROW_BYTES, err) ||
-          !encode_plane(&maps[3], bl, N, K, Kp, BN, 2, C_::ROW_BYTES, err))
+          !encode_plane(&maps[3], bl, N, K, Kp, C_::B_ROWS, 2, C_::ROW_BYTES, err))
         return cudaErrorInvalidValue;
     } else {
       maps[1] = maps[0];
@@ -1036,20 +1256,20 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
     }
   }
   TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, st.dev, epi.aux, epi.ldaux};
-  const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  dim3 grid((unsigned)std::min(tiles, num_sms()));
+  const int tiles = ((M + TM - 1) / TM) * ((N + BN - 1) / BN);
+  int grid_ctas = 0;
   hook_begin(hooks, s);
-  if (epi.kind == 1) e = launch_leaf<MODE, 1>(maps, prm, grid, s);
-  else if (epi.kind == 2) e = launch_leaf<MODE, 2>(maps, prm, grid, s);
-  else e = launch_leaf<MODE, 0>(maps, prm, grid, s);
+  if (epi.kind == 1) e = launch_leaf<MODE, 1, PAIR>(maps, prm, tiles, s, &grid_ctas);
+  else if (epi.kind == 2) e = launch_leaf<MODE, 2, PAIR>(maps, prm, tiles, s, &grid_ctas);
+  else e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, s, &grid_ctas);
   hook_end(hooks, s);
   if (e != cudaSuccess) return e;
   kernels += 1;
   if (rep) {
     rep->kernels = kernels;
-    rep->grid_x = (int)grid.x; rep->grid_y = (int)grid.y; rep->grid_z = 1;
+    rep->grid_x = grid_ctas; rep->grid_y = 1; rep->grid_z = 1;
     rep->block_threads = THREADS;
-    rep->tile_m = BM; rep->tile_n = BN; rep->tile_k = C_::BK;
+    rep->tile_m = TM; rep->tile_n = BN; rep->tile_k = C_::BK;
     rep->smem_bytes = (int)C_::SMEM_BYTES;
     rep->literal = 0;
     rep->workspace_bytes = (int64_t)L.total;
@@ -1078,7 +1298,8 @@ cudaError_t launch_batch_kernels(const TcBatch& b, const DeviceStatus& st, cudaS
   prm.status = st.dev;
   GroupParams gp{static_cast<const GroupInst*>(b.d_insts), static_cast<const GroupTile*>(b.d_tiles), b.num_tiles};
   hook_begin(hooks, s);
-  sgemm_tc<MODE, 0, true><<<b.grid, THREADS, C_::SMEM_BYTES, s>>>(unused[0], unused[1], unused[2], unused[3], prm, gp);
+  sgemm_tc<MODE, 0, true, false>
+      <<<b.grid, THREADS, C_::SMEM_BYTES, s>>>(unused[0], unused[1], unused[2], unused[3], prm, gp);
   hook_end(hooks, s);
   return cudaGetLastError();
 }
@@ -1238,13 +1459,13 @@ int tc_batch_build(TcBatch* b, std::string* err) {
   // kernel attributes now, so a run can be captured into a CUDA graph
   cudaError_t e;
   if (mode == 3) {
-    e = cudaFuncSetAttribute(sgemm_tc<3, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sgemm_tc<3, 0, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg<3>::SMEM_BYTES);
-    if (e == cudaSuccess) e = check_register_split(sgemm_tc<3, 0, true>);
+    if (e == cudaSuccess) e = check_register_split(sgemm_tc<3, 0, true, false>);
   } else {
-    e = cudaFuncSetAttribute(sgemm_tc<1, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sgemm_tc<1, 0, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg<1>::SMEM_BYTES);
-    if (e == cudaSuccess) e = check_register_split(sgemm_tc<1, 0, true>);
+    if (e == cudaSuccess) e = check_register_split(sgemm_tc<1, 0, true, false>);
   }
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
@@ -1314,8 +1535,8 @@ namespace {
 
 }  // namespace
 
-void tc_tile(int /*tier*/, int* tm, int* tn) {
-  *tm = BM;
+void tc_tile(int tier, int* tm, int* tn) {
+  *tm = pair_for_mode(mode_of_tier(tier)) ? 2 * BM : BM;  // a CTA pair's tile, or one CTA's
   *tn = BN;
 }
 
