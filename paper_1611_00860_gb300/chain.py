@@ -130,8 +130,11 @@ class ChainEngine:
 
     def close(self):
         if self.ctx:
-            H.hpvm_cleanup(self.ctx)
-            self.ctx = None
+            try:
+                self._drain()
+            finally:
+                H.hpvm_cleanup(self.ctx)
+                self.ctx = None
 
     def __del__(self):
         try:
@@ -144,15 +147,29 @@ class ChainEngine:
         return torch.cuda.current_stream(self.device).cuda_stream
 
     def _run(self, root: int, args) -> None:
-        """Launch asynchronously on the current stream; launches of one
-        forward or backward share the workspace in stream order and are
-        waited for together (``_drain``)."""
+        """Launch asynchronously on the current stream. Launches share the
+        workspace in stream order; their handles are released once finished
+        (``_reap``, which never blocks) or waited for by ``_drain``."""
         need = H.hpvm_workspace_size(self.ctx, root, args)
         if need and (self._ws is None or self._ws.numel() < need):
             self._drain()
             self._ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
             H.hpvm_set_workspace(self.ctx, self._ws.data_ptr(), self._ws.numel())
+        self._reap()
         self._pending.append(H.hpvm_launch(self.ctx, root, args, False, self._stream()))
+
+    def _reap(self) -> None:
+        """Release the handles of launches that have finished, oldest first,
+        without waiting (a device fault surfaces here or in ``_drain``)."""
+        while self._pending:
+            try:
+                H.hpvm_wait(self._pending[0], 0)
+            except H.HpvmError as e:
+                if e.code == H.HPVM_ERR_TIMEOUT:
+                    return
+                self._pending.pop(0)
+                raise
+            self._pending.pop(0)
 
     def _drain(self, timeout_ms: int = 600000) -> None:
         pending, self._pending = self._pending, []
@@ -176,7 +193,6 @@ class ChainEngine:
         H_1..H_{L-1} (the tanh outputs, the chain's intermediate buffers)."""
         outs = [torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws]
         self._run(self.chain, self.chain_records(X, Ws, outs))
-        self._drain()
         return (outs[-1], outs[:-1]) if keep else outs[-1]
 
     def recompute(self, X: torch.Tensor, Ws):
@@ -220,7 +236,6 @@ class ChainEngine:
             else:
                 self._run(self.stage_plain, a)
                 dX = dH
-        self._drain()
         return dX, dWs
 
     # -- streaming -----------------------------------------------------------------

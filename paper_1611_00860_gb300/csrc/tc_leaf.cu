@@ -51,10 +51,15 @@ constexpr int THREADS = EPI_WARP0 * 32 + EPI_WARPS * 32;  // 3 warpgroups
 // control warpgroup gives registers back and the two epilogue warpgroups,
 // which hold a 128-column FP32 running sum per thread, take them.
 constexpr int LAUNCH_REGS = 168;
-constexpr int CTRL_REGS = 40;
-constexpr int EPI_REGS = 232;
-static_assert(EPI_WARP0 * 32 * CTRL_REGS + EPI_WARPS * 32 * EPI_REGS <= THREADS * LAUNCH_REGS,
-              "register split exceeds the launch's registers");
+// The split per leaf variant: ptxas's spills (-Xptxas -v) for 40/232 and
+// 48/224 differ by variant, and each takes the one that spills least.
+template <int MODE, int EPI, bool PAIR>
+struct RegSplit {
+  static constexpr int EPI_R = ((MODE == 3 && EPI != 2 && !PAIR) || MODE == 8) ? 224 : 232;
+  static constexpr int CTRL_R = EPI_R == 224 ? 48 : 40;
+  static_assert(EPI_WARP0 * 32 * CTRL_R + EPI_WARPS * 32 * EPI_R <= THREADS * LAUNCH_REGS,
+                "register split exceeds the launch's registers");
+};
 constexpr uint32_t TMEM_COLS = 2 * BN;        // two FP32 BM x BN chunk buffers
 constexpr int GROUP_N = 8;          // column tiles per rasterisation group
 constexpr uint32_t SMEM_BUDGET = 226 * 1024;  // of the 227 KB a block may have
@@ -199,6 +204,9 @@ __device__ __forceinline__ void tma_load_2d_pair(const CUtensorMap* map, uint32_
       "%4}], [%2];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1)
       : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 __device__ __forceinline__ uint32_t cluster_ctarank() {
   uint32_t r;
@@ -384,12 +392,19 @@ __device__ __forceinline__ void split_tile_m(const float* __restrict__ X, int64_
                                              int64_t r0, int64_t k0) {
   __shared__ float t[64][65];
   const int tid = threadIdx.x;
-#pragma unroll 4
+  // all 16 loads of a thread in flight before the first shared-memory store
+  float v[16];
+#pragma unroll
   for (int it = 0; it < 16; ++it) {
-    int e = tid + it * 256;
-    int kk = e >> 6, rr = e & 63;
-    int64_t gr = r0 + rr, gk = k0 + kk;
-    t[kk][rr] = (gr < rows && gk < K) ? X[gr + gk * ld] : 0.f;
+    const int e = tid + it * 256;
+    const int kk = e >> 6, rr = e & 63;
+    const int64_t gr = r0 + rr, gk = k0 + kk;
+    v[it] = (gr < rows && gk < K) ? __ldcs(X + gr + gk * ld) : 0.f;
+  }
+#pragma unroll
+  for (int it = 0; it < 16; ++it) {
+    const int e = tid + it * 256;
+    t[e >> 6][e & 63] = v[it];
   }
   __syncthreads();
 #pragma unroll
@@ -413,16 +428,25 @@ template <int NPROD>
 __device__ __forceinline__ void split_tile_k(const float* __restrict__ X, int64_t ld, int rows, int K, int Kp,
                                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                              int64_t r0, int64_t k0) {
+  // both passes' 16 loads in flight before the first conversion
+  float v[2][8];
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int e = threadIdx.x + it * 256;
+    const int64_t r = r0 + (e >> 3), k = k0 + (e & 7) * 8;
+    const bool in = r < rows;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[it][u] = (in && k + u < K) ? __ldcs(X + r * ld + k + u) : 0.f;
+  }
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const int e = threadIdx.x + it * 256;
     const int64_t r = r0 + (e >> 3), k = k0 + (e & 7) * 8;
     if (r >= rows || k >= Kp) continue;
-    const float* src = X + r * ld + k;
     __align__(16) __nv_bfloat16 h[8];
     __align__(16) __nv_bfloat16 l[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) split_pair((k + u < K) ? src[u] : 0.f, h[u], l[u]);
+    for (int u = 0; u < 8; ++u) split_pair(v[it][u], h[u], l[u]);
     *reinterpret_cast<uint4*>(hi + r * Kp + k) = *reinterpret_cast<const uint4*>(h);
     if (NPROD == 3) *reinterpret_cast<uint4*>(lo + r * Kp + k) = *reinterpret_cast<const uint4*>(l);
   }
@@ -729,7 +753,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp < EPI_WARP0) {
     // control warpgroup: its registers go to the epilogue warpgroups
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(CTRL_REGS));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RegSplit<MODE, EPI, PAIR>::CTRL_R));
     if (warp == 0 && lane == 0) {
       // ---- producer: TMA loads of the operand slabs into the ring. PAIR:
       // this CTA's 128 rows of A and its half of B's rows; both CTAs' loads
@@ -874,7 +898,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                      : "memory");
     }
   } else {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(EPI_REGS));
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RegSplit<MODE, EPI, PAIR>::EPI_R));
     // ---- epilogue: every chunk, tensor memory -> FP32 registers (round to
     // nearest); at the end of a tile, registers -> C, coalesced per column.
     // PAIR: this CTA's tensor memory holds rows rank*128 .. +127 of the tile.
@@ -953,6 +977,25 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (!go) break;
+      if (!GROUPED && (EPI == 2 || p.beta != 0.f)) {
+        // The next tile's epilogue inputs (old C when beta != 0, H for the
+        // tanh adjoint) are fetched into L2 now, while its MMAs run: its
+        // loads then wait on L2 rather than on DRAM.
+        const int tn = t + num_units;
+        if (tn < num_tiles) {
+          int nm0, nn0;
+          tile_coords(tn, tiles_m, tiles_n, TM, &nm0, &nn0);
+          const int r0 = nm0 + (int)rank * BM + q * 32;  // this warp's 32 rows there
+          const int c0 = nn0 + h * (BN / 2);
+          if (r0 < p.M && c0 < p.N) {
+            const int nc = min(BN / 2, p.N - c0);
+            for (int u = lane; u < nc; u += 32) {
+              if (p.beta != 0.f) prefetch_l2(p.C + r0 + (int64_t)(c0 + u) * p.ldc);
+              if (EPI == 2) prefetch_l2(p.aux + r0 + (int64_t)(c0 + u) * p.ldaux);
+            }
+          }
+        }
+      }
       const int row = m_cta + q * 32 + lane;
       const int col0 = v.n0 + h * half;
       if (row < v.M) {
