@@ -323,11 +323,19 @@ def chain_section(args, H, W, torch, local, world, barrier):
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1) / steps
+    executed = (fwd + bwd + recompute) / (ms * 1e-3) / 1e12  # per GPU
+    peaks = load_peaks()
     out["train_step"] = {"value": (fwd + bwd) * world / (ms * 1e-3) / 1e12, "ms_per_step": ms, "steps": steps,
                          "executed_tflop_per_step": (fwd + bwd + recompute) / 1e12,
-                         "executed_rate": (fwd + bwd + recompute) * world / (ms * 1e-3) / 1e12,
+                         "executed_rate": executed * world,
                          "note": "value counts forward + backward products; the recomputed forward "
-                                 "of the activations is in executed_rate"}
+                                 "of the activations is in executed_rate",
+                         "roofline": {"bound": "tensor", "achieved": executed, "peak": peaks["bf16_tflops"],
+                                      "unit": "TFLOP/s", "frac": executed / peaks["bf16_tflops"],
+                                      "algorithmic": "15 products of 2*16384*4096*4096 FLOP per step (4 forward, "
+                                                     "3 recomputed, 8 adjoint), whole step incl. operand "
+                                                     "conversion and PyTorch's loss",
+                                      "peak_source": f"{peaks['_source']} dense BF16 burst (MEASURED_PEAKS.json)"}}
     with torch.no_grad():
         Wn = [x.detach() for x in Wd]
         xs = [Xd[i] for i in range(items)]
@@ -371,13 +379,31 @@ def batch_section(args, H, W, torch, local, world, rank, barrier):
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1) / reps
+    # the grouped leaf's own time (runtime's CUDA events around it), the rest
+    # of a batch being the batched split pre-pass
+    H.hpvm_set_kernel_timing(b.ctx, True)
+    for _ in range(reps):
+        b.run(stream)
+    barrier()
+    H.hpvm_set_kernel_timing(b.ctx, False)
+    leaf_total, leaf_n = H.hpvm_kernel_timing(b.ctx)
+    leaf_ms = leaf_total / max(1, leaf_n)
+    peaks = load_peaks()
+    algo_bytes = sum(4.0 * (m * k + n * k + m * n) for m, n, k in shapes)
+    achieved = algo_bytes / (ms * 1e-3) / 1e9
     out = {"workload": "512 sgemm DFG instances, M,N,K log-uniform in [32,2048] (seed 2), N(0,1), "
                        "alpha=1, beta=0, BF16x3 leaves", "unit": "TFLOP/s",
            "useful_tflop": flop / 1e12, "batch": {
                "value": flop * world / (ms * 1e-3) / 1e12, "ms_per_batch": ms,
                "launches": 2, "path": "hpvm_batch_prepare + hpvm_batch_autotune, hpvm_batch_run captured "
                                       "in a CUDA graph, replayed",
-               "autotuned_policy": best, "info": b.info()}}
+               "autotuned_policy": best, "info": b.info(),
+               "leaf_ms": leaf_ms, "split_ms": ms - leaf_ms,
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                            "algorithmic": "4*(M*K + N*K + M*N) bytes per instance: FP32 A and B read once, "
+                                           "C written once (beta = 0); the split planes are extra traffic",
+                            "peak_source": f"{peaks['_source']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}}}
     # one launch per instance (each: split of A, split of B, leaf)
     s = SgemmDFG(local)
     args_list = [s.args_for(p.M, p.N, p.K, A, p.lda, B, p.ldb, C, p.ldc, p.alpha, p.beta, p.transA,

@@ -607,10 +607,18 @@ struct GroupInst {
   int pad[10];
 };
 static_assert(sizeof(GroupInst) % 64 == 0, "tensor maps stay 64-byte aligned in an array");
-// One output tile of the batch's schedule.
+// One output tile of the batch's schedule, with what every role needs of
+// its instance besides the tensor maps: one 64-byte load per tile, issued a
+// tile ahead.
 struct GroupTile {
-  int inst, m0, n0, pad;
+  int inst, m0, n0, K;
+  int M, N, bn, pad0;
+  float* C;
+  int64_t ldc;
+  float alpha, beta;
+  int pad1[2];
 };
+static_assert(sizeof(GroupTile) == 64, "one 64-byte record per tile");
 struct GroupParams {
   const GroupInst* insts;
   const GroupTile* tiles;
@@ -673,20 +681,28 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + BN - 1) / BN;
   const int num_tiles = GROUPED ? gp.num_tiles : tiles_m * tiles_n;
 
-  auto view = [&](int t) {
+  // GROUPED: tile t's record (an empty one past the end); the roles load the
+  // next tile's record while they work on the current one
+  auto fetch = [&](int t) {
+    GroupTile gt{};
+    if constexpr (GROUPED) {
+      if (t < num_tiles) gt = gp.tiles[t];
+    }
+    return gt;
+  };
+  auto view = [&](int t, const GroupTile& gt) {
     TileView v;
     if constexpr (GROUPED) {
-      const GroupTile gt = gp.tiles[t];
       const GroupInst* in = gp.insts + gt.inst;
       for (int i = 0; i < 4; ++i) v.tm[i] = &in->tm[i];
-      v.C = in->C;
-      v.ldc = in->ldc;
-      v.M = in->M;
-      v.N = in->N;
-      v.K = in->K;
-      v.bn = in->bn;
-      v.alpha = in->alpha;
-      v.beta = in->beta;
+      v.C = gt.C;
+      v.ldc = gt.ldc;
+      v.M = gt.M;
+      v.N = gt.N;
+      v.K = gt.K;
+      v.bn = gt.bn;
+      v.alpha = gt.alpha;
+      v.beta = gt.beta;
       v.m0 = gt.m0;
       v.n0 = gt.n0;
     } else {
@@ -764,8 +780,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       int it = 0;
       bool go = true;
+      GroupTile nx = fetch(unit);
       for (int t = unit; go && t < num_tiles; t += num_units) {
-        const TileView v = view(t);
+        const GroupTile cur = nx;
+        nx = fetch(t + num_units);
+        const TileView v = view(t, cur);
         const int num_kb = (v.K + BK - 1) / BK;
         const uint32_t b_rows = PAIR ? (uint32_t)C_::B_ROWS : (uint32_t)v.bn;
         const uint32_t bytes = C_::PLANES * (C_::A_SLAB + b_rows * C_::ROW_BYTES);
@@ -795,14 +814,24 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           issued = it + 1;
         }
+        if (GROUPED && t + num_units < num_tiles && nx.K > 0) {
+          // the next tile's instance: its tensor maps into the TMA unit's cache
+          // (an instance with K = 0 has none)
+          const GroupInst* in = gp.insts + nx.inst;
+          for (int i = 0; i < (NPROD == 3 ? 4 : 3); i += (NPROD == 3 ? 1 : 2))
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in->tm[i])) : "memory");
+        }
       }
     } else if (warp == 1 && lane == 0 && leader) {
       // ---- MMA issuer: per K chunk, a fresh accumulation in tensor-memory
       // buffer (chunk parity); three (or one) products per K step
       int it = 0, g = 0;
       bool go = true;
+      GroupTile nx = fetch(unit);
       for (int t = unit; go && t < num_tiles; t += num_units) {
-        const TileView v = view(t);
+        const GroupTile cur = nx;
+        nx = fetch(t + num_units);
+        const TileView v = view(t, cur);
         const int num_kb = (v.K + BK - 1) / BK;
         const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
         const int n_mma = GROUPED ? v.bn : BN;
@@ -906,8 +935,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int h = (warp - EPI_WARP0) >> 2;  // which half of the tile's columns
     int g = 0;
     bool go = true;
+    GroupTile nx = fetch(unit);
     for (int t = unit; go && t < num_tiles; t += num_units) {
-      const TileView v = view(t);
+      const GroupTile cur = nx;
+      nx = fetch(t + num_units);
+      const TileView v = view(t, cur);
       const int m_cta = v.m0 + (int)rank * BM;  // first row of this CTA's half
       const int num_kb = (v.K + BK - 1) / BK;
       const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
@@ -1495,7 +1527,22 @@ int tc_batch_build(TcBatch* b, std::string* err) {
   std::vector<int> tiles;
   batch_schedule(b->d, b->bn, &tiles);
   std::vector<GroupTile> gt(tiles.size() / 4);
-  for (size_t t = 0; t < gt.size(); ++t) gt[t] = GroupTile{tiles[4 * t], tiles[4 * t + 1], tiles[4 * t + 2], 0};
+  for (size_t t = 0; t < gt.size(); ++t) {
+    const GroupInst& in = insts[tiles[4 * t]];
+    GroupTile& g = gt[t];
+    memset(&g, 0, sizeof g);
+    g.inst = tiles[4 * t];
+    g.m0 = tiles[4 * t + 1];
+    g.n0 = tiles[4 * t + 2];
+    g.K = in.K;
+    g.M = in.M;
+    g.N = in.N;
+    g.bn = in.bn;
+    g.C = in.C;
+    g.ldc = in.ldc;
+    g.alpha = in.alpha;
+    g.beta = in.beta;
+  }
   if (upload(&b->d_insts, insts, err) || upload(&b->d_tiles, gt, err)) return -1;
   b->num_tiles = (int)gt.size();
   b->grid = std::max(1, std::min(b->num_tiles, num_sms()));
