@@ -207,3 +207,21 @@ def test_bounded_wait_gives_up_and_context_survives(cuda_device):
         assert O.normwise_rel_err(got, O.sgemm_f64(p)) <= 5e-6
     finally:
         H.hpvm_cleanup(ctx)
+
+
+@pytest.mark.parametrize("tier,tile_m", [(H.HPVM_TIER_BF16, 256), (H.HPVM_TIER_BF16X3, 128),
+                                         (H.HPVM_TIER_FP8, 128)])
+def test_tile_mapping_per_tier(dfg, tier, tile_m):
+    # plain BF16 runs on clusters of two CTAs (a 256 x 256 tile per pair),
+    # the other tensor tiers on single CTAs (128 x 256 tiles); the grid never
+    # exceeds the tiles (or their CTAs) and pairs launch an even grid
+    M, N, K = 700, 600, 96
+    p = W.sgemm_problem(M, N, K, seed=4, alpha=1.0, beta=0.5)
+    got, info, _ = run(dfg, p, tier)
+    assert info["tile_m"] == tile_m and info["tile_n"] == 256
+    tiles = -(-M // tile_m) * -(-N // 256)
+    per_tile = tile_m // 128
+    assert info["grid_x"] == min(tiles * per_tile, info["grid_x"]) and info["grid_x"] % per_tile == 0
+    assert info["grid_x"] <= tiles * per_tile
+    tol = 6e-2 if tier == H.HPVM_TIER_FP8 else TOL[tier]
+    assert O.normwise_rel_err(got, O.sgemm_f64(p)) <= tol
