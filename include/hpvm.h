@@ -102,6 +102,26 @@ extern "C" {
                                   stream (use inside CUDA graph capture) */
 #define HPVM_LAUNCH_NO_FUSION 2 /* run a dependent elementwise leaf as its own
                                    kernel instead of merging it */
+/* Operand plane cache (tensor tiers; no counterpart in the paper). The
+ * BF16x3, BF16 and FP8 leaves read op(A) and op(B) as K-major BF16 / E4M3
+ * planes converted from the FP32 operands. With these flags a stage keeps
+ * the planes of an operand in its context, keyed by (device pointer, leading
+ * dimension, rows, K, layout, tier), so that later launches can skip the
+ * conversion:
+ *   CACHE: convert op(X) into the cache (replacing what an entry with the
+ *          same key held) and keep it;
+ *   REUSE: the caller guarantees op(X) holds the values it held when its
+ *          planes were cached: use them (converting and caching if the
+ *          cache has none). Reusing planes of an operand that changed
+ *          gives the product of the old values.
+ * Launches on other streams that read or refill an entry are ordered by
+ * CUDA events. The cache grows up to 4 GiB; beyond that operands are
+ * converted into the workspace as without the flags. hpvm_drop_planes
+ * frees it. */
+#define HPVM_LAUNCH_CACHE_A 4
+#define HPVM_LAUNCH_REUSE_A 8
+#define HPVM_LAUNCH_CACHE_B 16
+#define HPVM_LAUNCH_REUSE_B 32
 
 typedef struct hpvm_ctx hpvm_ctx;
 typedef struct hpvm_node hpvm_node;
@@ -278,6 +298,11 @@ HPVM_API int hpvm_workspace_size(hpvm_ctx* ctx, hpvm_node* root, const void* arg
 /* Use caller-owned device memory as workspace (NULL/0: the runtime
  * allocates and caches its own). Must stay valid while launches use it. */
 HPVM_API int hpvm_set_workspace(hpvm_ctx* ctx, void* dev_ptr, size_t bytes);
+/* The operand plane cache (HPVM_LAUNCH_CACHE_* / REUSE_*): its size in bytes,
+ * and freeing it (after every launch that reads a cached plane has finished;
+ * blocks the calling thread until then). */
+HPVM_API int hpvm_plane_cache_bytes(hpvm_ctx* ctx, int64_t* bytes);
+HPVM_API int hpvm_drop_planes(hpvm_ctx* ctx);
 
 /* ---- planning -----------------------------------------------------------
  * Leaf instance grid and internal grid for an M x N result in `tier`:

@@ -46,6 +46,10 @@ HPVM_TIER_FP8 = 4
 
 HPVM_LAUNCH_NO_EVENT = 1
 HPVM_LAUNCH_NO_FUSION = 2
+HPVM_LAUNCH_CACHE_A = 4
+HPVM_LAUNCH_REUSE_A = 8
+HPVM_LAUNCH_CACHE_B = 16
+HPVM_LAUNCH_REUSE_B = 32
 HPVM_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 HPVM_ROOTIN_PAPER_BYTES = 88
 HPVM_SGEMM_ROOT_ARGS_BYTES = 136
@@ -138,6 +142,8 @@ def _load() -> ctypes.CDLL:
         "hpvm_untrack_mem": (I, [P, P]),
         "hpvm_workspace_size": (I, [P, P, P, SZ, ctypes.POINTER(ctypes.c_size_t)]),
         "hpvm_set_workspace": (I, [P, P, SZ]),
+        "hpvm_plane_cache_bytes": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "hpvm_drop_planes": (I, [P]),
         "hpvm_plan_sgemm": (I, [I, I64, I64, I64] + [ctypes.POINTER(ctypes.c_int32)] * 4),
         "hpvm_set_kernel_timing": (I, [P, I]),
         "hpvm_kernel_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
@@ -285,6 +291,16 @@ def hpvm_workspace_size(ctx: int, root: int, args) -> int:
 
 def hpvm_set_workspace(ctx: int, ptr: int | None, nbytes: int) -> None:
     _check(LIB.hpvm_set_workspace(ctx, ptr, int(nbytes)))
+
+
+def hpvm_plane_cache_bytes(ctx: int) -> int:
+    v = ctypes.c_int64()
+    _check(LIB.hpvm_plane_cache_bytes(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def hpvm_drop_planes(ctx: int) -> None:
+    _check(LIB.hpvm_drop_planes(ctx))
 
 
 def hpvm_plan_sgemm(tier: int, M: int, N: int, K: int) -> tuple[int, int, int, int]:

@@ -176,12 +176,14 @@ class ChainEngine:
         for g in pending:
             H.hpvm_wait(g, timeout_ms)
 
-    def chain_records(self, X: torch.Tensor, Ws, outs):
-        """Records of the chain graph: stage l computes outs[l] = act(in_l) W_l."""
+    def chain_records(self, X: torch.Tensor, Ws, outs, plane_flags: int = 0):
+        """Records of the chain graph: stage l computes outs[l] = act(in_l) W_l.
+        plane_flags (HPVM_LAUNCH_CACHE_A / REUSE_A) applies to the weights,
+        the stages' A operands."""
         arr = (H.RootArgs * self.layers)()
         for l in range(self.layers):
             src = X if l == 0 else outs[l - 1]
-            arr[l] = _rm_product_args(outs[l], src, Ws[l], self.tier, self.flags)
+            arr[l] = _rm_product_args(outs[l], src, Ws[l], self.tier, self.flags | plane_flags)
             if l > 0:  # B arrives over the streaming edge
                 arr[l].B = None
                 arr[l].bytesB = 0
@@ -192,7 +194,9 @@ class ChainEngine:
         """Y for row-major X (rows x w). With keep, also the activations
         H_1..H_{L-1} (the tanh outputs, the chain's intermediate buffers)."""
         outs = [torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws]
-        self._run(self.chain, self.chain_records(X, Ws, outs))
+        # the weights' planes are made afresh (the weights may have changed
+        # since the last call) and kept for the recomputation in backward
+        self._run(self.chain, self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_CACHE_A))
         return (outs[-1], outs[:-1]) if keep else outs[-1]
 
     def recompute(self, X: torch.Tensor, Ws):
@@ -200,7 +204,9 @@ class ChainEngine:
         Hs = [X]
         for l in range(self.layers - 1):
             out = torch.empty(X.shape[0], Ws[l].shape[1], device=X.device)
-            self._run(self.stage_tanh, _rm_product_args(out, Hs[-1], Ws[l], self.tier, self.flags))
+            # autograd guarantees the saved weights are unchanged since forward
+            self._run(self.stage_tanh, _rm_product_args(out, Hs[-1], Ws[l], self.tier,
+                                                        self.flags | H.HPVM_LAUNCH_REUSE_A))
             Hs.append(out)
         return Hs
 
@@ -246,8 +252,10 @@ class ChainEngine:
         rec0 = self.chain_records(items[0], Ws, outs_all[0])
         g = H.hpvm_launch(self.ctx, self.chain, rec0, True, self._stream())
         try:
-            for X, outs in zip(items, outs_all):
-                H.hpvm_push(g, self.chain_records(X, Ws, outs))
+            for i, (X, outs) in enumerate(zip(items, outs_all)):
+                # the weights are the same for every item: converted once
+                pf = H.HPVM_LAUNCH_CACHE_A if i == 0 else H.HPVM_LAUNCH_REUSE_A
+                H.hpvm_push(g, self.chain_records(X, Ws, outs, pf))
             popped = []
             for _ in items:
                 rec = (H.RootArgs * self.layers)()

@@ -82,10 +82,25 @@ void fp32_tiled_tile(int* tm, int* tn);
 size_t tc_workspace_bytes(const SgemmDesc& d, int tier);
 // Returns a cudaError_t; on a host-side precondition failure returns
 // cudaErrorInvalidValue and fills *err.
+// Planes of one operand kept outside the workspace (the context's plane
+// cache): `base` holds the hi plane, the lo plane (BF16x3) and the block
+// scales (FP8) at the offsets tc_operand_layout gives. ready: they already
+// hold the operand, so its conversion is skipped; otherwise it is converted
+// into them and `converted` (if set) is recorded on the stream right after.
+struct OperandPlanes {
+  void* base = nullptr;
+  bool ready = false;
+  cudaEvent_t converted = nullptr;
+};
+struct OperandLayout {
+  size_t hi = 0, lo = 0, scales = 0, total = 0;
+};
+OperandLayout tc_operand_layout(int tier, int64_t rows, int64_t K);
 cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes,
                       const DeviceStatus& st, cudaStream_t s,
                       KernelReport* rep, std::string* err,
-                      const LaunchHooks* hooks, const Epilogue& epi = Epilogue());
+                      const LaunchHooks* hooks, const Epilogue& epi = Epilogue(),
+                      const OperandPlanes& pa = OperandPlanes(), const OperandPlanes& pb = OperandPlanes());
 void tc_tile(int tier, int* tm, int* tn);
 
 // ---- batches of independent instances (tc_leaf.cu) ------------------------

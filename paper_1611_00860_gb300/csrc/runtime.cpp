@@ -171,6 +171,23 @@ struct hpvm_batch {
   uint64_t signature = 0;
 };
 
+// One operand's planes in the context's plane cache (HPVM_LAUNCH_CACHE_* /
+// REUSE_*): the key, the device buffer, whether it holds the operand, the
+// event recorded after its conversion, and per stream the event recorded
+// after the last launch there that read it (a refill waits for those).
+struct PlaneEntry {
+  const void* src = nullptr;
+  int64_t ld = 0, rows = 0, K = 0;
+  int layout = 0, tier = 0;
+  void* buf = nullptr;
+  size_t bytes = 0;
+  bool valid = false;
+  cudaStream_t filled_on = nullptr;
+  cudaEvent_t converted = nullptr;
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
+};
+constexpr size_t kPlaneCacheLimit = size_t(4) << 30;
+
 struct hpvm_ctx {
   int device = -1;
   int next_id = 0;
@@ -186,6 +203,8 @@ struct hpvm_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed;  // main-kernel events
   std::set<hpvm_batch*> batches;
   std::vector<std::pair<uint64_t, int>> tuned;  // batch shape signature -> best policy
+  std::vector<std::unique_ptr<PlaneEntry>> planes;  // the operand plane cache
+  size_t plane_bytes = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -746,6 +765,96 @@ int ensure_workspace(hpvm_ctx* ctx, size_t need, void** ws, size_t* ws_bytes) {
 }
 
 // Enqueue every stage of a lowered graph on stream s.
+// Waits for every launch that reads a cached plane, then frees the cache.
+void free_planes(hpvm_ctx* ctx) {
+  for (auto& e : ctx->planes) {
+    for (auto& u : e->uses) {
+      cudaEventSynchronize(u.second);
+      cudaEventDestroy(u.second);
+    }
+    if (e->converted) {
+      cudaEventSynchronize(e->converted);
+      cudaEventDestroy(e->converted);
+    }
+    if (e->buf) cudaFree(e->buf);
+  }
+  ctx->planes.clear();
+  ctx->plane_bytes = 0;
+}
+
+// The plane cache entry of an operand (key: its device pointer, leading
+// dimension, rows, K, source layout and tier) and what the leaf does with
+// it: read its planes (reuse of a valid entry; on another stream only after
+// the event of its conversion) or convert into them (a refill waits for the
+// launches on other streams that still read them). *out stays null when the
+// cache has no room: the operand is then converted into the workspace.
+int plane_entry(hpvm_ctx* ctx, const void* src, int64_t ld, int64_t rows, int64_t K, int layout, int tier,
+                bool reuse, cudaStream_t s, PlaneEntry** out, hpvm::OperandPlanes* op) {
+  *out = nullptr;
+  *op = hpvm::OperandPlanes();
+  PlaneEntry* e = nullptr;
+  for (auto& p : ctx->planes)
+    if (p->src == src && p->ld == ld && p->rows == rows && p->K == K && p->layout == layout && p->tier == tier) {
+      e = p.get();
+      break;
+    }
+  if (!e) {
+    const size_t bytes = hpvm::tc_operand_layout(tier, rows, K).total;
+    if (ctx->plane_bytes + bytes > kPlaneCacheLimit) return HPVM_OK;
+    auto ne = std::make_unique<PlaneEntry>();
+    ne->src = src;
+    ne->ld = ld;
+    ne->rows = rows;
+    ne->K = K;
+    ne->layout = layout;
+    ne->tier = tier;
+    if (cudaMalloc(&ne->buf, bytes) != cudaSuccess) {
+      cudaGetLastError();  // no room on the device: convert into the workspace
+      return HPVM_OK;
+    }
+    cudaError_t c = cudaEventCreateWithFlags(&ne->converted, cudaEventDisableTiming);
+    if (c != cudaSuccess) {
+      cudaFree(ne->buf);
+      return cuda_fail(c, "cudaEventCreate");
+    }
+    ne->bytes = bytes;
+    ctx->plane_bytes += bytes;
+    e = ne.get();
+    ctx->planes.push_back(std::move(ne));
+  }
+  op->base = e->buf;
+  if (reuse && e->valid) {
+    if (e->filled_on != s) cudaStreamWaitEvent(s, e->converted, 0);
+    op->ready = true;
+  } else {
+    for (auto& u : e->uses)
+      if (u.first != s) cudaStreamWaitEvent(s, u.second, 0);
+    e->valid = false;
+    op->converted = e->converted;
+  }
+  *out = e;
+  return HPVM_OK;
+}
+
+// After a launch on stream s read (or filled) entry e.
+int plane_used(PlaneEntry* e, const hpvm::OperandPlanes& op, cudaStream_t s) {
+  if (!op.ready) {
+    e->valid = true;
+    e->filled_on = s;
+  }
+  for (auto& u : e->uses)
+    if (u.first == s) {
+      cudaError_t c = cudaEventRecord(u.second, s);
+      return c == cudaSuccess ? HPVM_OK : cuda_fail(c, "cudaEventRecord");
+    }
+  cudaEvent_t ev;
+  cudaError_t c = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (c == cudaSuccess) c = cudaEventRecord(ev, s);
+  if (c != cudaSuccess) return cuda_fail(c, "plane cache event");
+  e->uses.emplace_back(s, ev);
+  return HPVM_OK;
+}
+
 int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t ws_bytes, hpvm_launch_info* inf) {
   memset(inf, 0, sizeof *inf);
   int64_t h2d = 0;
@@ -785,6 +894,28 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
       // run it as its own kernel after the sgemm leaf.
       const bool tensor = tier >= HPVM_TIER_BF16X3;
       const bool fuse = tensor && !(flags & HPVM_LAUNCH_NO_FUSION);
+      // operand plane cache (A's rows are contiguous unless transposed, B's
+      // N rows only when transposed: the layouts the conversions read)
+      hpvm::OperandPlanes pa, pb;
+      PlaneEntry *ea = nullptr, *eb = nullptr;
+      if (tensor && S.d.K > 0) {
+        if ((flags & (HPVM_LAUNCH_CACHE_A | HPVM_LAUNCH_REUSE_A)) &&
+            (rc = plane_entry(ctx, S.d.A, S.d.lda, S.d.M, S.d.K, !S.d.transA, tier,
+                              !(flags & HPVM_LAUNCH_CACHE_A), s, &ea, &pa)) != HPVM_OK)
+          return rc;
+        if ((flags & (HPVM_LAUNCH_CACHE_B | HPVM_LAUNCH_REUSE_B)) &&
+            (rc = plane_entry(ctx, S.d.B, S.d.ldb, S.d.N, S.d.K, S.d.transB != 0, tier,
+                              !(flags & HPVM_LAUNCH_CACHE_B), s, &eb, &pb)) != HPVM_OK)
+          return rc;
+        if (ea && ea == eb) {
+          // one entry serves both operands (the same matrix): A's conversion,
+          // which the leaf launch runs first, fills it for both
+          pb = pa;
+          pb.ready = true;
+          pb.converted = nullptr;
+          eb = nullptr;
+        }
+      }
       hpvm::Epilogue none;
       cudaError_t e;
       switch (tier) {
@@ -796,11 +927,14 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
           e = hpvm::launch_fp32_tiled(S.d, s, &rep, &hooks);
           break;
         default:
-          e = hpvm::launch_tc(S.d, tier, ws, ws_bytes, ctx->status, s, &rep, &err, &hooks, fuse ? S.epi : none);
+          e = hpvm::launch_tc(S.d, tier, ws, ws_bytes, ctx->status, s, &rep, &err, &hooks, fuse ? S.epi : none,
+                              pa, pb);
           if (e == cudaErrorInvalidValue && !err.empty()) return fail(HPVM_ERR_SHAPE, "%s", err.c_str());
           break;
       }
       if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+      if (ea && (rc = plane_used(ea, pa, s)) != HPVM_OK) return rc;
+      if (eb && (rc = plane_used(eb, pb, s)) != HPVM_OK) return rc;
       if (S.epi.kind && !fuse) {
         e = hpvm::launch_elementwise(S.d, S.epi, s);
         if (e != cudaSuccess) return cuda_fail(e, "elementwise leaf launch");
@@ -925,6 +1059,7 @@ int hpvm_cleanup(hpvm_ctx* ctx) {
       hpvm::tc_batch_free(&b->tb);
       delete b;
     }
+    free_planes(ctx);
   }
   delete ctx;
   return ok();
@@ -1087,6 +1222,21 @@ int hpvm_set_workspace(hpvm_ctx* ctx, void* dev_ptr, size_t bytes) {
   ctx->ws = dev_ptr;
   ctx->ws_bytes = dev_ptr ? bytes : 0;
   ctx->ws_owned = false;
+  return ok();
+}
+
+int hpvm_plane_cache_bytes(hpvm_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return fail(HPVM_ERR_INVALID_ARG, "ctx or bytes is NULL");
+  *bytes = (int64_t)ctx->plane_bytes;
+  return ok();
+}
+
+int hpvm_drop_planes(hpvm_ctx* ctx) {
+  if (!ctx) return fail(HPVM_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->device >= 0) {
+    cudaSetDevice(ctx->device);
+    free_planes(ctx);
+  }
   return ok();
 }
 

@@ -1162,6 +1162,26 @@ WsLayout ws_layout(const SgemmDesc& d, int mode) {
   return L;
 }
 
+// The planes of one operand of `rows` rows (a plane cache entry): hi, then
+// lo (BF16x3), then the block scales (FP8), each 256-byte aligned.
+OperandLayout operand_layout(int64_t rows, int64_t K, int mode) {
+  OperandLayout L;
+  const int eb = mode == 8 ? 1 : 2;
+  const int64_t Kp = (K + 16 / eb - 1) / (16 / eb) * (16 / eb);
+  const size_t plane = align256((size_t)rows * Kp * eb);
+  size_t off = plane;
+  if (mode == 3) {
+    L.lo = off;
+    off += plane;
+  }
+  if (mode == 8) {
+    L.scales = off;
+    off += align256((size_t)((rows + FP8_BLOCK - 1) / FP8_BLOCK) * ((K + FP8_BLOCK - 1) / FP8_BLOCK) * 4);
+  }
+  L.total = off;
+  return L;
+}
+
 template <int NPROD>
 cudaError_t launch_split(const float* X, int64_t ld, bool mmajor, int rows, int K, int Kp,
                          __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
@@ -1281,7 +1301,8 @@ cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, int tiles,
 
 template <int MODE>
 cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStream_t s, KernelReport* rep,
-                   std::string* err, const LaunchHooks* hooks, const Epilogue& epi) {
+                   std::string* err, const LaunchHooks* hooks, const Epilogue& epi, const OperandPlanes& pa,
+                   const OperandPlanes& pb) {
   constexpr bool PAIR = pair_for_mode(MODE);
   constexpr int TM = PAIR ? 2 * BM : BM;
   using C_ = Cfg<MODE, PAIR>;
@@ -1296,23 +1317,44 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
   void* bl = w + L.b_lo;
   float* sa = reinterpret_cast<float*>(w + L.sa);
   float* sb = reinterpret_cast<float*>(w + L.sb);
+  if (pa.base) {  // op(A)'s planes live in the plane cache
+    const OperandLayout O = operand_layout(M, K, MODE);
+    uint8_t* b = static_cast<uint8_t*>(pa.base);
+    ah = b + O.hi;
+    al = b + O.lo;
+    sa = reinterpret_cast<float*>(b + O.scales);
+  }
+  if (pb.base) {
+    const OperandLayout O = operand_layout(N, K, MODE);
+    uint8_t* b = static_cast<uint8_t*>(pb.base);
+    bh = b + O.hi;
+    bl = b + O.lo;
+    sb = reinterpret_cast<float*>(b + O.scales);
+  }
   int kernels = 0;
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   if (K > 0) {
     // op(A) rows are contiguous when A is not transposed; op(B)'s N rows when B is
-    if (C_::FP8) {
-      e = launch_quant(d.A, d.lda, !d.transA, M, K, Kp, static_cast<uint8_t*>(ah), sa, L.nkb, s);
+    if (!pa.ready) {
+      if (C_::FP8)
+        e = launch_quant(d.A, d.lda, !d.transA, M, K, Kp, static_cast<uint8_t*>(ah), sa, L.nkb, s);
+      else
+        e = launch_split<NPROD>(d.A, d.lda, !d.transA, M, K, Kp, static_cast<__nv_bfloat16*>(ah),
+                                static_cast<__nv_bfloat16*>(al), s);
       if (e != cudaSuccess) return e;
-      e = launch_quant(d.B, d.ldb, d.transB != 0, N, K, Kp, static_cast<uint8_t*>(bh), sb, L.nkb, s);
-    } else {
-      e = launch_split<NPROD>(d.A, d.lda, !d.transA, M, K, Kp, static_cast<__nv_bfloat16*>(ah),
-                              static_cast<__nv_bfloat16*>(al), s);
-      if (e != cudaSuccess) return e;
-      e = launch_split<NPROD>(d.B, d.ldb, d.transB != 0, N, K, Kp, static_cast<__nv_bfloat16*>(bh),
-                              static_cast<__nv_bfloat16*>(bl), s);
+      if (pa.converted) cudaEventRecord(pa.converted, s);
+      kernels += 1;
     }
-    if (e != cudaSuccess) return e;
-    kernels += 2;
+    if (!pb.ready) {
+      if (C_::FP8)
+        e = launch_quant(d.B, d.ldb, d.transB != 0, N, K, Kp, static_cast<uint8_t*>(bh), sb, L.nkb, s);
+      else
+        e = launch_split<NPROD>(d.B, d.ldb, d.transB != 0, N, K, Kp, static_cast<__nv_bfloat16*>(bh),
+                                static_cast<__nv_bfloat16*>(bl), s);
+      if (e != cudaSuccess) return e;
+      if (pb.converted) cudaEventRecord(pb.converted, s);
+      kernels += 1;
+    }
   }
   alignas(64) CUtensorMap maps[4];
   memset(maps, 0, sizeof maps);
@@ -1634,7 +1676,7 @@ size_t tc_workspace_bytes(const SgemmDesc& d, int tier) { return ws_layout(d, mo
 
 cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, const DeviceStatus& st,
                       cudaStream_t s, KernelReport* rep, std::string* err, const LaunchHooks* hooks,
-                      const Epilogue& epi) {
+                      const Epilogue& epi, const OperandPlanes& pa, const OperandPlanes& pb) {
   if (d.M > INT32_MAX / 2 || d.N > INT32_MAX / 2 || d.K > INT32_MAX / 2) {
     *err = "M, N and K must each fit in 30 bits for the tensor-core tiers";
     return cudaErrorInvalidValue;
@@ -1643,9 +1685,13 @@ cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, c
     *err = "workspace too small or not 256-byte aligned";
     return cudaErrorInvalidValue;
   }
-  if (tier == 2) return run_tc<3>(d, ws, st, s, rep, err, hooks, epi);
-  if (tier == 4) return run_tc<8>(d, ws, st, s, rep, err, hooks, epi);
-  return run_tc<1>(d, ws, st, s, rep, err, hooks, epi);
+  if (tier == 2) return run_tc<3>(d, ws, st, s, rep, err, hooks, epi, pa, pb);
+  if (tier == 4) return run_tc<8>(d, ws, st, s, rep, err, hooks, epi, pa, pb);
+  return run_tc<1>(d, ws, st, s, rep, err, hooks, epi, pa, pb);
+}
+
+OperandLayout tc_operand_layout(int tier, int64_t rows, int64_t K) {
+  return operand_layout(rows, K, mode_of_tier(tier));
 }
 
 }  // namespace hpvm

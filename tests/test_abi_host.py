@@ -306,3 +306,14 @@ def test_chain_graph_lowers_on_host(ctx):
 def test_push_pop_need_a_streaming_graph(ctx):
     with pytest.raises(H.HpvmError):
         H.hpvm_pop(0)
+
+
+def test_plane_cache_on_a_host_only_context(ctx):
+    # nothing is cached without a device; dropping the empty cache is fine
+    assert H.hpvm_plane_cache_bytes(ctx) == 0
+    H.hpvm_drop_planes(ctx)
+    assert H.hpvm_plane_cache_bytes(ctx) == 0
+    flags = (H.HPVM_LAUNCH_CACHE_A, H.HPVM_LAUNCH_REUSE_A, H.HPVM_LAUNCH_CACHE_B, H.HPVM_LAUNCH_REUSE_B)
+    assert len(set(flags)) == 4 and all(f & (H.HPVM_LAUNCH_NO_EVENT | H.HPVM_LAUNCH_NO_FUSION) == 0 for f in flags)
+    with pytest.raises(H.HpvmError):
+        H.hpvm_plane_cache_bytes(None)
