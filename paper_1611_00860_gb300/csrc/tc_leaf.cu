@@ -55,12 +55,12 @@ constexpr int LAUNCH_REGS = 168;
 // 48/224 differ by variant, and each takes the one that spills least.
 template <int MODE, int EPI, bool PAIR>
 struct RegSplit {
-  static constexpr int EPI_R = ((MODE == 3 && EPI != 2 && !PAIR) || MODE == 8) ? 224 : 232;
+  static constexpr int EPI_R = (MODE == 8 || (MODE == 3 && EPI == 2)) ? 224 : 232;
   static constexpr int CTRL_R = EPI_R == 224 ? 48 : 40;
   static_assert(EPI_WARP0 * 32 * CTRL_R + EPI_WARPS * 32 * EPI_R <= THREADS * LAUNCH_REGS,
                 "register split exceeds the launch's registers");
 };
-constexpr uint32_t TMEM_COLS = 2 * BN;        // two FP32 BM x BN chunk buffers
+constexpr uint32_t TMEM_COLS = 2 * BN;        // all 512 columns: the FP32 chunk buffers
 constexpr int GROUP_N = 8;          // column tiles per rasterisation group
 constexpr uint32_t SMEM_BUDGET = 226 * 1024;  // of the 227 KB a block may have
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per bounded wait
@@ -86,7 +86,18 @@ struct Cfg {
   // already give 6 MMAs per slab and whose 4 planes need the smaller stages.
   static constexpr int ROW_BYTES = MODE == 3 ? 64 : 128;
   static constexpr uint32_t A_SLAB = BM * ROW_BYTES;  // bytes of one A plane slab
-  static constexpr int B_ROWS = PAIR ? BN / 2 : BN;     // rows of B this CTA stages
+  // Tile columns and tensor-memory buffers, and the split of a tile's
+  // columns between the two epilogue warps of a lane quarter (multiples of
+  // 32). Every leaf takes 256-column tiles in two buffers: narrower FP8
+  // tiles in more buffers (128 x 4, 160 x 3, 192 x 2) measured 1.7-1.9x
+  // slower at 8192, an MMA of N < 256 costing nearly as much as N = 256.
+  static constexpr int TN = BN;
+  static constexpr int NBUF = 2;
+  static constexpr int COLS0 = TN / 2;
+  static constexpr int COLS1 = TN - COLS0;
+  static constexpr int ACC = COLS0 > COLS1 ? COLS0 : COLS1;
+  static_assert(NBUF * TN <= (int)TMEM_COLS && COLS0 % 32 == 0 && COLS1 % 32 == 0, "tensor-memory buffers");
+  static constexpr int B_ROWS = PAIR ? TN / 2 : TN;     // rows of B this CTA stages
   static constexpr uint32_t B_SLAB = B_ROWS * ROW_BYTES;  // bytes of one B plane slab
   static constexpr int BK = ROW_BYTES / ELEM_BYTES;   // K elements per slab
   static constexpr int MMA_K = 32 / ELEM_BYTES;           // K per tcgen05.mma
@@ -102,7 +113,7 @@ struct Cfg {
   static constexpr int STAGES = (int)((SMEM_BUDGET - 1536) / STAGE_BYTES) > 8
                                     ? 8 : (int)((SMEM_BUDGET - 1536) / STAGE_BYTES);
   static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
-  static_assert(2 * STAGES * 8 + 4 * 8 + 8 <= 512, "barrier area");
+  static_assert(2 * STAGES * 8 + 2 * NBUF * 8 + 8 <= 512, "barrier area");
   static_assert(MODE == 1 || KC_SLABS * BK == 128, "chunk of 128 K elements");
 };
 
@@ -351,6 +362,32 @@ __device__ __forceinline__ void cta_barrier_all() {
   asm volatile("barrier.sync 1, %0;" ::"n"(THREADS) : "memory");
 }
 
+// A 32-column tensor-memory load without its wait (several go in flight),
+// and the wait that ends them; the wait takes the loaded registers as
+// operands so nothing that reads them can be scheduled before it.
+__device__ __forceinline__ void tmem_ld_x32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld_into(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                 "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                 "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]),
+                 "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]),
+                 "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
 // Two 32-column tensor-memory loads in flight before one wait.
 __device__ __forceinline__ void tmem_ld_2x32(uint32_t taddr0, uint32_t taddr1, uint32_t (&r)[32],
                                              uint32_t (&s)[32]) {
@@ -582,13 +619,14 @@ __global__ void __launch_bounds__(QTHREADS) quant_fp8(const float* __restrict__ 
 // Persistent: CTA b handles tiles b, b + gridDim.x, ... in a grouped order
 // (GROUP_N column tiles at a time, M fastest) so CTAs that run together share
 // operand panels in L2.
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int tile_rows, int* m0, int* n0) {
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int tile_rows, int tile_cols, int* m0,
+                                            int* n0) {
   const int group = GROUP_N * tiles_m;
   const int g = t / group, r = t % group;
   const int first_n = g * GROUP_N;
   const int gn = min(GROUP_N, tiles_n - first_n);
   *m0 = (r / gn) * tile_rows;
-  *n0 = (first_n + r % gn) * BN;
+  *n0 = (first_n + r % gn) * tile_cols;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -666,9 +704,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * C_::STAGE_BYTES);
   uint64_t* empty = full + S;
-  uint64_t* tfull = empty + S;   // [2] MMA -> epilogue: chunk accumulated in buffer b
-  uint64_t* tempty = tfull + 2;  // [2] epilogue -> MMA: buffer b read out
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* tfull = empty + S;      // [NBUF] MMA -> epilogue: chunk accumulated in buffer b
+  uint64_t* tempty = tfull + C_::NBUF;  // [NBUF] epilogue -> MMA: buffer b read out
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + C_::NBUF);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -678,7 +716,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int num_units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   // the peer's abort flag (raised with ours, so it stops waiting for us)
   const uint32_t peer_abort = PAIR ? mapa_rank(smem_u32((const void*)abort_flag), rank ^ 1u) : 0u;
-  const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + BN - 1) / BN;
+  constexpr int TN = C_::TN, NBUF = C_::NBUF;
+  const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + TN - 1) / TN;
   const int num_tiles = GROUPED ? gp.num_tiles : tiles_m * tiles_n;
 
   // GROUPED: tile t's record (an empty one past the end); the roles load the
@@ -715,10 +754,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       v.M = p.M;
       v.N = p.N;
       v.K = p.K;
-      v.bn = BN;
+      v.bn = TN;
       v.alpha = p.alpha;
       v.beta = p.beta;
-      tile_coords(t, tiles_m, tiles_n, TM, &v.m0, &v.n0);
+      tile_coords(t, tiles_m, tiles_n, TM, TN, &v.m0, &v.n0);
     }
     return v;
   };
@@ -734,7 +773,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NBUF; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], PAIR ? 2 * EPI_WARPS : EPI_WARPS);  // PAIR: both CTAs' epilogues
     }
@@ -834,18 +873,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         const TileView v = view(t, cur);
         const int num_kb = (v.K + BK - 1) / BK;
         const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
-        const int n_mma = GROUPED ? v.bn : BN;
+        const int n_mma = GROUPED ? v.bn : TN;
         const uint32_t idesc = C_::FP8 ? idesc_e4m3(TM, n_mma) : idesc_bf16(TM, n_mma);
         for (int c = 0; go && c < num_chunks; ++c, ++g) {
-          const int buf = g & 1;
-          const uint32_t use = (uint32_t)(g >> 1);
+          const int buf = g % NBUF;
+          const uint32_t use = (uint32_t)(g / NBUF);
           if (!mbar_wait<PAIR>(&tempty[buf], (use & 1) ^ 1, abort_flag, p.status, ST_MMA, WAIT_LIMIT_NS,
                                peer_abort)) {
             go = false;
             break;
           }
           tc_fence_after();
-          const uint32_t dst = tmem + buf * BN;
+          const uint32_t dst = tmem + buf * TN;
           const int kb_end = min(num_kb, (c + 1) * KC_SLABS);
           for (int kb = c * KC_SLABS; kb < kb_end; ++kb, ++it) {
             const int s = it % S;
@@ -943,19 +982,23 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int m_cta = v.m0 + (int)rank * BM;  // first row of this CTA's half
       const int num_kb = (v.K + BK - 1) / BK;
       const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
-      const int half = GROUPED ? v.bn / 2 : BN / 2;  // columns this warp owns
-      float acc[BN / 2];
+      // the columns this warp owns: [coff, coff + cols) of the tile
+      const int cols = GROUPED ? v.bn / 2 : (h ? C_::COLS1 : C_::COLS0);
+      const int coff = GROUPED ? h * (v.bn / 2) : (h ? C_::COLS0 : 0);
+      constexpr int ACC = C_::ACC;
+      float acc[ACC];
 #pragma unroll
-      for (int u = 0; u < BN / 2; ++u) acc[u] = 0.f;
+      for (int u = 0; u < ACC; ++u) acc[u] = 0.f;
       // FP8: this warp's 128 columns are exactly one 128-wide block of
       // op(B)^T rows and this CTA's tile rows one block of op(A) rows
+      static_assert(!C_::FP8 || (C_::COLS0 == FP8_BLOCK && C_::COLS1 == FP8_BLOCK), "one scale block per warp");
+      const bool live = v.n0 + coff < v.N && m_cta < v.M;
       const float* sa = nullptr;
       const float* sb = nullptr;
       if (C_::FP8) {
         sa = p.scaleA + (int64_t)(m_cta / FP8_BLOCK) * p.nkb;
-        sb = p.scaleB + (int64_t)((v.n0 + h * (BN / 2)) / FP8_BLOCK) * p.nkb;
+        sb = p.scaleB + (int64_t)((v.n0 + coff) / FP8_BLOCK) * p.nkb;
       }
-      const bool live = v.n0 + h * half < v.N && m_cta < v.M;
       // FP8: the block scales of chunks c and c + 1, loaded two chunks ahead
       // so their L2 round trips stay off the chunk-to-chunk critical path
       float sa0 = 0.f, sb0 = 0.f, sa1 = 0.f, sb1 = 0.f;
@@ -964,9 +1007,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (num_chunks > 1) sa1 = __ldg(sa + 1), sb1 = __ldg(sb + 1);
       }
       for (int c = 0; c < num_chunks; ++c, ++g) {
-        const int buf = g & 1;
-        const uint32_t use = (uint32_t)(g >> 1);
-        float scale = 1.f;
+        const int buf = g % NBUF;
+        const uint32_t use = (uint32_t)(g / NBUF);
+        float scale = 1.f;  // FP8: the chunk's sA * sB
         if (C_::FP8) {
           scale = sa0 * sb0;
           sa0 = sa1;
@@ -979,24 +1022,49 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc_fence_after();
         __syncwarp();
-        const uint32_t src = tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * BN + h * half;
+        const uint32_t src = tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * TN + coff;
+        if constexpr (ACC <= 96) {
+          // every 32-column load of this warp in flight before one wait
+          uint32_t r[ACC / 32][32];
 #pragma unroll
-        for (int i = 0; i < BN / 64; i += 2) {
-          // 64 columns per step, two loads in flight (half is a multiple of 32;
-          // a 32-wide half of a 64-column tile takes the single-load path)
-          if (i * 32 + 32 < half) {
-            uint32_t r[32], r2[32];
-            tmem_ld_2x32(src + i * 32, src + i * 32 + 32, r, r2);
+          for (int i = 0; i < ACC / 32; ++i)
+            if (i * 32 < cols) tmem_ld_x32_issue(src + i * 32, r[i]);
 #pragma unroll
-            for (int u = 0; u < 32; u += 2) ffma2(acc[i * 32 + u], acc[i * 32 + u + 1], scale, r[u], r[u + 1]);
+          for (int i = 0; i < ACC / 32; ++i)
+            if (i * 32 < cols) tmem_wait_ld_into(r[i]);
 #pragma unroll
-            for (int u = 0; u < 32; u += 2)
-              ffma2(acc[i * 32 + 32 + u], acc[i * 32 + 33 + u], scale, r2[u], r2[u + 1]);
-          } else if (i * 32 < half) {
-            uint32_t r[32];
-            tmem_ld_x32(src + i * 32, r);
+          for (int i = 0; i < ACC / 32; ++i) {
+            if (i * 32 < cols) {
 #pragma unroll
-            for (int u = 0; u < 32; u += 2) ffma2(acc[i * 32 + u], acc[i * 32 + u + 1], scale, r[u], r[u + 1]);
+              for (int u = 0; u < 32; u += 2) {
+                ffma2(acc[i * 32 + u], acc[i * 32 + u + 1], scale, r[i][u], r[i][u + 1]);
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < ACC / 32; i += 2) {
+            // 64 columns per step, two loads in flight (cols is a multiple of
+            // 32; a 32-column warp share takes the single-load path)
+            if (i * 32 + 32 < cols) {
+              uint32_t r[32], r2[32];
+              tmem_ld_2x32(src + i * 32, src + i * 32 + 32, r, r2);
+#pragma unroll
+              for (int u = 0; u < 32; u += 2) {
+                ffma2(acc[i * 32 + u], acc[i * 32 + u + 1], scale, r[u], r[u + 1]);
+              }
+#pragma unroll
+              for (int u = 0; u < 32; u += 2) {
+                ffma2(acc[i * 32 + 32 + u], acc[i * 32 + 33 + u], scale, r2[u], r2[u + 1]);
+              }
+            } else if (i * 32 < cols) {
+              uint32_t r[32];
+              tmem_ld_x32(src + i * 32, r);
+#pragma unroll
+              for (int u = 0; u < 32; u += 2) {
+                ffma2(acc[i * 32 + u], acc[i * 32 + u + 1], scale, r[u], r[u + 1]);
+              }
+            }
           }
         }
         tc_fence_before();
@@ -1016,11 +1084,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int tn = t + num_units;
         if (tn < num_tiles) {
           int nm0, nn0;
-          tile_coords(tn, tiles_m, tiles_n, TM, &nm0, &nn0);
+          tile_coords(tn, tiles_m, tiles_n, TM, TN, &nm0, &nn0);
           const int r0 = nm0 + (int)rank * BM + q * 32;  // this warp's 32 rows there
-          const int c0 = nn0 + h * (BN / 2);
+          const int c0 = nn0 + coff;
           if (r0 < p.M && c0 < p.N) {
-            const int nc = min(BN / 2, p.N - c0);
+            const int nc = min(cols, p.N - c0);
             for (int u = lane; u < nc; u += 32) {
               if (p.beta != 0.f) prefetch_l2(p.C + r0 + (int64_t)(c0 + u) * p.ldc);
               if (EPI == 2) prefetch_l2(p.aux + r0 + (int64_t)(c0 + u) * p.ldaux);
@@ -1029,16 +1097,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       const int row = m_cta + q * 32 + lane;
-      const int col0 = v.n0 + h * half;
+      const int col0 = v.n0 + coff;
       if (row < v.M) {
         // C in groups of CGRP columns: all loads of old C values first, so
         // their DRAM round trips overlap, then the stores (streaming hints:
         // C is touched once and should not displace operand panels in L2)
         float* cp = v.C + row + (int64_t)col0 * v.ldc;
-        const int ncols = min(half, v.N - col0);
+        const int ncols = min(cols, v.N - col0);
         constexpr int CGRP = EPI == 2 ? 4 : 8;  // the tanh adjoint also reads H
 #pragma unroll
-        for (int u0 = 0; u0 < BN / 2; u0 += CGRP) {
+        for (int u0 = 0; u0 < ACC; u0 += CGRP) {
           float old[CGRP];
           if (v.beta != 0.f) {
 #pragma unroll
@@ -1373,7 +1441,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
     }
   }
   TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, st.dev, epi.aux, epi.ldaux};
-  const int tiles = ((M + TM - 1) / TM) * ((N + BN - 1) / BN);
+  const int tiles = ((M + TM - 1) / TM) * ((N + C_::TN - 1) / C_::TN);
   int grid_ctas = 0;
   hook_begin(hooks, s);
   if (epi.kind == 1) e = launch_leaf<MODE, 1, PAIR>(maps, prm, tiles, s, &grid_ctas);
@@ -1386,7 +1454,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
     rep->kernels = kernels;
     rep->grid_x = grid_ctas; rep->grid_y = 1; rep->grid_z = 1;
     rep->block_threads = THREADS;
-    rep->tile_m = TM; rep->tile_n = BN; rep->tile_k = C_::BK;
+    rep->tile_m = TM; rep->tile_n = C_::TN; rep->tile_k = C_::BK;
     rep->smem_bytes = (int)C_::SMEM_BYTES;
     rep->literal = 0;
     rep->workspace_bytes = (int64_t)L.total;
@@ -1668,8 +1736,10 @@ namespace {
 }  // namespace
 
 void tc_tile(int tier, int* tm, int* tn) {
-  *tm = pair_for_mode(mode_of_tier(tier)) ? 2 * BM : BM;  // a CTA pair's tile, or one CTA's
-  *tn = BN;
+  const int mode = mode_of_tier(tier);
+  *tm = pair_for_mode(mode) ? 2 * BM : BM;  // a CTA pair's tile, or one CTA's
+  *tn = Cfg<1>::TN;
+  (void)mode;
 }
 
 size_t tc_workspace_bytes(const SgemmDesc& d, int tier) { return ws_layout(d, mode_of_tier(tier)).total; }

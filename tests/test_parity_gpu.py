@@ -209,17 +209,17 @@ def test_bounded_wait_gives_up_and_context_survives(cuda_device):
         H.hpvm_cleanup(ctx)
 
 
-@pytest.mark.parametrize("tier,tile_m", [(H.HPVM_TIER_BF16, 256), (H.HPVM_TIER_BF16X3, 128),
-                                         (H.HPVM_TIER_FP8, 128)])
-def test_tile_mapping_per_tier(dfg, tier, tile_m):
+@pytest.mark.parametrize("tier,tile_m,tile_n", [(H.HPVM_TIER_BF16, 256, 256), (H.HPVM_TIER_BF16X3, 128, 256),
+                                                (H.HPVM_TIER_FP8, 128, 256)])
+def test_tile_mapping_per_tier(dfg, tier, tile_m, tile_n):
     # plain BF16 runs on clusters of two CTAs (a 256 x 256 tile per pair),
-    # the other tensor tiers on single CTAs (128 x 256 tiles); the grid never
-    # exceeds the tiles (or their CTAs) and pairs launch an even grid
+    # BF16x3 and FP8 on single CTAs (128 x 256); the grid never exceeds the
+    # tiles (or their CTAs) and pairs launch an even grid
     M, N, K = 700, 600, 96
     p = W.sgemm_problem(M, N, K, seed=4, alpha=1.0, beta=0.5)
     got, info, _ = run(dfg, p, tier)
-    assert info["tile_m"] == tile_m and info["tile_n"] == 256
-    tiles = -(-M // tile_m) * -(-N // 256)
+    assert info["tile_m"] == tile_m and info["tile_n"] == tile_n
+    tiles = -(-M // tile_m) * -(-N // tile_n)
     per_tile = tile_m // 128
     assert info["grid_x"] == min(tiles * per_tile, info["grid_x"]) and info["grid_x"] % per_tile == 0
     assert info["grid_x"] <= tiles * per_tile
