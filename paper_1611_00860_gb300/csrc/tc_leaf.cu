@@ -80,11 +80,12 @@ struct Cfg {
   static constexpr bool FP8 = MODE == 8;
   static constexpr int PLANES = MODE == 3 ? 2 : 1;
   static constexpr int ELEM_BYTES = FP8 ? 1 : 2;
-  // One K slab row in shared memory: 128 bytes (128-byte swizzle) for BF16
-  // and FP8, so a slab carries 4 MMAs and the per-slab handshake is paid
-  // once per 4; 64 bytes (64-byte swizzle) for BF16x3, whose 3 products
-  // already give 6 MMAs per slab and whose 4 planes need the smaller stages.
-  static constexpr int ROW_BYTES = MODE == 3 ? 64 : 128;
+  // One K slab row in shared memory: 128 bytes (128-byte swizzle), so a
+  // slab carries 4 K steps and the per-slab handshake is paid once per 4.
+  // BF16x3 on a single CTA (the batch) keeps 64-byte rows (64-byte swizzle):
+  // its 4 planes of 384 rows would leave two 96 KiB stages; on a pair each
+  // CTA stages 256 rows and three 64 KiB stages fit.
+  static constexpr int ROW_BYTES = (MODE == 3 && !PAIR) ? 64 : 128;
   static constexpr uint32_t A_SLAB = BM * ROW_BYTES;  // bytes of one A plane slab
   // Tile columns and tensor-memory buffers, and the split of a tile's
   // columns between the two epilogue warps of a lane quarter (multiples of
@@ -1104,7 +1105,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         // C is touched once and should not displace operand panels in L2)
         float* cp = v.C + row + (int64_t)col0 * v.ldc;
         const int ncols = min(cols, v.N - col0);
-        constexpr int CGRP = EPI == 2 ? 4 : 8;  // the tanh adjoint also reads H
+        // 16 columns per group (8 and 32 measured 1% slower at 8192); 4 for the
+        // tanh adjoint, which also reads H
+        constexpr int CGRP = EPI == 2 ? 4 : 16;
 #pragma unroll
         for (int u0 = 0; u0 < ACC; u0 += CGRP) {
           float old[CGRP];
@@ -1311,10 +1314,13 @@ cudaError_t check_register_split(Kern* kernel) {
 // Which leaves of a single instance run on CTA pairs (256 x 256 tiles,
 // cta_group::2) rather than on single CTAs (128 x 256 tiles). Measured at
 // M = N = K = 8192 and 16384: pairs make plain BF16 (one accumulation per
-// tile) 5-10% faster; BF16x3 runs the same either way; FP8, which hands a
-// tensor-memory buffer between the MMA and epilogue warps every 128 K, runs
-// 2.3x slower, its hand-offs now crossing CTAs. So only BF16 pairs.
-constexpr bool pair_for_mode(int mode) { return mode == 1; }
+// tile) 5-10% faster; BF16x3 on pairs with 128-byte slab rows is 4% faster
+// than on single CTAs with 64-byte rows (1.90 vs 1.98 ms at 8192; with
+// 64-byte rows on pairs, or 128-byte rows in two stages on single CTAs, it
+// is not faster); FP8, which hands a tensor-memory buffer between the MMA
+// and epilogue warps every 128 K, runs 2.3x slower on pairs, its hand-offs
+// then crossing CTAs. So BF16 and BF16x3 run on pairs, FP8 on single CTAs.
+constexpr bool pair_for_mode(int mode) { return mode == 1 || mode == 3; }
 
 // The single-instance leaf, persistent: PAIR runs clusters of 2, one cluster
 // per 256 x 256 tile at a time, as many clusters as fit on the GPU at once;

@@ -209,11 +209,11 @@ def test_bounded_wait_gives_up_and_context_survives(cuda_device):
         H.hpvm_cleanup(ctx)
 
 
-@pytest.mark.parametrize("tier,tile_m,tile_n", [(H.HPVM_TIER_BF16, 256, 256), (H.HPVM_TIER_BF16X3, 128, 256),
+@pytest.mark.parametrize("tier,tile_m,tile_n", [(H.HPVM_TIER_BF16, 256, 256), (H.HPVM_TIER_BF16X3, 256, 256),
                                                 (H.HPVM_TIER_FP8, 128, 256)])
 def test_tile_mapping_per_tier(dfg, tier, tile_m, tile_n):
-    # plain BF16 runs on clusters of two CTAs (a 256 x 256 tile per pair),
-    # BF16x3 and FP8 on single CTAs (128 x 256); the grid never exceeds the
+    # plain BF16 and BF16x3 run on clusters of two CTAs (a 256 x 256 tile
+    # per pair), FP8 on single CTAs (128 x 256); the grid never exceeds the
     # tiles (or their CTAs) and pairs launch an even grid
     M, N, K = 700, 600, 96
     p = W.sgemm_problem(M, N, K, seed=4, alpha=1.0, beta=0.5)
