@@ -1105,9 +1105,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         // C is touched once and should not displace operand panels in L2)
         float* cp = v.C + row + (int64_t)col0 * v.ldc;
         const int ncols = min(cols, v.N - col0);
-        // 16 columns per group (8 and 32 measured 1% slower at 8192); 4 for the
-        // tanh adjoint, which also reads H
-        constexpr int CGRP = EPI == 2 ? 4 : 16;
+        // 16 columns per group (8 measured 1% slower at 8192, 32 no faster);
+        // 8 for the tanh adjoint, which also reads H (4 made the chain's
+        // training step 5% slower, 16 columns of H alone no faster)
+        constexpr int CGRP = EPI == 2 ? 8 : 16;
 #pragma unroll
         for (int u0 = 0; u0 < ACC; u0 += CGRP) {
           float old[CGRP];
