@@ -75,13 +75,16 @@ def _add_stage(ctx: int, root: int, base: int, ew_kind: int | None, b_from_edge:
     return st
 
 
-def build_chain_graph(ctx: int, layers: int) -> int:
-    """Root -> ``layers`` stages, tanh merged into every stage but the last,
-    stage l's result streamed into stage l+1's B. Returns the root."""
+def build_chain_graph(ctx: int, layers: int, tanh_last: bool = False) -> int:
+    """Root -> ``layers`` stages, tanh merged into every stage but the last
+    (into the last too with ``tanh_last``: the recomputation of the
+    activations), stage l's result streamed into stage l+1's B. Returns the
+    root."""
     root = H.hpvm_create_node(ctx, None, H.HPVM_NODE_INTERNAL)
     prev = None
     for l in range(layers):
-        st = _add_stage(ctx, root, REC * l, H.HPVM_NODE_TANH_LEAF if l + 1 < layers else None,
+        tanh = l + 1 < layers or tanh_last
+        st = _add_stage(ctx, root, REC * l, H.HPVM_NODE_TANH_LEAF if tanh else None,
                         b_from_edge=prev is not None)
         if prev is not None:
             H.hpvm_create_edge(prev, st, H.HPVM_ALL_TO_ALL, 0, 3, stream=True)
@@ -122,6 +125,8 @@ class ChainEngine:
         self.flags = 0 if fuse else H.HPVM_LAUNCH_NO_FUSION
         self.ctx = H.hpvm_init(device)
         self.chain = build_chain_graph(self.ctx, layers)
+        # H_1 .. H_{L-1} again in backward: the first L - 1 stages, all with tanh
+        self.rechain = build_chain_graph(self.ctx, layers - 1, tanh_last=True) if layers > 1 else None
         self.stage_tanh = build_single_stage_graph(self.ctx, H.HPVM_NODE_TANH_LEAF)
         self.stage_dtanh = build_single_stage_graph(self.ctx, H.HPVM_NODE_TANH_GRAD_LEAF)
         self.stage_plain = build_single_stage_graph(self.ctx, None)
@@ -177,11 +182,11 @@ class ChainEngine:
             H.hpvm_wait(g, timeout_ms)
 
     def chain_records(self, X: torch.Tensor, Ws, outs, plane_flags: int = 0):
-        """Records of the chain graph: stage l computes outs[l] = act(in_l) W_l.
-        plane_flags (HPVM_LAUNCH_CACHE_A / REUSE_A) applies to the weights,
-        the stages' A operands."""
-        arr = (H.RootArgs * self.layers)()
-        for l in range(self.layers):
+        """Records of a chain graph of len(Ws) stages: stage l computes
+        outs[l] = act(in_l) W_l. plane_flags (HPVM_LAUNCH_CACHE_A / REUSE_A)
+        applies to the weights, the stages' A operands."""
+        arr = (H.RootArgs * len(Ws))()
+        for l in range(len(Ws)):
             src = X if l == 0 else outs[l - 1]
             arr[l] = _rm_product_args(outs[l], src, Ws[l], self.tier, self.flags | plane_flags)
             if l > 0:  # B arrives over the streaming edge
@@ -200,15 +205,14 @@ class ChainEngine:
         return (outs[-1], outs[:-1]) if keep else outs[-1]
 
     def recompute(self, X: torch.Tensor, Ws):
-        """H_0 = X and H_l = tanh(H_{l-1} W_{l-1}) for l = 1..L-1, stage by stage."""
-        Hs = [X]
-        for l in range(self.layers - 1):
-            out = torch.empty(X.shape[0], Ws[l].shape[1], device=X.device)
-            # autograd guarantees the saved weights are unchanged since forward
-            self._run(self.stage_tanh, _rm_product_args(out, Hs[-1], Ws[l], self.tier,
-                                                        self.flags | H.HPVM_LAUNCH_REUSE_A))
-            Hs.append(out)
-        return Hs
+        """H_0 = X and H_l = tanh(H_{l-1} W_{l-1}) for l = 1..L-1: one launch
+        of the first L - 1 stages, every one with its tanh leaf merged."""
+        if self.rechain is None:
+            return [X]
+        outs = [torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws[:-1]]
+        # autograd guarantees the saved weights are unchanged since forward
+        self._run(self.rechain, self.chain_records(X, Ws[:-1], outs, H.HPVM_LAUNCH_REUSE_A))
+        return [X] + outs
 
     # -- backward -----------------------------------------------------------------
     def backward(self, X: torch.Tensor, Ws, G: torch.Tensor):

@@ -57,10 +57,16 @@ inline void hook_end(const LaunchHooks* h, cudaStream_t s) {
 
 // Elementwise leaf merged into (or run after) a sgemm leaf:
 // kind 1: C <- tanh(C); kind 2: C <- C * (1 - H^2) with H column-major (ldaux).
+// fwd (tensor-core BF16x3 and BF16 leaves only): the epilogue also writes
+// the operand planes of its result for a later leaf that reads this C as
+// op(B) = B with K = this M (a streaming edge between stages): column n of
+// C becomes plane row n, at the offsets tc_operand_layout(tier, N, M) gives
+// from fwd. Those planes equal what that leaf's own conversion of C makes.
 struct Epilogue {
   int kind = 0;
   const float* aux = nullptr;
   int64_t ldaux = 0;
+  void* fwd = nullptr;
 };
 // Standalone elementwise kernel on the M x N column-major C (fp32_leaf.cu).
 cudaError_t launch_elementwise(const SgemmDesc& d, const Epilogue& e, cudaStream_t s);

@@ -670,11 +670,51 @@ size_t workspace_need(const Stage& S, int tier) {
   return 0;
 }
 
-size_t plan_workspace(const Plan& P) {
-  size_t need = 0;
-  for (auto& S : P.stages) need = std::max(need, workspace_need(S, record_i32(P, S.rec, kTierOffset)));
-  return need;
+// Streaming edges lowered into the producer's epilogue: stage i's result C
+// is stage i+1's op(B) = B (K of stage i+1 = M of stage i) on the same
+// BF16x3 or BF16 tier, merged (no HPVM_LAUNCH_NO_FUSION) and not taken from
+// the plane cache. Stage i's epilogue then also writes the planes of C that
+// stage i+1 reads, and stage i+1 skips its conversion of B: the result makes
+// one trip through HBM instead of being written, read back and converted.
+bool forwards_b(const Plan& P, size_t i) {
+  if (i + 1 >= P.stages.size()) return false;
+  const Stage& a = P.stages[i];
+  const Stage& b = P.stages[i + 1];
+  const int tier = record_i32(P, a.rec, kTierOffset);
+  if (tier != record_i32(P, b.rec, kTierOffset) || (tier != HPVM_TIER_BF16X3 && tier != HPVM_TIER_BF16))
+    return false;
+  const int fa = record_i32(P, a.rec, kFlagsOffset), fb = record_i32(P, b.rec, kFlagsOffset);
+  if ((fa | fb) & HPVM_LAUNCH_NO_FUSION) return false;
+  if (fb & (HPVM_LAUNCH_CACHE_B | HPVM_LAUNCH_REUSE_B)) return false;
+  const hpvm::SgemmDesc& x = a.d;
+  const hpvm::SgemmDesc& y = b.d;
+  return x.M > 0 && x.N > 0 && y.M > 0 && y.K > 0 && y.B == x.C && !y.transB && y.ldb == x.ldc &&
+         y.K == x.M && y.N == x.N;
 }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Workspace of a plan: the planes of its largest stage, then (when stages
+// forward planes) two regions for forwarded planes, used alternately so a
+// stage reads its B from one while its epilogue writes the next stage's
+// into the other.
+struct WsPlan {
+  size_t stage = 0, fwd = 0;
+  size_t total() const { return fwd ? align256(stage) + 2 * align256(fwd) : stage; }
+  size_t region(size_t i) const { return align256(stage) + (i & 1) * align256(fwd); }
+};
+WsPlan plan_ws(const Plan& P) {
+  WsPlan W;
+  for (size_t i = 0; i < P.stages.size(); ++i) {
+    const Stage& S = P.stages[i];
+    const int tier = record_i32(P, S.rec, kTierOffset);
+    W.stage = std::max(W.stage, workspace_need(S, tier));
+    if (forwards_b(P, i)) W.fwd = std::max(W.fwd, hpvm::tc_operand_layout(tier, S.d.N, S.d.M).total);
+  }
+  return W;
+}
+
+size_t plan_workspace(const Plan& P) { return plan_ws(P).total(); }
 
 TrackEntry* find_tracked(hpvm_ctx* ctx, const void* p, int64_t* offset) {
   const char* c = static_cast<const char*>(p);
@@ -860,7 +900,11 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
   int64_t h2d = 0;
   int rc;
   bool first = true;
-  for (const Stage& S0 : P.stages) {
+  const WsPlan WP = plan_ws(P);
+  if (WP.fwd && (!ws || ws_bytes < WP.total()))
+    return fail(HPVM_ERR_SHAPE, "workspace of %zu bytes, the plan needs %zu", ws_bytes, WP.total());
+  for (size_t si = 0; si < P.stages.size(); ++si) {
+    const Stage& S0 = P.stages[si];
     const int tier = record_i32(P, S0.rec, kTierOffset);
     const int flags = record_i32(P, S0.rec, kFlagsOffset);
     if ((rc = check_stage_tier(S0, tier)) != HPVM_OK) return rc;
@@ -915,7 +959,14 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
           pb.converted = nullptr;
           eb = nullptr;
         }
+        if (si > 0 && forwards_b(P, si - 1)) {
+          // B's planes were written by the previous stage's epilogue
+          pb = hpvm::OperandPlanes();
+          pb.base = static_cast<uint8_t*>(ws) + WP.region(si - 1);
+          pb.ready = true;
+        }
       }
+      if (forwards_b(P, si)) S.epi.fwd = static_cast<uint8_t*>(ws) + WP.region(si);
       hpvm::Epilogue none;
       cudaError_t e;
       switch (tier) {

@@ -134,6 +134,11 @@ struct TcParams {
   int* status;
   const float* aux;     // EPI 2: H, column-major with leading dimension ldaux
   int64_t ldaux;
+  // Forwarded operand planes of C (or null): column n of C as K-major row n
+  // (fwd_kp elements a row) of a BF16 hi plane and, BF16x3, a lo plane.
+  __nv_bfloat16* fwd_hi;
+  __nv_bfloat16* fwd_lo;
+  int64_t fwd_kp;
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -1140,6 +1145,14 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (EPI == 1) x = tanhf(x);
               if (EPI == 2) x = x * (1.f - hx[u] * hx[u]);
               __stcs(cp + (int64_t)(u0 + u) * v.ldc, x);
+              if (!GROUPED && !C_::FP8 && p.fwd_hi) {
+                // the next stage's operand planes of this output (a warp
+                // writes 32 consecutive K elements of one plane row)
+                const int64_t o = (int64_t)(col0 + u0 + u) * p.fwd_kp + row;
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                p.fwd_hi[o] = h;
+                if (NPROD == 3) p.fwd_lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+              }
             }
           }
         }
@@ -1458,7 +1471,16 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
       maps[3] = maps[2];
     }
   }
-  TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, st.dev, epi.aux, epi.ldaux};
+  TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, st.dev, epi.aux, epi.ldaux,
+               nullptr, nullptr, 0};
+  if (epi.fwd && !C_::FP8) {
+    // the planes of C as op(B) of a leaf with K = M: rows = N, row length M
+    const OperandLayout F = operand_layout(N, M, MODE);
+    uint8_t* f = static_cast<uint8_t*>(epi.fwd);
+    prm.fwd_hi = reinterpret_cast<__nv_bfloat16*>(f + F.hi);
+    prm.fwd_lo = reinterpret_cast<__nv_bfloat16*>(f + F.lo);
+    prm.fwd_kp = (M + 7) / 8 * 8;
+  }
   const int tiles = ((M + TM - 1) / TM) * ((N + C_::TN - 1) / C_::TN);
   int grid_ctas = 0;
   hook_begin(hooks, s);

@@ -68,6 +68,36 @@ def test_merged_equals_unmerged(cuda_device, tier, kind):
 
 
 @pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
+@pytest.mark.parametrize("rows,w", [(300, 264), (77, 260)])
+def test_forwarded_planes_equal_converted(cuda_device, tier, rows, w):
+    # One launch of the chain graph: with the stages merged, each stage's
+    # epilogue writes the planes of its result that the next stage reads as
+    # B (the streaming edge lowered into the producer), so only X's planes
+    # and the weights' are converted. The unmerged launch converts every B
+    # from the FP32 result. Both round the same FP32 values: every stage's
+    # output must match bit for bit (w = 260: plane rows padded to 264).
+    layers = 4
+    X, Ws, _ = _inputs(1, rows, w, layers, seed=rows)
+    Xd = X[0].cuda()
+    Wd = [W.cuda() for W in Ws]
+    got, kernels = [], []
+    for fuse in (True, False):
+        eng = ChainEngine(layers, tier=tier, fuse=fuse)
+        try:
+            Y, Hs = eng.forward(Xd, Wd, keep=True)
+            kernels.append(H.hpvm_graph_info(eng._pending[-1]).kernels)
+            eng._drain()
+            got.append([t.cpu() for t in Hs + [Y]])
+        finally:
+            eng.close()
+    for a, b in zip(*got):
+        assert torch.equal(a, b)
+    # merged: 4 leaves + 4 weight conversions + X's; unmerged: 4 leaves,
+    # 3 tanh kernels, 4 + 4 conversions
+    assert kernels == [2 * layers + 1, 2 * layers + (layers - 1) + layers]
+
+
+@pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
 @pytest.mark.parametrize("items,rows,w,layers", [(3, 24, 16, 4), (2, 300, 256, 4), (1, 7, 5, 2)])
 def test_forward_and_streaming_match_oracle(cuda_device, tier, items, rows, w, layers):
     X, Ws, _ = _inputs(items, rows, w, layers, seed=rows + w)
