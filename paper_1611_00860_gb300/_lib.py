@@ -9,6 +9,7 @@ missing, importing this module raises ``ImportError`` (call
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 import re
 
@@ -303,7 +304,9 @@ def hpvm_drop_planes(ctx: int) -> None:
     _check(LIB.hpvm_drop_planes(ctx))
 
 
+@functools.lru_cache(maxsize=4096)
 def hpvm_plan_sgemm(tier: int, M: int, N: int, K: int) -> tuple[int, int, int, int]:
+    # a pure function of its arguments: memoised (records are packed per item)
     v = [ctypes.c_int32() for _ in range(4)]
     _check(LIB.hpvm_plan_sgemm(int(tier), int(M), int(N), int(K), *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)

@@ -254,12 +254,23 @@ class ChainEngine:
         streaming graph and pop the outputs in order (hpvm_push / hpvm_pop)."""
         outs_all = [[torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws] for X in items]
         rec0 = self.chain_records(items[0], Ws, outs_all[0])
+        # items of one shape differ only in X and the stage results: later
+        # items' records are the first's with those pointers replaced
+        reuse = self.chain_records(items[0], Ws, outs_all[0], H.HPVM_LAUNCH_REUSE_A)
         g = H.hpvm_launch(self.ctx, self.chain, rec0, True, self._stream())
         try:
             for i, (X, outs) in enumerate(zip(items, outs_all)):
                 # the weights are the same for every item: converted once
-                pf = H.HPVM_LAUNCH_CACHE_A if i == 0 else H.HPVM_LAUNCH_REUSE_A
-                H.hpvm_push(g, self.chain_records(X, Ws, outs, pf))
+                if i == 0:
+                    rec = self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_CACHE_A)
+                elif X.shape == items[0].shape:
+                    rec = type(reuse).from_buffer_copy(reuse)
+                    rec[0].B = X.data_ptr()
+                    for l, o in enumerate(outs):
+                        rec[l].C = o.data_ptr()
+                else:
+                    rec = self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_REUSE_A)
+                H.hpvm_push(g, rec)
             popped = []
             for _ in items:
                 rec = (H.RootArgs * self.layers)()

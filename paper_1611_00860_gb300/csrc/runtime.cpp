@@ -162,7 +162,9 @@ struct hpvm_graph {
   std::vector<void*> slot_ws;
   std::vector<size_t> slot_ws_bytes;
   std::deque<StreamItem> items;
+  std::vector<cudaEvent_t> spare_events;  // events of popped items, reused
   uint64_t pushed = 0;
+  uint64_t validated = ~uint64_t(0);  // the context's structure version validated at launch
 };
 
 struct hpvm_batch {
@@ -205,6 +207,10 @@ struct hpvm_ctx {
   std::vector<std::pair<uint64_t, int>> tuned;  // batch shape signature -> best policy
   std::vector<std::unique_ptr<PlaneEntry>> planes;  // the operand plane cache
   size_t plane_bytes = 0;
+  // bumped by every call that changes a graph (nodes, edges, bindings): a
+  // streaming graph validated at launch is not validated again per push
+  // unless this moved
+  uint64_t structure = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -612,14 +618,14 @@ struct Plan {
   Records R{nullptr, 0};
 };
 
-int lower_graph(hpvm_node* root, const void* args, size_t args_size, Plan* P) {
+int lower_graph(hpvm_node* root, const void* args, size_t args_size, Plan* P, bool validated = false) {
   if (!root || root->parent != nullptr)
     return fail(HPVM_ERR_INVALID_ARG, "launch needs the root node of a graph");
   if (root->kind != HPVM_NODE_INTERNAL || root->ndims != 0)
     return fail(HPVM_ERR_INVALID_GRAPH, "the root must be a single-instance internal node");
   if (!args || args_size < kRecBytes)
     return fail(HPVM_ERR_INVALID_ARG, "argument record too small (%zu < %zu bytes)", args_size, kRecBytes);
-  int rc = validate_node(root);
+  int rc = validated ? HPVM_OK : validate_node(root);
   if (rc != HPVM_OK) return rc;
   P->R = Records{static_cast<const uint8_t*>(args), (int)std::min<size_t>(args_size / kRecBytes, kMaxRecords)};
   std::vector<hpvm_node*> order;
@@ -1042,6 +1048,7 @@ void free_graph(hpvm_graph* g) {
   if (g->done) cudaEventDestroy(g->done);
   for (auto& it : g->items)
     if (it.done) cudaEventDestroy(it.done);
+  for (auto ev : g->spare_events) cudaEventDestroy(ev);
   for (size_t i = 0; i < g->slots.size(); ++i) {
     if (g->slots[i]) {
       cudaStreamSynchronize(g->slots[i]);
@@ -1150,6 +1157,7 @@ int hpvm_create_node(hpvm_ctx* ctx, hpvm_node* parent, int kind, int ndims, cons
   hpvm_node* raw = n.get();
   ctx->nodes.push_back(std::move(n));
   if (parent) parent->children.push_back(raw);
+  ctx->structure++;
   *out = raw;
   return ok();
 }
@@ -1175,6 +1183,7 @@ int hpvm_create_edge(hpvm_node* src, hpvm_node* dst, int repl, int sp, int dp, i
   hpvm_edge* raw = e.get();
   src->ctx->edges.push_back(std::move(e));
   src->parent->edges.push_back(raw);
+  src->ctx->structure++;
   if (out) *out = raw;
   return ok();
 }
@@ -1187,6 +1196,7 @@ int hpvm_bind_input(hpvm_node* child, int ip, int ic, int stream) {
   if (ic < 0 || ic >= in_arity(child))
     return fail(HPVM_ERR_INVALID_ARG, "input %d of %s is out of range", ic, node_label(child).c_str());
   child->parent->in_binds.push_back(Bind{child, ip, ic, stream != 0});
+  child->ctx->structure++;
   return ok();
 }
 
@@ -1200,6 +1210,7 @@ int hpvm_bind_output(hpvm_node* child, int oc, int op, int stream) {
   for (auto& b : child->parent->out_binds)
     if (b.outer == op) return fail(HPVM_ERR_INVALID_GRAPH, "parent output %d is already bound", op);
   child->parent->out_binds.push_back(Bind{child, op, oc, stream != 0});
+  child->ctx->structure++;
   return ok();
 }
 
@@ -1310,6 +1321,7 @@ int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args, size_t args_si
   g->stream = s;
   g->root = root;
   if (stream_graph) {
+    g->validated = ctx->structure;  // lower_graph above validated the structure
     // A streaming graph stays alive: nothing runs now; every hpvm_push runs
     // one item on the next stream of the ring, after the work enqueued on
     // the caller's stream before this launch.
@@ -1360,7 +1372,7 @@ int hpvm_push(hpvm_graph* g, const void* args, size_t args_size) {
   if (!ctx->graphs.count(g)) return fail(HPVM_ERR_INVALID_ARG, "unknown or finished graph handle");
   if (!g->streaming) return fail(HPVM_ERR_INVALID_ARG, "push needs a graph launched as a streaming graph");
   Plan P;
-  int rc = lower_graph(g->root, args, args_size, &P);
+  int rc = lower_graph(g->root, args, args_size, &P, g->validated == ctx->structure);
   if (rc != HPVM_OK) return rc;
   cudaSetDevice(ctx->device);
   const int slot = (int)(g->pushed % g->slots.size());
@@ -1370,8 +1382,13 @@ int hpvm_push(hpvm_graph* g, const void* args, size_t args_size) {
   if ((rc = execute_plan(ctx, P, s, g->slot_ws[slot], g->slot_ws_bytes[slot], &inf)) != HPVM_OK) return rc;
   StreamItem it;
   it.record.assign(static_cast<const uint8_t*>(args), static_cast<const uint8_t*>(args) + args_size);
-  cudaError_t e = cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  if (!g->spare_events.empty()) {
+    it.done = g->spare_events.back();
+    g->spare_events.pop_back();
+  } else {
+    cudaError_t e = cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  }
   cudaEventRecord(it.done, s);
   g->items.push_back(std::move(it));
   g->info = inf;
@@ -1391,7 +1408,8 @@ int hpvm_pop(hpvm_graph* g, void* out, size_t out_size, int64_t timeout_ms) {
   if (rc == HPVM_ERR_TIMEOUT) return rc;  // the item stays queued
   if (rc == HPVM_OK) rc = check_status(ctx);
   if (out && out_size) memcpy(out, it.record.data(), std::min(out_size, it.record.size()));
-  cudaEventDestroy(it.done);
+  if (rc == HPVM_OK) g->spare_events.push_back(it.done);  // completed: reusable
+  else cudaEventDestroy(it.done);
   g->items.pop_front();
   return rc == HPVM_OK ? ok() : rc;
 }
