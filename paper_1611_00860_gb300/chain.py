@@ -75,17 +75,17 @@ def _add_stage(ctx: int, root: int, base: int, ew_kind: int | None, b_from_edge:
     return st
 
 
-def build_chain_graph(ctx: int, layers: int, tanh_last: bool = False) -> int:
-    """Root -> ``layers`` stages, tanh merged into every stage but the last
-    (into the last too with ``tanh_last``: the recomputation of the
-    activations), stage l's result streamed into stage l+1's B. Returns the
-    root."""
+def build_chain_graph(ctx: int, layers: int, tanh_last: bool = False,
+                      ew_kind: int = H.HPVM_NODE_TANH_LEAF) -> int:
+    """Root -> ``layers`` stages, an elementwise leaf (tanh, or with
+    ``ew_kind`` the tanh adjoint) merged into every stage but the last (into
+    the last too with ``tanh_last``: the recomputation of the activations),
+    stage l's result streamed into stage l+1's B. Returns the root."""
     root = H.hpvm_create_node(ctx, None, H.HPVM_NODE_INTERNAL)
     prev = None
     for l in range(layers):
-        tanh = l + 1 < layers or tanh_last
-        st = _add_stage(ctx, root, REC * l, H.HPVM_NODE_TANH_LEAF if tanh else None,
-                        b_from_edge=prev is not None)
+        ew = l + 1 < layers or tanh_last
+        st = _add_stage(ctx, root, REC * l, ew_kind if ew else None, b_from_edge=prev is not None)
         if prev is not None:
             H.hpvm_create_edge(prev, st, H.HPVM_ALL_TO_ALL, 0, 3, stream=True)
             H.hpvm_create_edge(prev, st, H.HPVM_ALL_TO_ALL, 1, 4, stream=True)
@@ -127,6 +127,9 @@ class ChainEngine:
         self.chain = build_chain_graph(self.ctx, layers)
         # H_1 .. H_{L-1} again in backward: the first L - 1 stages, all with tanh
         self.rechain = build_chain_graph(self.ctx, layers - 1, tanh_last=True) if layers > 1 else None
+        # the adjoint chain dH_l^T = W_l dZ_l^T, l = L-1 .. 0, the tanh adjoint
+        # merged into every stage but the last (whose result is dX)
+        self.adjchain = build_chain_graph(self.ctx, layers, ew_kind=H.HPVM_NODE_TANH_GRAD_LEAF)
         self.stage_tanh = build_single_stage_graph(self.ctx, H.HPVM_NODE_TANH_LEAF)
         self.stage_dtanh = build_single_stage_graph(self.ctx, H.HPVM_NODE_TANH_GRAD_LEAF)
         self.stage_plain = build_single_stage_graph(self.ctx, None)
@@ -216,16 +219,36 @@ class ChainEngine:
 
     # -- backward -----------------------------------------------------------------
     def backward(self, X: torch.Tensor, Ws, G: torch.Tensor):
-        """dX and dW_l of sum(Y * G), recomputing the activations."""
+        """dX and dW_l of sum(Y * G), recomputing the activations.
+
+        The input adjoints run as one launch of the adjoint chain: stage j
+        (layer l = L-1-j) computes dH_l^T = W_l dZ_l^T with op(A) = A^T, and
+        for l > 0 its merged tanh adjoint gives dZ_{l-1} = dH_l * (1 - H_l^2),
+        streamed into stage j+1's B (so its planes come from stage j's
+        epilogue). The weight adjoints dW_l^T = dZ_l^T H_l follow, one launch
+        each (op(B) = B^T)."""
         Hs = self.recompute(X, Ws)
         L = self.layers
-        dWs = [None] * L
-        dZ = G.contiguous()
-        dX = None
         rows = X.shape[0]
+        G = G.contiguous()
+        dHs = [torch.empty(rows, W.shape[0], device=X.device) for W in Ws]  # dH_l: rows x w_in
+        recs = (H.RootArgs * L)()
+        for j, l in enumerate(range(L - 1, -1, -1)):
+            W = Ws[l]
+            w_in, w_out = W.shape
+            a = make_args(w_in, rows, w_out, W.data_ptr(), W.numel() * 4, w_out,
+                          G.data_ptr() if j == 0 else None, G.numel() * 4 if j == 0 else 0, w_out,
+                          dHs[l].data_ptr(), dHs[l].numel() * 4, w_in, 1.0, 0.0, True, False, self.tier,
+                          flags=self.flags)
+            if l > 0:
+                a.aux, a.bytesAux, a.ldaux = Hs[l].data_ptr(), Hs[l].numel() * 4, w_in
+            recs[j] = a
+        self._run(self.adjchain, recs)
+        dWs = [None] * L
         for l in range(L - 1, -1, -1):
             W = Ws[l]
             w_in, w_out = W.shape
+            dZ = G if l == L - 1 else dHs[l + 1]
             # dW^T = dZ^T H_l: M = w_out, N = w_in, K = rows; A = dZ buffer, B = H_l buffer (B^T)
             dW = torch.empty_like(W)
             a = make_args(w_out, w_in, rows, dZ.data_ptr(), dZ.numel() * 4, w_out, Hs[l].data_ptr(),
@@ -233,20 +256,7 @@ class ChainEngine:
                           False, True, self.tier, flags=self.flags)
             self._run(self.stage_plain, a)
             dWs[l] = dW
-            # dH^T = W dZ^T: M = w_in, N = rows, K = w_out; A = W buffer (A^T), B = dZ buffer
-            dH = torch.empty(rows, w_in, device=X.device)
-            a = make_args(w_in, rows, w_out, W.data_ptr(), W.numel() * 4, w_out, dZ.data_ptr(),
-                          dZ.numel() * 4, w_out, dH.data_ptr(), dH.numel() * 4, w_in, 1.0, 0.0,
-                          True, False, self.tier, flags=self.flags)
-            if l > 0:
-                # merged tanh adjoint: dZ_{l-1} = dH * (1 - H_l^2)
-                a.aux, a.bytesAux, a.ldaux = Hs[l].data_ptr(), Hs[l].numel() * 4, w_in
-                self._run(self.stage_dtanh, a)
-                dZ = dH
-            else:
-                self._run(self.stage_plain, a)
-                dX = dH
-        return dX, dWs
+        return dHs[0], dWs
 
     # -- streaming -----------------------------------------------------------------
     def stream_forward(self, items, Ws, timeout_ms: int = 600000):

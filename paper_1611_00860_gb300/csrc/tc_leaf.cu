@@ -1,27 +1,34 @@
 // Tensor-core (tcgen05) lowerings of the SgemmLeaf node (Section 5.1) for
-// sm_103a: the BF16x3 split tier and the plain BF16 tier.
+// sm_103a: the BF16x3 split tier, the plain BF16 tier and the block-scaled
+// FP8 (E4M3) tier.
 //
 // The leaf computes C <- alpha*op(A)*op(B) + beta*C (column-major FP32, C
 // not read when beta == 0). The paper computes in FP32 on CUDA cores; here
 // each FP32 operand x is split into BF16 parts hi = bf16_rn(x) and
 // lo = bf16_rn(x - hi) and the leaf sums the three products
 // hi*hi + hi*lo + lo*hi on the tensor cores into one FP32 accumulator in
-// tensor memory (the BF16 tier keeps hi*hi only).
+// tensor memory (the BF16 tier keeps hi*hi only; the FP8 tier multiplies
+// E4M3 codes and scales each 128-wide K block by its two block scales).
 //
 // Mapping of the dataflow graph (Section 4.4): one internal-node instance
-// (an output tile of BM x BN) is one CTA; the Allocation node's tile memory
-// is a ring of STAGES shared-memory slabs filled by TMA (the paper's scratch-
-// pad tiles), plus the accumulator tile in tensor memory; the replicated
-// leaf's multiply-accumulate is a sequence of tcgen05.mma instructions.
+// (an output tile) is one CTA (128 x 256) or a pair of CTAs in a cluster
+// (256 x 256, cta_group::2); the Allocation node's tile memory is a ring of
+// STAGES shared-memory slabs filled by TMA (the paper's scratchpad tiles),
+// plus the accumulator tiles in tensor memory; the replicated leaf's
+// multiply-accumulate is a sequence of tcgen05.mma instructions.
 //
 // Kernels
-//   split_mmajor / split_kmajor: FP32 op(X) -> K-major BF16 hi (and lo)
-//       planes in the workspace, rows of Kp = roundup(K, 8) elements.
-//   sgemm_tc<NPROD>: warp 0 issues TMA loads, warp 1 allocates tensor
-//       memory and issues the MMAs, warps 2..5 read the accumulator
-//       (tcgen05.ld) and write C. Every mbarrier wait is bounded; on
-//       expiry the kernel sets a bit in the status word, drains its own
-//       copies and MMAs (bounded again), frees tensor memory and returns.
+//   split_mmajor / split_kmajor / split_batch: FP32 op(X) -> K-major BF16
+//       hi (and lo) planes, rows of Kp = roundup(K, 8) elements.
+//   quant_fp8: FP32 op(X) -> E4M3 codes and one FP32 scale per 128 x 128
+//       block.
+//   sgemm_tc<MODE, EPI, GROUPED, PAIR>: persistent; warp 0 issues TMA loads,
+//       warp 1 allocates tensor memory and issues the MMAs, warps 4..11
+//       read the accumulator (tcgen05.ld) into FP32 registers and write C
+//       (with a merged elementwise leaf, EPI). Every mbarrier wait is
+//       bounded; on expiry the kernel sets a bit in the status word, drains
+//       its own copies and MMAs (bounded again), frees tensor memory and
+//       returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>

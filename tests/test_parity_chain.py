@@ -162,6 +162,37 @@ def test_pop_without_push_and_push_without_stream(cuda_device):
         eng.close()
 
 
+def test_push_revalidates_a_graph_changed_after_launch(cuda_device):
+    # A streaming graph is validated at launch; pushes skip the validation
+    # while no node, edge or binding has been added since. A binding added
+    # after the launch that feeds a stage input twice makes the graph
+    # invalid, and the next push must refuse it.
+    from paper_1611_00860_gb300.chain import _add_stage
+    eng = ChainEngine(1)
+    try:
+        root = H.hpvm_create_node(eng.ctx, None, H.HPVM_NODE_INTERNAL)
+        st = _add_stage(eng.ctx, root, 0, H.HPVM_NODE_TANH_LEAF, b_from_edge=False)
+        H.hpvm_bind_output(st, 0, 0, stream=True)
+        X = torch.randn(8, 16, device="cuda")
+        W = torch.randn(16, 16, device="cuda") / 4
+        out = torch.empty(8, 16, device="cuda")
+        rec = eng.chain_records(X, [W], [out])
+        g = H.hpvm_launch(eng.ctx, root, rec, True, 0)
+        for _ in range(2):
+            H.hpvm_push(g, rec)
+            H.hpvm_pop(g, None, 60000)
+        torch.cuda.synchronize()
+        assert O.normwise_rel_err(out.double().cpu().numpy(),
+                                  np.tanh(X.double().cpu().numpy() @ W.double().cpu().numpy())) <= 1e-2
+        H.hpvm_bind_input(st, 0, 0)  # input 0 of the stage is now fed twice
+        with pytest.raises(H.HpvmError) as e:
+            H.hpvm_push(g, rec)
+        assert e.value.code == H.HPVM_ERR_INVALID_GRAPH
+        H.hpvm_wait(g, 60000)
+    finally:
+        eng.close()
+
+
 @pytest.mark.slow
 def test_chain_workload_sampled_rows(cuda_device):
     # the chain workload: 64 items of 256 x 4096, four 4096 x 4096 weights,
