@@ -565,55 +565,48 @@ __global__ void __launch_bounds__(256) split_kmajor(const float* __restrict__ X,
 // Y (rows x K; element (r, k) at X[k + r*ld] when KCONTIG, else X[r + k*ld])
 // -> E4M3 codes q[r*Kp + k] and one FP32 scale per 128 x 128 block,
 // scales[rb*nkb + kb] = amax / 448 (1 when the block is all zero), codes
-// e4m3_rn_satfinite(x / scale). One CTA of 512 threads per block: every
-// thread first issues all eight of its (float4 when VEC) loads, then the
-// block is staged in shared memory, reduced to its amax, and quantised.
+// e4m3_rn_satfinite(x / scale). One CTA of 512 threads per block: thread t
+// holds row t % 128, K elements 32 * (t / 128) .. + 31 of the block in
+// registers (m-major source: each of its 32 loads reads 32 consecutive rows
+// of one K column across the warp; K-contiguous: 8 float4 of its row). The
+// block's amax comes from a warp shuffle and 16 partials in shared memory;
+// each thread then quantises its 32 values (x / scale rounded as IEEE
+// division rounds it) into a 128 x 128 byte tile, which the CTA writes out
+// as 128-byte row segments.
 constexpr int QTHREADS = 512;
+constexpr int QROW = FP8_BLOCK + 16;  // byte tile row: 16-byte aligned, 144 B apart
 template <bool KCONTIG, bool VEC>
-__global__ void __launch_bounds__(QTHREADS) quant_fp8(const float* __restrict__ X, int64_t ld, int rows, int K,
-                                                      int Kp, uint8_t* __restrict__ q, float* __restrict__ scales,
-                                                      int nkb) {
-  extern __shared__ float tile[];  // [128][129]
+__global__ void __launch_bounds__(QTHREADS, 2) quant_fp8(const float* __restrict__ X, int64_t ld, int rows, int K,
+                                                         int Kp, uint8_t* __restrict__ q,
+                                                         float* __restrict__ scales, int nkb) {
+  __shared__ __align__(16) uint8_t codes[FP8_BLOCK * QROW];
   __shared__ float red[QTHREADS / 32];
   __shared__ float s_sh;
-  constexpr int T = FP8_BLOCK + 1;
   const int tid = threadIdx.x;
+  const int r = tid % FP8_BLOCK, kq = (tid / FP8_BLOCK) * 32;
   const int64_t r0 = (int64_t)blockIdx.x * FP8_BLOCK, k0 = (int64_t)blockIdx.y * FP8_BLOCK;
-  // 4096 groups of 4 elements consecutive in memory: g % 32 runs along the
-  // contiguous dimension, g / 32 along the other one
-  float4 v[8];
+  const int64_t gr = r0 + r, gk = k0 + kq;
+  const bool row_in = gr < rows;
+  float v[32];
+  if (KCONTIG) {
+    const float* src = X + gk + gr * ld;
 #pragma unroll
-  for (int it = 0; it < 8; ++it) {
-    const int g = tid + it * QTHREADS;
-    const int c = (g % 32) * 4, o = g / 32;
-    const int64_t gr = r0 + (KCONTIG ? o : c), gk = k0 + (KCONTIG ? c : o);
-    const float* src = KCONTIG ? X + gk + gr * ld : X + gr + gk * ld;
-    const bool full4 = KCONTIG ? (gr < rows && gk + 3 < K) : (gk < K && gr + 3 < rows);
-    if (VEC && full4) {
-      v[it] = *reinterpret_cast<const float4*>(src);
-    } else {
-      float t[4];
+    for (int u = 0; u < 32; u += 4) {
+      if (VEC && row_in && gk + u + 3 < K) {
+        const float4 t = __ldcs(reinterpret_cast<const float4*>(src + u));
+        v[u] = t.x, v[u + 1] = t.y, v[u + 2] = t.z, v[u + 3] = t.w;
+      } else {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool ok = KCONTIG ? (gr < rows && gk + u < K) : (gk < K && gr + u < rows);
-        t[u] = ok ? src[u] : 0.f;
+        for (int w = 0; w < 4; ++w) v[u + w] = (row_in && gk + u + w < K) ? __ldcs(src + u + w) : 0.f;
       }
-      v[it] = make_float4(t[0], t[1], t[2], t[3]);
     }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 32; ++u) v[u] = (row_in && gk + u < K) ? __ldcs(X + gr + (gk + u) * ld) : 0.f;
   }
   float amax = 0.f;
 #pragma unroll
-  for (int it = 0; it < 8; ++it) {
-    const int g = tid + it * QTHREADS;
-    const int c = (g % 32) * 4, o = g / 32;
-    const float t[4] = {v[it].x, v[it].y, v[it].z, v[it].w};
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      amax = fmaxf(amax, fabsf(t[u]));
-      if (KCONTIG) tile[o * T + c + u] = t[u];
-      else tile[(c + u) * T + o] = t[u];
-    }
-  }
+  for (int u = 0; u < 32; ++u) amax = fmaxf(amax, fabsf(v[u]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if ((tid & 31) == 0) red[tid >> 5] = amax;
@@ -627,15 +620,40 @@ __global__ void __launch_bounds__(QTHREADS) quant_fp8(const float* __restrict__ 
   }
   __syncthreads();
   const float s = s_sh;
-  for (int task = tid; task < FP8_BLOCK * (FP8_BLOCK / 16); task += QTHREADS) {
-    const int r = task / (FP8_BLOCK / 16), kc = (task % (FP8_BLOCK / 16)) * 16;
-    const int64_t gr = r0 + r, gk = k0 + kc;
-    if (gr >= rows || gk >= Kp) continue;
-    __align__(16) uint8_t c[16];
+  // x / s rounded to nearest, as IEEE division gives it. For s in
+  // [2^-80, 2^80] (every block of real data) one correction step suffices
+  // (Markstein's theorem: with rs = RN(1/s) and q0 = RN(x * rs) within an
+  // ulp of x / s, the remainder e = x - q0 * s is exact in an FMA and
+  // RN(q0 + e * rs) is the correctly rounded quotient; quotients that a
+  // subnormal remainder could disturb are below 2^-10, which E4M3 rounds
+  // to zero either way). Other scales take the IEEE division itself.
+  const bool fast = s >= 0x1p-80f && s <= 0x1p80f;
+  const float rs = __frcp_rn(s);
+  auto quotient = [&](float x) {
+    if (!fast) return __fdiv_rn(x, s);
+    const float q0 = x * rs;
+    return fmaf(fmaf(-q0, s, x), rs, q0);
+  };
+  // this thread's 32 codes, 4 to a word, into its row of the byte tile
+  uint32_t w[8];
 #pragma unroll
-    for (int u = 0; u < 16; ++u)
-      c[u] = __nv_cvt_float_to_fp8(__fdiv_rn(tile[r * T + kc + u], s), __NV_SATFINITE, __NV_E4M3);
-    *reinterpret_cast<uint4*>(q + gr * Kp + gk) = *reinterpret_cast<const uint4*>(c);
+  for (int u = 0; u < 32; u += 4) {
+    uint32_t b = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      b |= (uint32_t)__nv_cvt_float_to_fp8(quotient(v[u + e]), __NV_SATFINITE, __NV_E4M3) << (8 * e);
+    w[u / 4] = b;
+  }
+  uint4* dst = reinterpret_cast<uint4*>(codes + r * QROW + kq);
+  dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  __syncthreads();
+  // 128 rows x 8 segments of 16 bytes: a warp writes 4 rows of 128 bytes
+  for (int i = tid; i < FP8_BLOCK * (FP8_BLOCK / 16); i += QTHREADS) {
+    const int row = i / (FP8_BLOCK / 16), seg = (i % (FP8_BLOCK / 16)) * 16;
+    const int64_t orow = r0 + row, ok = k0 + seg;
+    if (orow >= rows || ok >= Kp) continue;
+    *reinterpret_cast<uint4*>(q + orow * Kp + ok) = *reinterpret_cast<const uint4*>(codes + row * QROW + seg);
   }
 }
 
@@ -1304,28 +1322,14 @@ cudaError_t launch_split(const float* X, int64_t ld, bool mmajor, int rows, int 
 cudaError_t launch_quant(const float* X, int64_t ld, bool mmajor, int rows, int K, int Kp, uint8_t* q,
                          float* scales, int nkb, cudaStream_t s) {
   if (rows == 0 || K == 0) return cudaSuccess;
-  constexpr int smem = FP8_BLOCK * (FP8_BLOCK + 1) * 4;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(quant_fp8<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(quant_fp8<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(quant_fp8<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(quant_fp8<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   // float4 loads need 16-byte aligned groups: base aligned and ld % 4 == 0
   const bool vec = (reinterpret_cast<uintptr_t>(X) & 15u) == 0 && ld % 4 == 0;
   dim3 grid((rows + FP8_BLOCK - 1) / FP8_BLOCK, nkb);
   if (mmajor) {
-    if (vec) quant_fp8<false, true><<<grid, QTHREADS, smem, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
-    else quant_fp8<false, false><<<grid, QTHREADS, smem, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
+    quant_fp8<false, false><<<grid, QTHREADS, 0, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
   } else {
-    if (vec) quant_fp8<true, true><<<grid, QTHREADS, smem, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
-    else quant_fp8<true, false><<<grid, QTHREADS, smem, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
+    if (vec) quant_fp8<true, true><<<grid, QTHREADS, 0, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
+    else quant_fp8<true, false><<<grid, QTHREADS, 0, s>>>(X, ld, rows, K, Kp, q, scales, nkb);
   }
   return cudaGetLastError();
 }

@@ -80,6 +80,60 @@ def test_quant_fp8_bit_exact(kcontig, rows, K):
     assert np.array_equal(got_codes[:, :K], codes) and not got_codes[:, K:].any()
 
 
+def _e4m3_midpoints():
+    """Every point halfway between two consecutive non-negative E4M3 values
+    (where rounding x / s to E4M3 depends on the last bit of the FP32
+    quotient), as float64."""
+    vals = torch.arange(256, dtype=torch.uint8).view(torch.float8_e4m3fn).double()
+    v = np.unique(vals[torch.isfinite(vals) & (vals >= 0)].numpy())
+    return (v[:-1] + v[1:]) / 2
+
+
+@pytest.mark.parametrize("kcontig", [False, True])
+def test_quant_fp8_rounding_midpoints_bit_exact(kcontig):
+    # Each 128 x 128 block gets its own scale s (one element 448 t sets
+    # amax), and values x = RN(m s) and their FP32 neighbours for every E4M3
+    # midpoint m (both signs): x / s lies within an ulp of m, so the E4M3
+    # code depends on the quotient being rounded exactly as IEEE division
+    # rounds it. Scales span 2^-60 .. 2^60, and two blocks take scales
+    # near 2^-100 and 2^90 (outside the quantiser's reciprocal path, where
+    # it divides). The codes must equal the oracle's (numpy FP32 division).
+    rows, K = 256, 384
+    g = np.random.default_rng(11)
+    Y = (g.standard_normal((rows, K)) * 0.01).astype(np.float32)
+    mids = _e4m3_midpoints()
+    mids = mids[mids < 416]
+    for bi in range(rows // 128):
+        for bj in range(K // 128):
+            t = np.float32(2.0 ** g.uniform(-60, 60) * g.uniform(1, 2))
+            if (bi, bj) == (0, 0):
+                t = np.float32(2.0 ** -100 * 1.37)
+            if (bi, bj) == (1, 2):
+                t = np.float32(2.0 ** 90 * 1.11)
+            amax = np.float32(np.float32(448) * t)
+            s = np.float32(amax / np.float32(448))
+            x = (mids * np.float64(s)).astype(np.float32)
+            xs = np.concatenate([x, np.nextafter(x, np.float32(np.inf)), np.nextafter(x, np.float32(0))])
+            xs = np.concatenate([xs, -xs])
+            blk = Y[bi * 128:(bi + 1) * 128, bj * 128:(bj + 1) * 128]
+            blk *= np.float32(t)  # the random fill scaled with the block (below amax)
+            flat = blk.reshape(-1)
+            flat[1:1 + xs.size] = xs
+            flat[0] = amax
+            Y[bi * 128:(bi + 1) * 128, bj * 128:(bj + 1) * 128] = flat.reshape(128, 128)
+    X = torch.from_numpy(np.ascontiguousarray(Y.T if not kcontig else Y)).reshape(-1)
+    ld = rows if not kcontig else K
+    q = torch.zeros(rows * K, dtype=torch.uint8, device="cuda")
+    sc = torch.zeros((rows // 128) * (K // 128), dtype=torch.float32, device="cuda")
+    H.hpvm_quant_fp8(X.cuda().data_ptr(), ld, kcontig, rows, K, q.data_ptr(), sc.data_ptr(),
+                     torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    codes, scales = Q.fp8_block_quant(Y)
+    assert np.array_equal(sc.cpu().numpy().reshape(rows // 128, K // 128), scales)
+    got = q.view(torch.float8_e4m3fn).float().cpu().numpy().reshape(rows, K)
+    assert np.array_equal(got, codes), np.argwhere(got != codes)[:5]
+
+
 SHAPES = [(128, 256, 128), (300, 200, 260), (129, 257, 33), (1, 1, 1), (500, 130, 1024), (64, 40, 0)]
 
 
