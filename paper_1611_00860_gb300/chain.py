@@ -184,14 +184,17 @@ class ChainEngine:
         for g in pending:
             H.hpvm_wait(g, timeout_ms)
 
-    def chain_records(self, X: torch.Tensor, Ws, outs, plane_flags: int = 0):
+    def chain_records(self, X: torch.Tensor, Ws, outs, plane_flags: int = 0, x_flags: int = 0):
         """Records of a chain graph of len(Ws) stages: stage l computes
         outs[l] = act(in_l) W_l. plane_flags (HPVM_LAUNCH_CACHE_A / REUSE_A)
-        applies to the weights, the stages' A operands."""
+        applies to the weights, the stages' A operands; x_flags
+        (HPVM_LAUNCH_CACHE_B / REUSE_B) to X, the first stage's B (later
+        stages take their B planes from the previous stage's epilogue)."""
         arr = (H.RootArgs * len(Ws))()
         for l in range(len(Ws)):
             src = X if l == 0 else outs[l - 1]
-            arr[l] = _rm_product_args(outs[l], src, Ws[l], self.tier, self.flags | plane_flags)
+            arr[l] = _rm_product_args(outs[l], src, Ws[l], self.tier,
+                                      self.flags | plane_flags | (x_flags if l == 0 else 0))
             if l > 0:  # B arrives over the streaming edge
                 arr[l].B = None
                 arr[l].bytesB = 0
@@ -202,9 +205,9 @@ class ChainEngine:
         """Y for row-major X (rows x w). With keep, also the activations
         H_1..H_{L-1} (the tanh outputs, the chain's intermediate buffers)."""
         outs = [torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws]
-        # the weights' planes are made afresh (the weights may have changed
+        # the weights' and X's planes are made afresh (they may have changed
         # since the last call) and kept for the recomputation in backward
-        self._run(self.chain, self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_CACHE_A))
+        self._run(self.chain, self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_CACHE_A, H.HPVM_LAUNCH_CACHE_B))
         return (outs[-1], outs[:-1]) if keep else outs[-1]
 
     def recompute(self, X: torch.Tensor, Ws):
@@ -213,8 +216,8 @@ class ChainEngine:
         if self.rechain is None:
             return [X]
         outs = [torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws[:-1]]
-        # autograd guarantees the saved weights are unchanged since forward
-        self._run(self.rechain, self.chain_records(X, Ws[:-1], outs, H.HPVM_LAUNCH_REUSE_A))
+        # autograd guarantees the saved X and weights are unchanged since forward
+        self._run(self.rechain, self.chain_records(X, Ws[:-1], outs, H.HPVM_LAUNCH_REUSE_A, H.HPVM_LAUNCH_REUSE_B))
         return [X] + outs
 
     # -- backward -----------------------------------------------------------------
