@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--fp8-n", type=int, default=16384)
     ap.add_argument("--no-chain", action="store_true", help="skip the streamed chain section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances section")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="instances of the batched workload (a smaller batch for profiling)")
     ap.add_argument("--only", choices=["chain", "batch", "fp8"], default=None,
                     help="run one workload section alone and print its JSON (for profiling); "
                          "no headline line")
@@ -111,15 +113,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(src_hash: str):
-    """DRAM bytes per launch of the leaf kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "sgemm_tc_bf16x3_8192.md")
+def traffic_from_profiles(src_hash: str, name: str = "sgemm_tc_bf16x3_8192.md",
+                          what: str = "per launch"):
+    """DRAM bytes (read + write) from a committed ncu summary, if it was
+    taken on the current kernel source: per launch of the headline leaf, or
+    per run of the batch (split pre-pass and grouped leaf)."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_hash = re.search(r"kernel source sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
-    m_bytes = re.search(r"dram bytes per launch \(read \+ write\)\W*([0-9.eE+]+)", text)
+    m_bytes = re.search(r"dram bytes " + re.escape(what) + r" \(read \+ write\)\W*([0-9.eE+]+)", text)
     if not m_hash or not m_bytes or m_hash.group(1) != src_hash:
         return None
     return float(m_bytes.group(1))
@@ -360,7 +364,7 @@ def batch_section(args, H, W, torch, local, world, rank, barrier):
     instance on the same inputs."""
     from paper_1611_00860_gb300.batch import BatchDFG
     from paper_1611_00860_gb300.sgemm import SgemmDFG
-    shapes = W.batched_shapes()
+    shapes = W.batched_shapes(args.batch_count)
     probs = [W.sgemm_problem(m, n, k, seed=20000 + i, alpha=1.0, beta=0.0) for i, (m, n, k) in enumerate(shapes)]
     flop = sum(2.0 * m * n * k for m, n, k in shapes)
     dev = [tuple(t.to(f"cuda:{local}") for t in (p.A, p.B, p.C)) for p in probs]
@@ -391,7 +395,7 @@ def batch_section(args, H, W, torch, local, world, rank, barrier):
     peaks = load_peaks()
     algo_bytes = sum(4.0 * (m * k + n * k + m * n) for m, n, k in shapes)
     achieved = algo_bytes / (ms * 1e-3) / 1e9
-    out = {"workload": "512 sgemm DFG instances, M,N,K log-uniform in [32,2048] (seed 2), N(0,1), "
+    out = {"workload": f"{args.batch_count} sgemm DFG instances, M,N,K log-uniform in [32,2048] (seed 2), N(0,1), "
                        "alpha=1, beta=0, BF16x3 leaves", "unit": "TFLOP/s",
            "useful_tflop": flop / 1e12, "batch": {
                "value": flop * world / (ms * 1e-3) / 1e12, "ms_per_batch": ms,
@@ -400,7 +404,9 @@ def batch_section(args, H, W, torch, local, world, rank, barrier):
                "autotuned_policy": best, "info": b.info(),
                "leaf_ms": leaf_ms, "split_ms": ms - leaf_ms,
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                            "frac": achieved / peaks["hbm_gbs"],
+                            "traffic": traffic_from_profiles(kernel_source_hash(), "launches_batch_512.md",
+                                                             "per batch") if args.batch_count == 512 else None,
                             "algorithmic": "4*(M*K + N*K + M*N) bytes per instance: FP32 A and B read once, "
                                            "C written once (beta = 0); the split planes are extra traffic",
                             "peak_source": f"{peaks['_source']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}}}
