@@ -246,7 +246,11 @@ HPVM_API int hpvm_validate(hpvm_node* root);
  * (tile grids, one per stage, ordered by their edges: an all-to-all edge
  * from a stage's output 0 to the next stage's input carries the result
  * matrix); each holds one Allocation, one SgemmLeaf and at most one
- * elementwise leaf.
+ * elementwise leaf. When stage i + 1 reads stage i's result as its B
+ * (op(B) = B, its K = stage i's M, the same BF16X3 or BF16 tier, merged,
+ * no plane-cache flag on that B), stage i's epilogue also writes the BF16
+ * planes stage i + 1 reads, and stage i + 1 converts no B (the planes equal
+ * the converted ones bit for bit; HPVM_LAUNCH_NO_FUSION turns this off).
  * Launch the graph under `root` asynchronously on `cuda_stream` (a
  * cudaStream_t; NULL = the legacy default stream) with the argument records
  * `args` (hpvm_sgemm_root_args[], args_size >= 136). Errors found before any
@@ -266,7 +270,10 @@ HPVM_API int hpvm_wait(hpvm_graph* graph, int64_t timeout_ms);
  * (as for hpvm_launch). The item runs asynchronously on the next of the
  * graph's CUDA streams (4, round robin), so successive items overlap on
  * the GPU; every stream first waits for the work the caller's stream had
- * when the graph was launched. Items must not write the same buffers. */
+ * when the graph was launched. Items must not write the same buffers. The
+ * graph's structure is validated at launch and again at a push only if a
+ * node, edge or binding was added in the context since (an invalid graph
+ * then gives HPVM_ERR_INVALID_GRAPH and nothing is enqueued). */
 HPVM_API int hpvm_push(hpvm_graph* graph, const void* args, size_t args_size);
 /* Pop the oldest pushed item: wait for it (at most timeout_ms, < 0: no
  * limit; HPVM_ERR_TIMEOUT leaves it queued), then copy its records into
@@ -291,8 +298,9 @@ HPVM_API int hpvm_request_mem(hpvm_ctx* ctx, void* p, int64_t bytes);
 HPVM_API int hpvm_untrack_mem(hpvm_ctx* ctx, void* p);
 
 /* ---- workspace ----------------------------------------------------------
- * Device scratch the tensor-core tiers use (split operands). Bytes a launch
- * of `root` with `args` needs: */
+ * Device scratch the tensor-core tiers use: the operand planes of the
+ * largest stage and, when stages forward planes to the next stage's B, two
+ * regions for those. Bytes a launch of `root` with `args` needs: */
 HPVM_API int hpvm_workspace_size(hpvm_ctx* ctx, hpvm_node* root, const void* args,
                         size_t args_size, size_t* out);
 /* Use caller-owned device memory as workspace (NULL/0: the runtime
