@@ -1354,8 +1354,9 @@ cudaError_t check_register_split(Kern* kernel) {
 // than on single CTAs with 64-byte rows (1.90 vs 1.98 ms at 8192; with
 // 64-byte rows on pairs, or 128-byte rows in two stages on single CTAs, it
 // is not faster); FP8, which hands a tensor-memory buffer between the MMA
-// and epilogue warps every 128 K, runs 2.3x slower on pairs, its hand-offs
-// then crossing CTAs. So BF16 and BF16x3 run on pairs, FP8 on single CTAs.
+// and epilogue warps every 128 K, runs 3% slower on pairs (2.2x slower
+// when the peer released buffers with a cluster-scope release). So BF16
+// and BF16x3 run on pairs, FP8 on single CTAs.
 constexpr bool pair_for_mode(int mode) { return mode == 1 || mode == 3; }
 
 // The single-instance leaf, persistent: PAIR runs clusters of 2, one cluster
