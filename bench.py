@@ -262,7 +262,7 @@ def fp8_section(args, dfg, H, W, torch, local, peaks, world, rank, barrier):
         kms, kn = H.hpvm_kernel_timing(dfg.ctx)
         for g in gs:
             dfg.wait(g)
-        ms = ev0.elapsed_time(ev1) / steps
+        ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, f"cuda:{local}")
         ent = {"value": flop * world / (ms * 1e-3) / 1e12, "ms_per_step": ms, "steps": steps,
                "leaf_ms": kms / max(1, kn)}
         if name == "fp8":
@@ -326,7 +326,7 @@ def chain_section(args, H, W, torch, local, world, barrier):
         step()
     ev1.record(stream)
     barrier()
-    ms = ev0.elapsed_time(ev1) / steps
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, dev)
     executed = (fwd + bwd + recompute) / (ms * 1e-3) / 1e12  # per GPU
     peaks = load_peaks()
     out["train_step"] = {"value": (fwd + bwd) * world / (ms * 1e-3) / 1e12, "ms_per_step": ms, "steps": steps,
@@ -349,6 +349,7 @@ def chain_section(args, H, W, torch, local, world, barrier):
         eng.stream_forward(xs, Wn)
         barrier()
         dt = time.perf_counter() - t0
+    dt = max_over_ranks(dt * 1e3, dev) * 1e-3
     out["streamed_forward"] = {"value": fwd * world / dt / 1e12, "ms_per_batch": dt * 1e3,
                                "items": items, "path": "hpvm_launch(stream_graph=1) + 64 x hpvm_push + 64 x hpvm_pop"}
     eng.close()
@@ -382,7 +383,7 @@ def batch_section(args, H, W, torch, local, world, rank, barrier):
         graph.replay()
     ev1.record(stream)
     barrier()
-    ms = ev0.elapsed_time(ev1) / reps
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / reps, f"cuda:{local}")
     # the grouped leaf's own time (runtime's CUDA events around it), the rest
     # of a batch being the batched split pre-pass
     H.hpvm_set_kernel_timing(b.ctx, True)
@@ -427,7 +428,7 @@ def batch_section(args, H, W, torch, local, world, rank, barrier):
     wall = (time.perf_counter() - t0) * 1e3
     for g in gs:
         s.wait(g)
-    ms1 = ev0.elapsed_time(ev1)
+    ms1 = max_over_ranks(ev0.elapsed_time(ev1), f"cuda:{local}")
     out["one_launch_per_instance"] = {"value": flop * world / (ms1 * 1e-3) / 1e12, "ms_per_batch": ms1,
                                       "host_ms": wall, "launches": 3 * len(probs)}
     out["speedup"] = ms1 / ms
@@ -621,7 +622,7 @@ def main():
     for _ in range(args.e2e_steps):
         h2d = e2e_step()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps * 1e3, f"cuda:{local}") * 1e-3
     for t in (hA, hB, hC):
         H.hpvm_untrack_mem(ctx, t.data_ptr())
     e2e = {"value": flop * world / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
