@@ -269,11 +269,12 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor of tcgen05 (K-major, 64-byte swizzle):
-// start address >> 4 in bits 0-13, leading byte offset >> 4 in 16-29 (not
-// used by swizzled K-major layouts), stride byte offset >> 4 in 32-45 (the
-// distance between groups of 8 rows: 8 * 64 bytes), descriptor version 1 in
-// bits 46-47, swizzle mode in bits 61-63 (4 = 64-byte swizzle).
+// Shared-memory matrix descriptor of tcgen05 (K-major, 64- or 128-byte
+// swizzle): start address >> 4 in bits 0-13, leading byte offset >> 4 in
+// 16-29 (not used by swizzled K-major layouts), stride byte offset >> 4 in
+// 32-45 (the distance between groups of 8 rows: 8 * ROW_BYTES), descriptor
+// version 1 in bits 46-47, swizzle mode in bits 61-63 (4 = 64-byte, 2 =
+// 128-byte swizzle).
 template <int ROW_BYTES>
 __device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr) {
   static_assert(ROW_BYTES == 64 || ROW_BYTES == 128, "64- or 128-byte swizzle");
@@ -659,8 +660,8 @@ __global__ void __launch_bounds__(QTHREADS, 2) quant_fp8(const float* __restrict
 
 // ---- the leaf kernel -------------------------------------------------------------
 // Persistent: CTA b handles tiles b, b + gridDim.x, ... in a grouped order
-// (GROUP_N column tiles at a time, M fastest) so CTAs that run together share
-// operand panels in L2.
+// (GROUP_N column tiles at a time, N fastest within them) so CTAs that run
+// together share operand panels in L2.
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int tile_rows, int tile_cols, int* m0,
                                             int* n0) {
   const int group = GROUP_N * tiles_m;
@@ -1221,7 +1222,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
 }
 
 // K-major operand plane: rows x K elements of `elem_bytes` bytes, row stride
-// Kp elements; TMA box of one 64-byte slab row width x box_rows rows.
+// Kp elements; TMA box of one slab row (row_bytes, 64 or 128, with the
+// matching swizzle) x box_rows rows.
 bool encode_plane(CUtensorMap* map, const void* base, int rows, int K, int Kp, int box_rows, int elem_bytes,
                   int row_bytes, std::string* err) {
   auto enc = get_encoder();
