@@ -420,8 +420,12 @@ HPVM_API int hpvm_batch_autotune(hpvm_batch* batch, void* cuda_stream, int reps,
 HPVM_API int hpvm_batch_info(hpvm_batch* batch, hpvm_batch_stats* out);
 HPVM_API int hpvm_batch_free(hpvm_batch* batch);
 /* Host-only: the tile widths a policy (0..3) picks for instances of the
- * given shapes, and the leaf's tile schedule, 4 ints per tile (instance,
- * m0, n0, 0) in launch order; tiles may be NULL to query num_tiles. */
+ * given shapes, and the leaf's schedule in launch order, 4 ints per slot
+ * (instance, m0, n0, cta): tiles go longest first to the persistent CTA
+ * with the least work so far, CTA u runs slots u, u + G, u + 2G, ... (G =
+ * the CTAs, at most the current device's SMs), and a CTA with fewer tiles
+ * than the busiest has empty slots (instance -1). tiles may be NULL to
+ * query num_tiles (the slot count). */
 HPVM_API int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, const int64_t* K, int policy,
                              int32_t* bn, int32_t* tiles, int64_t tile_cap, int64_t* num_tiles);
 

@@ -376,7 +376,8 @@ def hpvm_batch_free(batch: int) -> None:
 
 
 def hpvm_batch_plan(M, N, K, policy: int):
-    """Tile widths and the tile schedule (list of (instance, m0, n0))."""
+    """Tile widths and the schedule: one (instance, m0, n0, cta) per slot in
+    launch order, instance -1 for an empty slot."""
     n = len(M)
     arr = lambda v: (ctypes.c_int64 * max(n, 1))(*[int(x) for x in v])
     Ma, Na, Ka = arr(M), arr(N), arr(K)
@@ -385,7 +386,7 @@ def hpvm_batch_plan(M, N, K, policy: int):
     _check(LIB.hpvm_batch_plan(n, Ma, Na, Ka, int(policy), bn, None, 0, ctypes.byref(cnt)))
     tiles = (ctypes.c_int32 * max(4 * cnt.value, 1))()
     _check(LIB.hpvm_batch_plan(n, Ma, Na, Ka, int(policy), bn, tiles, cnt.value, ctypes.byref(cnt)))
-    return list(bn)[:n], [tuple(tiles[4 * i:4 * i + 3]) for i in range(cnt.value)]
+    return list(bn)[:n], [tuple(tiles[4 * i:4 * i + 4]) for i in range(cnt.value)]
 
 
 def hpvm_selftest_wait_timeout(ctx: int, limit_ms: int, cuda_stream: int = 0) -> None:

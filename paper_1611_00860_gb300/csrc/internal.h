@@ -126,12 +126,16 @@ struct TcBatch {
   int num_split_tiles = 0;
   void* d_insts = nullptr;
   void* d_tiles = nullptr;
-  int num_tiles = 0;
+  int num_tiles = 0;   // slots of the schedule (output tiles and empty slots)
+  int real_tiles = 0;  // output tiles
   int grid = 0;
 };
 std::vector<int> batch_choose_bn(const std::vector<SgemmDesc>& d, int policy);
 // tiles: 4 ints per tile (instance, m0, n0, 0) in schedule order
-void batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, std::vector<int>* tiles);
+int batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, int units, std::vector<int>* tiles);
+// SMs of the current device (148 when none answers): the persistent CTAs a
+// batch's leaf launch uses.
+int tc_num_sms();
 int tc_batch_build(TcBatch* b, std::string* err);
 cudaError_t tc_batch_run(const TcBatch& b, const DeviceStatus& st, cudaStream_t s, const LaunchHooks* hooks);
 int tc_batch_autotune(TcBatch* b, const DeviceStatus& st, cudaStream_t s, int reps, int* best_policy,

@@ -1581,7 +1581,7 @@ int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, const int64_t
   }
   auto w = hpvm::batch_choose_bn(d, policy);
   std::vector<int> t;
-  hpvm::batch_schedule(d, w, &t);
+  hpvm::batch_schedule(d, w, hpvm::tc_num_sms(), &t);
   if (bn)
     for (int i = 0; i < count; ++i) bn[i] = w[i];
   *num_tiles = (int64_t)(t.size() / 4);
@@ -1685,7 +1685,7 @@ int hpvm_batch_info(hpvm_batch* b, hpvm_batch_stats* out) {
   out->count = (int32_t)b->tb.d.size();
   out->tier = b->tb.tier;
   out->policy = b->tb.policy;
-  out->tiles = b->tb.num_tiles;
+  out->tiles = b->tb.real_tiles;
   out->split_tiles = b->tb.num_split_tiles;
   out->grid = b->tb.grid;
   out->workspace_bytes = (int64_t)b->tb.ws_bytes;

@@ -1589,9 +1589,13 @@ std::vector<int> batch_choose_bn(const std::vector<SgemmDesc>& d, int policy) {
   return bn;
 }
 
-void batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, std::vector<int>* tiles) {
-  // every output tile of every instance, in decreasing cost (longest first:
-  // the persistent CTAs take them round robin, which balances them)
+int batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, int units, std::vector<int>* tiles) {
+  // Every output tile of every instance, longest first (cost: padded K x
+  // width plus a per-tile overhead), each given to the persistent CTA with
+  // the least work so far (LPT). CTA u runs slots u, u + G, u + 2G, ...:
+  // slot r * G + u holds its r-th tile, or an empty record (instance -1)
+  // when it has fewer tiles than the busiest CTA. 4 ints per slot:
+  // (instance, m0, n0, CTA). Returns G, the CTAs the launch needs.
   struct T {
     int64_t cost;
     int inst, m0, n0;
@@ -1605,12 +1609,30 @@ void batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn,
   }
   std::stable_sort(v.begin(), v.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
   tiles->clear();
-  for (auto& t : v) {
-    tiles->push_back(t.inst);
-    tiles->push_back(t.m0);
-    tiles->push_back(t.n0);
-    tiles->push_back(0);
+  if (v.empty()) return 1;
+  const int G = std::max(1, std::min<int>((int)v.size(), units));
+  std::vector<std::vector<int>> per(G);
+  std::vector<int64_t> load(G, 0);
+  // least loaded CTA, lowest index among equals (a linear scan: G <= a few hundred)
+  for (size_t i = 0; i < v.size(); ++i) {
+    int u = 0;
+    for (int w = 1; w < G; ++w)
+      if (load[w] < load[u]) u = w;
+    per[u].push_back((int)i);
+    load[u] += v[i].cost;
   }
+  size_t rounds = 0;
+  for (auto& q : per) rounds = std::max(rounds, q.size());
+  for (size_t r = 0; r < rounds; ++r)
+    for (int u = 0; u < G; ++u) {
+      const bool has = r < per[u].size();
+      const T& t = has ? v[per[u][r]] : v[0];
+      tiles->push_back(has ? t.inst : -1);
+      tiles->push_back(has ? t.m0 : 0);
+      tiles->push_back(has ? t.n0 : 0);
+      tiles->push_back(u);
+    }
+  return G;
 }
 
 int tc_batch_build(TcBatch* b, std::string* err) {
@@ -1689,12 +1711,15 @@ int tc_batch_build(TcBatch* b, std::string* err) {
     }
   }
   std::vector<int> tiles;
-  batch_schedule(b->d, b->bn, &tiles);
+  const int G = batch_schedule(b->d, b->bn, num_sms(), &tiles);
   std::vector<GroupTile> gt(tiles.size() / 4);
+  b->real_tiles = 0;
   for (size_t t = 0; t < gt.size(); ++t) {
-    const GroupInst& in = insts[tiles[4 * t]];
     GroupTile& g = gt[t];
     memset(&g, 0, sizeof g);
+    if (tiles[4 * t] < 0) continue;  // an empty slot: M = N = K = 0, nothing to do
+    ++b->real_tiles;
+    const GroupInst& in = insts[tiles[4 * t]];
     g.inst = tiles[4 * t];
     g.m0 = tiles[4 * t + 1];
     g.n0 = tiles[4 * t + 2];
@@ -1709,7 +1734,7 @@ int tc_batch_build(TcBatch* b, std::string* err) {
   }
   if (upload(&b->d_insts, insts, err) || upload(&b->d_tiles, gt, err)) return -1;
   b->num_tiles = (int)gt.size();
-  b->grid = std::max(1, std::min(b->num_tiles, num_sms()));
+  b->grid = G;
   // kernel attributes now, so a run can be captured into a CUDA graph
   cudaError_t e;
   if (mode == 3) {
@@ -1797,6 +1822,8 @@ void tc_tile(int tier, int* tm, int* tn) {
 }
 
 size_t tc_workspace_bytes(const SgemmDesc& d, int tier) { return ws_layout(d, mode_of_tier(tier)).total; }
+
+int tc_num_sms() { return num_sms(); }
 
 cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, const DeviceStatus& st,
                       cudaStream_t s, KernelReport* rep, std::string* err, const LaunchHooks* hooks,

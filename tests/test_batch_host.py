@@ -13,14 +13,24 @@ def _grid(M, N, bn):
 def test_schedule_covers_every_tile_once(policy):
     shapes = W.batched_shapes(64, seed=5)
     M, N, K = zip(*shapes)
-    bn, tiles = H.hpvm_batch_plan(M, N, K, policy)
+    bn, slots = H.hpvm_batch_plan(M, N, K, policy)
+    tiles = [t for t in slots if t[0] >= 0]
     assert len(tiles) == len(set(tiles))
     for i, (m, n, _k) in enumerate(shapes):
         got = {(t[1], t[2]) for t in tiles if t[0] == i}
         assert got == _grid(m, n, bn[i])
-    # longest tiles first: cost (padded K x width) never increases
-    cost = [((K[t[0]] + 127) // 128 * 128) * bn[t[0]] for t in tiles]
-    assert all(a >= b for a, b in zip(cost, cost[1:]))
+    # CTA u runs slots u, u + G, ...; each CTA's tiles longest first, and
+    # the CTAs' loads (longest-first to the least loaded) differ by at most
+    # one tile's cost
+    G = max(t[3] for t in slots) + 1
+    assert len(slots) % G == 0 and all(t[3] == p % G for p, t in enumerate(slots))
+    cost = lambda t: ((K[t[0]] + 127) // 128 * 128) * bn[t[0]] + 4096
+    loads = []
+    for u in range(G):
+        c = [cost(t) for t in slots[u::G] if t[0] >= 0]
+        assert all(a >= b for a, b in zip(c, c[1:]))
+        loads.append(sum(c))
+    assert max(loads) - min(loads) <= max(cost(t) for t in tiles)
 
 
 def test_policies():
@@ -40,7 +50,8 @@ def test_batched_workload_plan():
     assert len(shapes) == 512
     assert all(32 <= x <= 2048 for s in shapes for x in s)
     M, N, K = zip(*shapes)
-    _, tiles = H.hpvm_batch_plan(M, N, K, 2)
+    _, slots = H.hpvm_batch_plan(M, N, K, 2)
+    tiles = [t for t in slots if t[0] >= 0]
     assert len(tiles) == sum(len(_grid(m, n, b)) for (m, n, _), b in zip(shapes, H.hpvm_batch_plan(M, N, K, 2)[0]))
 
 
