@@ -303,6 +303,33 @@ def test_chain_graph_lowers_on_host(ctx):
     assert H.hpvm_workspace_size(ctx, g, a) > 0
 
 
+def test_chain_workspace_holds_forwarded_planes(ctx):
+    # A 4-stage chain whose stages read the previous stage's result as B:
+    # merged, each stage's epilogue writes the next stage's B planes into one
+    # of two regions after the largest stage's planes; unmerged
+    # (HPVM_LAUNCH_NO_FUSION) every B is converted and the regions are absent.
+    from paper_1611_00860_gb300.chain import build_chain_graph
+    root = build_chain_graph(ctx, 4)
+    w, rows = 64, 48  # each stage: M = K = 64, N = 48
+
+    def al(x):
+        return (x + 255) // 256 * 256
+
+    def records(tier, flags):
+        arr = (H.RootArgs * 4)()
+        for l in range(4):
+            arr[l] = make_args(w, rows, w, 0x1000, w * w * 4, w, 0 if l else 0x2000, rows * w * 4, w,
+                               0x3000 + 0x10000 * l, rows * w * 4, w, 1.0, 0.0, False, False, tier,
+                               flags=flags)
+        return arr
+
+    for tier, planes in ((H.HPVM_TIER_BF16, 1), (H.HPVM_TIER_BF16X3, 2)):
+        stage = planes * (al(w * w * 2) + al(rows * w * 2))  # A (64 x 64) and B (48 x 64) planes
+        region = planes * al(rows * w * 2)                    # C as the next B: 48 rows of 64
+        assert H.hpvm_workspace_size(ctx, root, records(tier, 0)) == al(stage) + 2 * al(region)
+        assert H.hpvm_workspace_size(ctx, root, records(tier, H.HPVM_LAUNCH_NO_FUSION)) == stage
+
+
 def test_push_pop_need_a_streaming_graph(ctx):
     with pytest.raises(H.HpvmError):
         H.hpvm_pop(0)
