@@ -117,11 +117,20 @@ extern "C" {
  * Launches on other streams that read or refill an entry are ordered by
  * CUDA events. The cache grows up to 4 GiB; beyond that operands are
  * converted into the workspace as without the flags. hpvm_drop_planes
- * frees it. */
+ * frees it.
+ * CACHE_C: a stage whose epilogue applies a merged elementwise leaf (BF16
+ *          or BF16x3 tier, fusion on) also writes the planes of its result
+ *          C, read with C's rows as operand rows, into the cache: the entry
+ *          a later launch finds with REUSE_A for op(A) = A over C (lda =
+ *          ldc, M = C's rows, K = C's columns) or REUSE_B for op(B) = B^T
+ *          over C, the same planes that launch would convert from C, bit
+ *          for bit. Other stages drop what such an entry holds, so a later
+ *          REUSE converts. */
 #define HPVM_LAUNCH_CACHE_A 4
 #define HPVM_LAUNCH_REUSE_A 8
 #define HPVM_LAUNCH_CACHE_B 16
 #define HPVM_LAUNCH_REUSE_B 32
+#define HPVM_LAUNCH_CACHE_C 64
 
 typedef struct hpvm_ctx hpvm_ctx;
 typedef struct hpvm_node hpvm_node;

@@ -118,11 +118,16 @@ class ChainEngine:
     a merged tanh (recomputation) or tanh adjoint, and the plain sgemm stage
     (weight gradients, input gradient)."""
 
-    def __init__(self, layers: int, device: int = 0, tier: int = H.HPVM_TIER_BF16, fuse: bool = True):
+    def __init__(self, layers: int, device: int = 0, tier: int = H.HPVM_TIER_BF16, fuse: bool = True,
+                 cache_results: bool = True):
         self.layers = layers
         self.device = device
         self.tier = tier
         self.flags = 0 if fuse else H.HPVM_LAUNCH_NO_FUSION
+        # the backward's weight adjoints read the planes of H_l and dZ_l that
+        # the producing stages' epilogues cached (needs fuse)
+        self.cache_results = cache_results and fuse
+        self.kernels = 0  # kernels launched so far (hpvm_graph_info)
         self.ctx = H.hpvm_init(device)
         self.chain = build_chain_graph(self.ctx, layers)
         # H_1 .. H_{L-1} again in backward: the first L - 1 stages, all with tanh
@@ -135,6 +140,7 @@ class ChainEngine:
         self.stage_plain = build_single_stage_graph(self.ctx, None)
         self._ws = None
         self._pending: list = []
+        self._bufs: dict = {}
 
     def close(self):
         if self.ctx:
@@ -164,7 +170,9 @@ class ChainEngine:
             self._ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
             H.hpvm_set_workspace(self.ctx, self._ws.data_ptr(), self._ws.numel())
         self._reap()
-        self._pending.append(H.hpvm_launch(self.ctx, root, args, False, self._stream()))
+        g = H.hpvm_launch(self.ctx, root, args, False, self._stream())
+        self._pending.append(g)
+        self.kernels += H.hpvm_graph_info(g).kernels
 
     def _reap(self) -> None:
         """Release the handles of launches that have finished, oldest first,
@@ -179,22 +187,33 @@ class ChainEngine:
                 raise
             self._pending.pop(0)
 
+    def _buf(self, name, shape, device) -> torch.Tensor:
+        """An engine-owned buffer, the same one for every call with this name
+        and shape: its pointer is the key of the planes cached for it."""
+        key = (name, tuple(shape), str(device))
+        t = self._bufs.get(key)
+        if t is None:
+            t = self._bufs[key] = torch.empty(*shape, device=device)
+        return t
+
     def _drain(self, timeout_ms: int = 600000) -> None:
         pending, self._pending = self._pending, []
         for g in pending:
             H.hpvm_wait(g, timeout_ms)
 
-    def chain_records(self, X: torch.Tensor, Ws, outs, plane_flags: int = 0, x_flags: int = 0):
+    def chain_records(self, X: torch.Tensor, Ws, outs, plane_flags: int = 0, x_flags: int = 0,
+                      out_flags: int = 0):
         """Records of a chain graph of len(Ws) stages: stage l computes
         outs[l] = act(in_l) W_l. plane_flags (HPVM_LAUNCH_CACHE_A / REUSE_A)
         applies to the weights, the stages' A operands; x_flags
         (HPVM_LAUNCH_CACHE_B / REUSE_B) to X, the first stage's B (later
-        stages take their B planes from the previous stage's epilogue)."""
+        stages take their B planes from the previous stage's epilogue);
+        out_flags (HPVM_LAUNCH_CACHE_C) to every stage's result."""
         arr = (H.RootArgs * len(Ws))()
         for l in range(len(Ws)):
             src = X if l == 0 else outs[l - 1]
             arr[l] = _rm_product_args(outs[l], src, Ws[l], self.tier,
-                                      self.flags | plane_flags | (x_flags if l == 0 else 0))
+                                      self.flags | plane_flags | out_flags | (x_flags if l == 0 else 0))
             if l > 0:  # B arrives over the streaming edge
                 arr[l].B = None
                 arr[l].bytesB = 0
@@ -212,13 +231,19 @@ class ChainEngine:
 
     def recompute(self, X: torch.Tensor, Ws):
         """H_0 = X and H_l = tanh(H_{l-1} W_{l-1}) for l = 1..L-1: one launch
-        of the first L - 1 stages, every one with its tanh leaf merged."""
+        of the first L - 1 stages, every one with its tanh leaf merged. The
+        H_l are engine buffers (valid until the next call), and each stage's
+        epilogue also caches their planes for the weight adjoints' op(B)."""
         if self.rechain is None:
             return [X]
-        outs = [torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws[:-1]]
+        outs = [self._buf(("H", l), (X.shape[0], W.shape[1]), X.device) for l, W in enumerate(Ws[:-1])]
         # autograd guarantees the saved X and weights are unchanged since forward
-        self._run(self.rechain, self.chain_records(X, Ws[:-1], outs, H.HPVM_LAUNCH_REUSE_A, H.HPVM_LAUNCH_REUSE_B))
+        self._run(self.rechain, self.chain_records(X, Ws[:-1], outs, H.HPVM_LAUNCH_REUSE_A, H.HPVM_LAUNCH_REUSE_B,
+                                                   self._cache_c()))
         return [X] + outs
+
+    def _cache_c(self) -> int:
+        return H.HPVM_LAUNCH_CACHE_C if self.cache_results else 0
 
     # -- backward -----------------------------------------------------------------
     def backward(self, X: torch.Tensor, Ws, G: torch.Tensor):
@@ -229,12 +254,16 @@ class ChainEngine:
         for l > 0 its merged tanh adjoint gives dZ_{l-1} = dH_l * (1 - H_l^2),
         streamed into stage j+1's B (so its planes come from stage j's
         epilogue). The weight adjoints dW_l^T = dZ_l^T H_l follow, one launch
-        each (op(B) = B^T)."""
+        each (op(B) = B^T), reading the planes of dZ_l (l < L-1) and of H_l
+        (l > 0) that the adjoint and recomputing stages' epilogues cached."""
         Hs = self.recompute(X, Ws)
         L = self.layers
         rows = X.shape[0]
         G = G.contiguous()
-        dHs = [torch.empty(rows, W.shape[0], device=X.device) for W in Ws]  # dH_l: rows x w_in
+        cc = self._cache_c()
+        # dH_l: rows x w_in; dH_0 = dX is the caller's, the others engine buffers
+        dHs = [torch.empty(rows, W.shape[0], device=X.device) if l == 0 else
+               self._buf(("dH", l), (rows, W.shape[0]), X.device) for l, W in enumerate(Ws)]
         recs = (H.RootArgs * L)()
         for j, l in enumerate(range(L - 1, -1, -1)):
             W = Ws[l]
@@ -242,7 +271,7 @@ class ChainEngine:
             a = make_args(w_in, rows, w_out, W.data_ptr(), W.numel() * 4, w_out,
                           G.data_ptr() if j == 0 else None, G.numel() * 4 if j == 0 else 0, w_out,
                           dHs[l].data_ptr(), dHs[l].numel() * 4, w_in, 1.0, 0.0, True, False, self.tier,
-                          flags=self.flags)
+                          flags=self.flags | (cc if l > 0 else 0))
             if l > 0:
                 a.aux, a.bytesAux, a.ldaux = Hs[l].data_ptr(), Hs[l].numel() * 4, w_in
             recs[j] = a
@@ -254,9 +283,12 @@ class ChainEngine:
             dZ = G if l == L - 1 else dHs[l + 1]
             # dW^T = dZ^T H_l: M = w_out, N = w_in, K = rows; A = dZ buffer, B = H_l buffer (B^T)
             dW = torch.empty_like(W)
+            reuse = 0
+            if cc:
+                reuse = (H.HPVM_LAUNCH_REUSE_A if l < L - 1 else 0) | (H.HPVM_LAUNCH_REUSE_B if l > 0 else 0)
             a = make_args(w_out, w_in, rows, dZ.data_ptr(), dZ.numel() * 4, w_out, Hs[l].data_ptr(),
                           Hs[l].numel() * 4, w_in, dW.data_ptr(), dW.numel() * 4, w_out, 1.0, 0.0,
-                          False, True, self.tier, flags=self.flags)
+                          False, True, self.tier, flags=self.flags | reuse)
             self._run(self.stage_plain, a)
             dWs[l] = dW
         return dHs[0], dWs

@@ -62,11 +62,16 @@ inline void hook_end(const LaunchHooks* h, cudaStream_t s) {
 // op(B) = B with K = this M (a streaming edge between stages): column n of
 // C becomes plane row n, at the offsets tc_operand_layout(tier, N, M) gives
 // from fwd. Those planes equal what that leaf's own conversion of C makes.
+// rows (same tiers): the epilogue also writes the planes of C with rows of
+// C as operand rows (row m of C is plane row m, K = N) at the offsets
+// tc_operand_layout(tier, M, N) gives from rows: the planes a later leaf
+// reading C as op(A) = A or op(B) = B^T converts from C, bit for bit.
 struct Epilogue {
   int kind = 0;
   const float* aux = nullptr;
   int64_t ldaux = 0;
   void* fwd = nullptr;
+  void* rows = nullptr;
 };
 // Standalone elementwise kernel on the M x N column-major C (fp32_leaf.cu).
 cudaError_t launch_elementwise(const SgemmDesc& d, const Epilogue& e, cudaStream_t s);

@@ -882,6 +882,13 @@ int plane_entry(hpvm_ctx* ctx, const void* src, int64_t ld, int64_t rows, int64_
   return HPVM_OK;
 }
 
+// Marks every cache entry of src read with this leading dimension, rows, K
+// and layout (any tier) as not holding the operand: its next use converts.
+void invalidate_planes(hpvm_ctx* ctx, const void* src, int64_t ld, int64_t rows, int64_t K, int layout) {
+  for (auto& p : ctx->planes)
+    if (p->src == src && p->ld == ld && p->rows == rows && p->K == K && p->layout == layout) p->valid = false;
+}
+
 // After a launch on stream s read (or filled) entry e.
 int plane_used(PlaneEntry* e, const hpvm::OperandPlanes& op, cudaStream_t s) {
   if (!op.ready) {
@@ -973,6 +980,21 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
         }
       }
       if (forwards_b(P, si)) S.epi.fwd = static_cast<uint8_t*>(ws) + WP.region(si);
+      // HPVM_LAUNCH_CACHE_C: the merged elementwise leaf's epilogue fills
+      // the cache entry of C read with C's rows as operand rows (the key of
+      // op(A) = A or op(B) = B^T over C, K = N); a stage that cannot (no
+      // merged leaf, FP8) drops the entry's contents instead
+      hpvm::OperandPlanes pc;
+      PlaneEntry* ec = nullptr;
+      if (flags & HPVM_LAUNCH_CACHE_C) {
+        if (fuse && S.epi.kind != 0 && (tier == HPVM_TIER_BF16 || tier == HPVM_TIER_BF16X3)) {
+          if ((rc = plane_entry(ctx, S.d.C, S.d.ldc, S.d.M, S.d.N, 1, tier, false, s, &ec, &pc)) != HPVM_OK)
+            return rc;
+          if (ec) S.epi.rows = pc.base;
+        } else {
+          invalidate_planes(ctx, S.d.C, S.d.ldc, S.d.M, S.d.N, 1);
+        }
+      }
       hpvm::Epilogue none;
       cudaError_t e;
       switch (tier) {
@@ -992,6 +1014,10 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
       if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
       if (ea && (rc = plane_used(ea, pa, s)) != HPVM_OK) return rc;
       if (eb && (rc = plane_used(eb, pb, s)) != HPVM_OK) return rc;
+      if (ec) {
+        if ((e = cudaEventRecord(ec->converted, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((rc = plane_used(ec, pc, s)) != HPVM_OK) return rc;
+      }
       if (S.epi.kind && !fuse) {
         e = hpvm::launch_elementwise(S.d, S.epi, s);
         if (e != cudaSuccess) return cuda_fail(e, "elementwise leaf launch");

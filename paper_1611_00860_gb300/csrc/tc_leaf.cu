@@ -146,6 +146,13 @@ struct TcParams {
   __nv_bfloat16* fwd_hi;
   __nv_bfloat16* fwd_lo;
   int64_t fwd_kp;
+  // Row planes of C (or null): row m of C as K-major row m (row_kp
+  // elements) of a BF16 hi plane and, BF16x3, of the lo plane that follows
+  // it (the operand_layout(M, N) offsets), for a later leaf that reads C
+  // with rows of C as operand rows (op(A) = A, op(B) = B^T). Two fields
+  // only: a third tips the plain leaf's epilogue into spills.
+  __nv_bfloat16* row_hi;
+  int64_t row_kp;
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -1164,20 +1171,73 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int u = 0; u < CGRP; ++u) hx[u] = (u0 + u < ncols) ? __ldcs(hp + (int64_t)(u0 + u) * p.ldaux) : 0.f;
           }
+          // C, the forwarded planes and, for the tanh stages (EPI != 0),
+          // C's row planes. The plain leaf keeps its own loop: ptxas spills
+          // its epilogue when that loop takes the blocked form below.
+          constexpr bool ROWS = !GROUPED && !C_::FP8 && EPI != 0;
+          if constexpr (!ROWS) {
 #pragma unroll
-          for (int u = 0; u < CGRP; ++u) {
-            if (u0 + u < ncols) {
-              float x = (v.beta == 0.f) ? v.alpha * acc[u0 + u] : fmaf(v.alpha, acc[u0 + u], v.beta * old[u]);
-              if (EPI == 1) x = tanhf(x);
-              if (EPI == 2) x = x * (1.f - hx[u] * hx[u]);
-              __stcs(cp + (int64_t)(u0 + u) * v.ldc, x);
-              if (!GROUPED && !C_::FP8 && p.fwd_hi) {
-                // the next stage's operand planes of this output (a warp
-                // writes 32 consecutive K elements of one plane row)
-                const int64_t o = (int64_t)(col0 + u0 + u) * p.fwd_kp + row;
-                const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                p.fwd_hi[o] = h;
-                if (NPROD == 3) p.fwd_lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+            for (int u = 0; u < CGRP; ++u) {
+              if (u0 + u < ncols) {
+                float x = (v.beta == 0.f) ? v.alpha * acc[u0 + u] : fmaf(v.alpha, acc[u0 + u], v.beta * old[u]);
+                if (EPI == 1) x = tanhf(x);
+                if (EPI == 2) x = x * (1.f - hx[u] * hx[u]);
+                __stcs(cp + (int64_t)(u0 + u) * v.ldc, x);
+                if (!GROUPED && !C_::FP8 && p.fwd_hi) {
+                  // the next stage's operand planes of this output (a warp
+                  // writes 32 consecutive K elements of one plane row)
+                  const int64_t o = (int64_t)(col0 + u0 + u) * p.fwd_kp + row;
+                  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                  p.fwd_hi[o] = h;
+                  if (NPROD == 3) p.fwd_lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+                }
+              }
+            }
+          } else {
+            // 8 columns at a time, one 16-byte store per row plane and row
+#pragma unroll
+            for (int j = 0; j < CGRP / 8; ++j) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                float x2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int u = 8 * j + 2 * e + h;
+                  x2[h] = 0.f;
+                  if (u0 + u < ncols) {
+                    float x = (v.beta == 0.f) ? v.alpha * acc[u0 + u] : fmaf(v.alpha, acc[u0 + u], v.beta * old[u]);
+                    if (EPI == 1) x = tanhf(x);
+                    if (EPI == 2) x = x * (1.f - hx[u] * hx[u]);
+                    x2[h] = x;
+                    __stcs(cp + (int64_t)(u0 + u) * v.ldc, x);
+                    if (!GROUPED && !C_::FP8 && p.fwd_hi) {
+                      // the next stage's operand planes of this output (a warp
+                      // writes 32 consecutive K elements of one plane row)
+                      const int64_t o = (int64_t)(col0 + u0 + u) * p.fwd_kp + row;
+                      const __nv_bfloat16 hv = __float2bfloat16_rn(x);
+                      p.fwd_hi[o] = hv;
+                      if (NPROD == 3) p.fwd_lo[o] = __float2bfloat16_rn(x - __bfloat162float(hv));
+                    }
+                  }
+                }
+                const __nv_bfloat162 hh = __floats2bfloat162_rn(x2[0], x2[1]);
+                hw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                if (NPROD == 3) {
+                  const __nv_bfloat162 ll = __floats2bfloat162_rn(x2[0] - __low2float(hh), x2[1] - __high2float(hh));
+                  lw[e] = *reinterpret_cast<const uint32_t*>(&ll);
+                }
+              }
+              const int c = col0 + u0 + 8 * j;  // a multiple of 8: 16-byte aligned
+              if (p.row_hi && c < v.N) {
+                // columns past N are zeros inside the plane row's padding
+                const int64_t o = (int64_t)row * p.row_kp + c;
+                *reinterpret_cast<uint4*>(p.row_hi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                if (NPROD == 3) {
+                  // the lo plane starts at the hi plane's 256-byte-aligned end
+                  const int64_t lo = (((int64_t)p.M * p.row_kp * 2 + 255) & ~(int64_t)255) / 2;
+                  *reinterpret_cast<uint4*>(p.row_hi + lo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
               }
             }
           }
@@ -1486,7 +1546,15 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
     }
   }
   TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, st.dev, epi.aux, epi.ldaux,
-               nullptr, nullptr, 0};
+               nullptr, nullptr, 0, nullptr, 0};
+  if (epi.rows && !C_::FP8) {
+    // the planes of C with rows of C as operand rows: rows = M, row length N
+    const OperandLayout F = operand_layout(M, N, MODE);
+    uint8_t* f = static_cast<uint8_t*>(epi.rows);
+    prm.row_hi = reinterpret_cast<__nv_bfloat16*>(f + F.hi);
+    prm.row_kp = (N + 7) / 8 * 8;
+    if (MODE == 3 && F.lo != align256((size_t)M * prm.row_kp * 2)) return cudaErrorInvalidValue;
+  }
   if (epi.fwd && !C_::FP8) {
     // the planes of C as op(B) of a leaf with K = M: rows = N, row length M
     const OperandLayout F = operand_layout(N, M, MODE);

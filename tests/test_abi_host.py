@@ -340,7 +340,8 @@ def test_plane_cache_on_a_host_only_context(ctx):
     assert H.hpvm_plane_cache_bytes(ctx) == 0
     H.hpvm_drop_planes(ctx)
     assert H.hpvm_plane_cache_bytes(ctx) == 0
-    flags = (H.HPVM_LAUNCH_CACHE_A, H.HPVM_LAUNCH_REUSE_A, H.HPVM_LAUNCH_CACHE_B, H.HPVM_LAUNCH_REUSE_B)
-    assert len(set(flags)) == 4 and all(f & (H.HPVM_LAUNCH_NO_EVENT | H.HPVM_LAUNCH_NO_FUSION) == 0 for f in flags)
+    flags = (H.HPVM_LAUNCH_CACHE_A, H.HPVM_LAUNCH_REUSE_A, H.HPVM_LAUNCH_CACHE_B, H.HPVM_LAUNCH_REUSE_B,
+             H.HPVM_LAUNCH_CACHE_C)
+    assert len(set(flags)) == 5 and all(f & (H.HPVM_LAUNCH_NO_EVENT | H.HPVM_LAUNCH_NO_FUSION) == 0 for f in flags)
     with pytest.raises(H.HpvmError):
         H.hpvm_plane_cache_bytes(None)

@@ -22,6 +22,7 @@ from oracle import adjoint as J
 from oracle import sgemm as O
 from paper_1611_00860_gb300 import _lib as H
 from paper_1611_00860_gb300.chain import ChainEngine, chain_apply, _rm_product_args
+from paper_1611_00860_gb300.sgemm import make_args
 
 pytestmark = pytest.mark.gpu
 
@@ -95,6 +96,80 @@ def test_forwarded_planes_equal_converted(cuda_device, tier, rows, w):
     # merged: 4 leaves + 4 weight conversions + X's; unmerged: 4 leaves,
     # 3 tanh kernels, 4 + 4 conversions
     assert kernels == [2 * layers + 1, 2 * layers + (layers - 1) + layers]
+
+
+@pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
+@pytest.mark.parametrize("rows,w", [(300, 264), (77, 260), (520, 136)])
+def test_cached_result_planes_equal_converted(cuda_device, tier, rows, w):
+    # HPVM_LAUNCH_CACHE_C: the recomputing stages' and the adjoint stages'
+    # epilogues also write the planes of H_l and dZ_l in the layout the
+    # weight adjoints read (rows of the result as operand rows, K = rows of
+    # the batch: 300, 77 and 520 are ragged against the 64-wide K slabs,
+    # w = 260 pads each plane row). The weight adjoints then convert only G
+    # and X: 2 (L - 1) conversions fewer, and every gradient bit for bit
+    # the same as with each operand converted from its FP32 values.
+    layers = 4
+    X, Ws, G = _inputs(1, rows, w, layers, seed=rows + 3 * w)
+    Xd, Gd = X[0].cuda(), G[0].cuda()
+    Wd = [W.cuda() for W in Ws]
+    got, kernels, cache = [], [], []
+    for cached in (True, False):
+        eng = ChainEngine(layers, tier=tier, cache_results=cached)
+        try:
+            for _ in range(2):  # the second step refills the entries the first made
+                eng.forward(Xd, Wd)
+                k0 = eng.kernels
+                dX, dWs = eng.backward(Xd, Wd, Gd)
+                eng._drain()
+            kernels.append(eng.kernels - k0)
+            cache.append(H.hpvm_plane_cache_bytes(eng.ctx))
+            got.append([t.cpu() for t in [dX] + dWs])
+        finally:
+            eng.close()
+    for a, b in zip(*got):
+        assert torch.equal(a, b)
+    assert kernels[1] - kernels[0] == 2 * (layers - 1)
+    # the cache holds the 2 (L - 1) result entries besides the weights' and X's
+    kp = -(-rows // 8) * 8
+    entry = -(-w * kp * 2 // 256) * 256 * (2 if tier == H.HPVM_TIER_BF16X3 else 1)
+    assert cache[0] - cache[1] == 2 * (layers - 1) * entry
+    ref = J.chain_backward(X[0].double().numpy(), [W.double().numpy() for W in Ws], G[0].double().numpy())
+    assert O.normwise_rel_err(got[0][0].double().numpy(), ref[0]) <= TOL[tier]
+
+
+@pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
+def test_cache_c_on_a_stage_without_merged_leaf_drops_the_entry(cuda_device, tier):
+    # A tanh stage with CACHE_C fills C's row-plane entry; a plain stage (no
+    # merged leaf: it cannot write planes) that overwrites C with CACHE_C
+    # must drop that entry, so a later REUSE_A over C converts the new values.
+    eng = ChainEngine(1, tier=tier)
+    try:
+        g = torch.Generator().manual_seed(5)
+        Hm = torch.randn(200, 96, generator=g).cuda()
+        W1 = (torch.randn(96, 136, generator=g) / 10).cuda()
+        W2 = (torch.randn(96, 136, generator=g) / 10).cuda()
+        V = torch.randn(200, 72, generator=g).cuda()
+        out = torch.empty(200, 136, device="cuda")  # C: 136 x 200 column-major
+        eng._run(eng.stage_tanh, _rm_product_args(out, Hm, W1, tier, H.HPVM_LAUNCH_CACHE_C))
+        eng._run(eng.stage_plain, _rm_product_args(out, Hm, W2, tier, H.HPVM_LAUNCH_CACHE_C))
+
+        def consume(flags):
+            # P = C V^T over the column-major C (136 x 200): op(A) = A, K = 200
+            P = torch.empty(72, 136, device="cuda")
+            eng._run(eng.stage_plain, make_args(136, 72, 200, out.data_ptr(), out.numel() * 4, 136,
+                                                V.data_ptr(), V.numel() * 4, 72, P.data_ptr(), P.numel() * 4,
+                                                136, 1.0, 0.0, False, True, tier, flags=flags))
+            eng._drain()
+            return P.cpu()
+        assert torch.equal(consume(H.HPVM_LAUNCH_REUSE_A), consume(0))
+        # and with the tanh stage last, the entry it fills is the one REUSE_A reads
+        eng._run(eng.stage_tanh, _rm_product_args(out, Hm, W1, tier, H.HPVM_LAUNCH_CACHE_C))
+        k0 = eng.kernels
+        reused = consume(H.HPVM_LAUNCH_REUSE_A)
+        assert eng.kernels - k0 == 2  # the leaf and V's conversion only
+        assert torch.equal(reused, consume(0))
+    finally:
+        eng.close()
 
 
 @pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
