@@ -66,12 +66,16 @@ inline void hook_end(const LaunchHooks* h, cudaStream_t s) {
 // C as operand rows (row m of C is plane row m, K = N) at the offsets
 // tc_operand_layout(tier, M, N) gives from rows: the planes a later leaf
 // reading C as op(A) = A or op(B) = B^T converts from C, bit for bit.
+// split_as (>= 0): the leaf splits its last round's tiles only where the
+// leaf with that merged elementwise kind would, so an unmerged stage (a
+// plain leaf, then the elementwise kernel) rounds as the merged one does.
 struct Epilogue {
   int kind = 0;
   const float* aux = nullptr;
   int64_t ldaux = 0;
   void* fwd = nullptr;
   void* rows = nullptr;
+  int split_as = -1;
 };
 // Standalone elementwise kernel on the M x N column-major C (fp32_leaf.cu).
 cudaError_t launch_elementwise(const SgemmDesc& d, const Epilogue& e, cudaStream_t s);

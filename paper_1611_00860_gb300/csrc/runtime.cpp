@@ -996,6 +996,7 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
         }
       }
       hpvm::Epilogue none;
+      none.split_as = S.epi.kind;  // unmerged: split the tail as the merged leaf would
       cudaError_t e;
       switch (tier) {
         case HPVM_TIER_FP32_DFG:

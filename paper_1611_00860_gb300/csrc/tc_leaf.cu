@@ -130,14 +130,19 @@ struct Cfg {
   static_assert(MODE != 3 || KC_SLABS * BK == 192, "BF16x3: chunks of 192 K elements");
 };
 
+// Kept within 120 bytes: ptxas spills the epilogue of the plain leaf once
+// this struct grows past 128 (the two K-major row lengths are 32-bit and
+// fill alignment gaps).
 struct TcParams {
   int M, N, K;
+  int row_kp;  // row planes: elements per plane row
   float* C;
   int64_t ldc;
   float alpha, beta;
   const float* scaleA;  // FP8: [ceil(M/128)][nkb] block scales of op(A)
   const float* scaleB;  // FP8: [ceil(N/128)][nkb] block scales of op(B)^T
   int nkb;              // FP8: ceil(K/128)
+  int fwd_kp;           // forwarded planes: elements per plane row
   int* status;
   const float* aux;     // EPI 2: H, column-major with leading dimension ldaux
   int64_t ldaux;
@@ -145,14 +150,15 @@ struct TcParams {
   // (fwd_kp elements a row) of a BF16 hi plane and, BF16x3, a lo plane.
   __nv_bfloat16* fwd_hi;
   __nv_bfloat16* fwd_lo;
-  int64_t fwd_kp;
   // Row planes of C (or null): row m of C as K-major row m (row_kp
   // elements) of a BF16 hi plane and, BF16x3, of the lo plane that follows
   // it (the operand_layout(M, N) offsets), for a later leaf that reads C
-  // with rows of C as operand rows (op(A) = A, op(B) = B^T). Two fields
-  // only: a third tips the plain leaf's epilogue into spills.
+  // with rows of C as operand rows (op(A) = A, op(B) = B^T).
   __nv_bfloat16* row_hi;
-  int64_t row_kp;
+  // Tail split (or null): the partial sums of the K halves of the last
+  // round's tiles, then one arrival counter per tile, CTA and epilogue warp
+  // (zeroed before the launch).
+  float* split_ws;
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -669,6 +675,25 @@ __global__ void __launch_bounds__(QTHREADS, 2) quant_fp8(const float* __restrict
 // Persistent: CTA b handles tiles b, b + gridDim.x, ... in a grouped order
 // (GROUP_N column tiles at a time, N fastest within them) so CTAs that run
 // together share operand panels in L2.
+// Tail split of a persistent single-instance launch: when the last round of
+// whole tiles would leave more than half of the units (CTAs or pairs) idle,
+// each of its tiles runs as two K halves on two units. Returns how many
+// tiles split (0: none). Host and kernel take the decision with this one
+// function, from the same tile count, unit count and K slabs.
+__host__ __device__ constexpr int tail_split_tiles(int tiles, int units, int num_kb) {
+  return (units > 0 && tiles >= units && tiles % units > 0 && 2 * (tiles % units) <= units && num_kb >= 4)
+             ? tiles % units
+             : 0;
+}
+
+// The leaf variants built with the tail split: BF16 and BF16x3 on pairs,
+// plain or with the tanh leaf merged (BF16 only). In the others (FP8, the
+// tanh adjoint, BF16x3 with tanh) ptxas spilled more of the epilogue's
+// registers with the split compiled in.
+__host__ __device__ constexpr bool tail_split_variant(int mode, int epi, bool grouped) {
+  return !grouped && mode != 8 && (epi == 0 || (epi == 1 && mode == 1));
+}
+
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int tile_rows, int tile_cols, int* m0,
                                             int* n0) {
   const int group = GROUP_N * tiles_m;
@@ -720,6 +745,9 @@ struct TileView {
   int64_t ldc;
   int M, N, K, bn, m0, n0;
   float alpha, beta;
+  int kb0, kb1;  // the K slabs this unit accumulates
+  int part;      // tail split: which K half (0, 1), else -1
+  int tail;      // tail split: the tile's index among the split tiles
 };
 
 // EPI: 0 none; 1 C = tanh(alpha*acc + beta*C); 2 C = (alpha*acc + beta*C)*(1 - H^2)
@@ -769,6 +797,23 @@ __global__ void __launch_bounds__(THREADS, 1)
   constexpr int TN = C_::TN, NBUF = C_::NBUF;
   const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + TN - 1) / TN;
   const int num_tiles = GROUPED ? gp.num_tiles : tiles_m * tiles_n;
+  // Work units: the tiles, except that a tail split (split_ws given) runs
+  // each of the last n_split tiles as two units, one per K half. Both
+  // halves write their partial sums to split_ws; the second to arrive adds
+  // the other's and writes C (a + b == b + a: the same C whichever is
+  // second), the first is done with the tile.
+  // (compiled in where it leaves ptxas's register allocation as it was)
+  constexpr bool TAIL = tail_split_variant(MODE, EPI, GROUPED);
+  const int num_kb_all = GROUPED ? 0 : (p.K + BK - 1) / BK;
+  const int n_split = (TAIL && p.split_ws) ? tail_split_tiles(num_tiles, num_units, num_kb_all) : 0;
+  const int split_base = num_tiles - n_split;
+  const int num_work = num_tiles + n_split;
+  auto work_tile = [&](int t, int* part) {
+    *part = -1;
+    if (t < split_base) return t;
+    *part = (t - split_base) & 1;
+    return split_base + ((t - split_base) >> 1);
+  };
 
   // GROUPED: tile t's record (an empty one past the end); the roles load the
   // next tile's record while they work on the current one
@@ -794,6 +839,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       v.beta = gt.beta;
       v.m0 = gt.m0;
       v.n0 = gt.n0;
+      v.kb0 = 0;
+      v.kb1 = (gt.K + BK - 1) / BK;
+      v.part = -1;
+      v.tail = 0;
     } else {
       v.tm[0] = &tmA_hi;
       v.tm[1] = &tmA_lo;
@@ -807,7 +856,19 @@ __global__ void __launch_bounds__(THREADS, 1)
       v.bn = TN;
       v.alpha = p.alpha;
       v.beta = p.beta;
-      tile_coords(t, tiles_m, tiles_n, TM, TN, &v.m0, &v.n0);
+      if constexpr (TAIL) {
+        const int tile = work_tile(t, &v.part);
+        tile_coords(tile, tiles_m, tiles_n, TM, TN, &v.m0, &v.n0);
+        v.kb0 = v.part == 1 ? num_kb_all / 2 : 0;
+        v.kb1 = v.part == 0 ? num_kb_all / 2 : num_kb_all;
+        v.tail = tile - split_base;
+      } else {
+        tile_coords(t, tiles_m, tiles_n, TM, TN, &v.m0, &v.n0);
+        v.kb0 = 0;
+        v.kb1 = num_kb_all;
+        v.part = -1;
+        v.tail = 0;
+      }
     }
     return v;
   };
@@ -870,16 +931,16 @@ __global__ void __launch_bounds__(THREADS, 1)
       int it = 0;
       bool go = true;
       GroupTile nx = fetch(unit);
-      for (int t = unit; go && t < num_tiles; t += num_units) {
+      for (int t = unit; go && t < num_work; t += num_units) {
         const GroupTile cur = nx;
         nx = fetch(t + num_units);
         const TileView v = view(t, cur);
-        const int num_kb = (v.K + BK - 1) / BK;
         const uint32_t b_rows = PAIR ? (uint32_t)C_::B_ROWS : (uint32_t)v.bn;
         const uint32_t bytes = C_::PLANES * (C_::A_SLAB + b_rows * C_::ROW_BYTES);
         const int ma = v.m0 + (int)rank * BM;
         const int nb = v.n0 + (int)rank * C_::B_ROWS;
-        for (int kb = 0; kb < num_kb; ++kb, ++it) {
+        const int kb_hi = TAIL ? v.kb1 : (v.K + BK - 1) / BK;
+        for (int kb = TAIL ? v.kb0 : 0; kb < kb_hi; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1;
           if (!mbar_wait<PAIR>(&empty[s], ph ^ 1, abort_flag, p.status, ST_PRODUCER, WAIT_LIMIT_NS, peer_abort)) {
@@ -917,12 +978,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       int it = 0, g = 0;
       bool go = true;
       GroupTile nx = fetch(unit);
-      for (int t = unit; go && t < num_tiles; t += num_units) {
+      for (int t = unit; go && t < num_work; t += num_units) {
         const GroupTile cur = nx;
         nx = fetch(t + num_units);
         const TileView v = view(t, cur);
-        const int num_kb = (v.K + BK - 1) / BK;
-        const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
+        const int kb_lo = TAIL ? v.kb0 : 0, kb_hi = TAIL ? v.kb1 : (v.K + BK - 1) / BK;
+        const int num_chunks = (kb_hi - kb_lo + KC_SLABS - 1) / KC_SLABS;
         const int n_mma = GROUPED ? v.bn : TN;
         const uint32_t idesc = C_::FP8 ? idesc_e4m3(TM, n_mma) : idesc_bf16(TM, n_mma);
         for (int c = 0; go && c < num_chunks; ++c, ++g) {
@@ -935,8 +996,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           tc_fence_after();
           const uint32_t dst = tmem + buf * TN;
-          const int kb_end = min(num_kb, (c + 1) * KC_SLABS);
-          for (int kb = c * KC_SLABS; kb < kb_end; ++kb, ++it) {
+          const int kb_first = kb_lo + c * KC_SLABS;
+          const int kb_end = min(kb_hi, kb_first + KC_SLABS);
+          for (int kb = kb_first; kb < kb_end; ++kb, ++it) {
             const int s = it % S;
             const uint32_t ph = (it / S) & 1;
             if (!mbar_wait<PAIR>(&full[s], ph, abort_flag, p.status, ST_MMA, WAIT_LIMIT_NS, peer_abort)) {
@@ -949,7 +1011,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int kk = 0; kk < BK / MMA_K; ++kk) {
               const uint32_t off = kk * MMA_K * C_::ELEM_BYTES;  // bytes along the slab row
-              const uint32_t acc = (kb == c * KC_SLABS && kk == 0) ? 0u : 1u;
+              const uint32_t acc = (kb == kb_first && kk == 0) ? 0u : 1u;
               constexpr int RB = C_::ROW_BYTES;
               if (C_::FP8) {
                 umma_e4m3<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, acc);
@@ -1025,13 +1087,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     int g = 0;
     bool go = true;
     GroupTile nx = fetch(unit);
-    for (int t = unit; go && t < num_tiles; t += num_units) {
+    for (int t = unit; go && t < num_work; t += num_units) {
       const GroupTile cur = nx;
       nx = fetch(t + num_units);
       const TileView v = view(t, cur);
       const int m_cta = v.m0 + (int)rank * BM;  // first row of this CTA's half
-      const int num_kb = (v.K + BK - 1) / BK;
-      const int num_chunks = (num_kb + KC_SLABS - 1) / KC_SLABS;
+      const int num_chunks = TAIL ? (v.kb1 - v.kb0 + KC_SLABS - 1) / KC_SLABS
+                                  : ((v.K + BK - 1) / BK + KC_SLABS - 1) / KC_SLABS;
       // the columns this warp owns: [coff, coff + cols) of the tile
       const int cols = GROUPED ? v.bn / 2 : (h ? C_::COLS1 : C_::COLS0);
       const int coff = GROUPED ? h * (v.bn / 2) : (h ? C_::COLS0 : 0);
@@ -1046,8 +1108,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       const float* sa = nullptr;
       const float* sb = nullptr;
       if (C_::FP8) {
-        sa = p.scaleA + (int64_t)(m_cta / FP8_BLOCK) * p.nkb;
-        sb = p.scaleB + (int64_t)((v.n0 + coff) / FP8_BLOCK) * p.nkb;
+        // (a K half starts at its first slab's scale block)
+        sa = p.scaleA + (int64_t)(m_cta / FP8_BLOCK) * p.nkb + (TAIL ? v.kb0 / KC_SLABS : 0);
+        sb = p.scaleB + (int64_t)((v.n0 + coff) / FP8_BLOCK) * p.nkb + (TAIL ? v.kb0 / KC_SLABS : 0);
       }
       // FP8: the block scales of chunks c and c + 1, loaded two chunks ahead
       // so their L2 round trips stay off the chunk-to-chunk critical path
@@ -1127,14 +1190,38 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (!go) break;
+      if (TAIL && v.part >= 0) {
+        // tail split: this half's partial sums out (per thread its ACC
+        // columns, coalesced across the warp), then one arrival per warp;
+        // the second half to arrive adds the other's and writes C
+        constexpr int RANKS = PAIR ? 2 : 1;
+        const int wi = warp - EPI_WARP0;
+        const int64_t slot = ((int64_t)(v.tail * 2 + v.part) * RANKS + (int)rank) * EPI_WARPS + wi;
+        const int64_t other = slot + (v.part ? -1 : 1) * (int64_t)RANKS * EPI_WARPS;
+        int* cnt = reinterpret_cast<int*>(p.split_ws + (int64_t)n_split * 2 * RANKS * EPI_WARPS * ACC * 32) +
+                   ((int64_t)v.tail * RANKS + (int)rank) * EPI_WARPS + wi;
+        float* mine = p.split_ws + slot * (ACC * 32) + lane;
+#pragma unroll
+        for (int u = 0; u < ACC; ++u) __stcg(mine + u * 32, acc[u]);
+        __threadfence();
+        __syncwarp();
+        int arrived = 0;
+        if (lane == 0) arrived = atomicAdd(cnt, 1);
+        arrived = __shfl_sync(0xffffffffu, arrived, 0);
+        if (arrived == 0) continue;  // the other half writes C
+        __threadfence();
+        const float* theirs = p.split_ws + other * (ACC * 32) + lane;
+#pragma unroll
+        for (int u = 0; u < ACC; ++u) acc[u] += __ldcg(theirs + u * 32);
+      }
       if (!GROUPED && (EPI == 2 || p.beta != 0.f)) {
         // The next tile's epilogue inputs (old C when beta != 0, H for the
         // tanh adjoint) are fetched into L2 now, while its MMAs run: its
         // loads then wait on L2 rather than on DRAM.
         const int tn = t + num_units;
-        if (tn < num_tiles) {
-          int nm0, nn0;
-          tile_coords(tn, tiles_m, tiles_n, TM, TN, &nm0, &nn0);
+        if (tn < num_work) {
+          int nm0, nn0, npart;
+          tile_coords(TAIL ? work_tile(tn, &npart) : tn, tiles_m, tiles_n, TM, TN, &nm0, &nn0);
           const int r0 = nm0 + (int)rank * BM + q * 32;  // this warp's 32 rows there
           const int c0 = nn0 + coff;
           if (r0 < p.M && c0 < p.N) {
@@ -1320,12 +1407,36 @@ int num_sms() {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Workspace layout of a mode: operand planes (and FP8 block scales).
+// Which leaves of a single instance run on CTA pairs (256 x 256 tiles,
+// cta_group::2) rather than on single CTAs (128 x 256 tiles). Measured at
+// M = N = K = 8192 and 16384: pairs make plain BF16 (one accumulation per
+// tile) 5-10% faster; BF16x3 on pairs with 128-byte slab rows is 4% faster
+// than on single CTAs with 64-byte rows (1.90 vs 1.98 ms at 8192; with
+// 64-byte rows on pairs, or 128-byte rows in two stages on single CTAs, it
+// is not faster); FP8, which hands a tensor-memory buffer between the MMA
+// and epilogue warps every 128 K, runs 3% slower on pairs (2.2x slower
+// when the peer released buffers with a cluster-scope release). So BF16
+// and BF16x3 run on pairs, FP8 on single CTAs.
+constexpr bool pair_for_mode(int mode) { return mode == 1 || mode == 3; }
+
+// Workspace layout of a mode: operand planes (and FP8 block scales), then
+// the tail split's region where the pairs' tiles call for one.
 struct WsLayout {
   int64_t Kp = 0;  // row stride of the planes, in elements (16-byte rows)
   size_t a_hi = 0, a_lo = 0, b_hi = 0, b_lo = 0, sa = 0, sb = 0, total = 0;
   int nkb = 0;     // FP8: scale blocks along K
+  size_t planes = 0;                   // end of the planes: the least a launch needs
+  size_t split = 0, split_bytes = 0;   // the tail split's partial sums and counters
 };
+
+// Bytes of a tail split of n tiles: per tile, K half, CTA and epilogue warp
+// ACC x 32 FP32 partial sums, then per tile, CTA and warp one counter.
+size_t split_sums_bytes(int n, int ranks, int acc) {
+  return (size_t)n * 2 * ranks * EPI_WARPS * acc * 32 * sizeof(float);
+}
+size_t split_region_bytes(int n, int ranks, int acc) {
+  return align256(split_sums_bytes(n, ranks, acc)) + align256((size_t)n * ranks * EPI_WARPS * sizeof(int));
+}
 WsLayout ws_layout(const SgemmDesc& d, int mode) {
   WsLayout L;
   const int eb = mode == 8 ? 1 : 2;
@@ -1340,6 +1451,19 @@ WsLayout ws_layout(const SgemmDesc& d, int mode) {
     L.nkb = (int)((d.K + FP8_BLOCK - 1) / FP8_BLOCK);
     L.sa = off; off += align256((size_t)((d.M + FP8_BLOCK - 1) / FP8_BLOCK) * L.nkb * 4);
     L.sb = off; off += align256((size_t)((d.N + FP8_BLOCK - 1) / FP8_BLOCK) * L.nkb * 4);
+  }
+  L.planes = off;
+  if (pair_for_mode(mode)) {
+    // the tail split's region, for the pairs the GPU runs at once
+    using P = Cfg<1, true>;
+    static_assert(Cfg<3, true>::BK == P::BK && Cfg<3, true>::ACC == P::ACC, "one split layout for both tiers");
+    const int64_t tiles = ((d.M + 2 * BM - 1) / (2 * BM)) * ((d.N + P::TN - 1) / P::TN);
+    const int n = tiles <= INT32_MAX ? tail_split_tiles((int)tiles, num_sms() / 2, (int)((d.K + P::BK - 1) / P::BK)) : 0;
+    if (n > 0) {
+      L.split = off;
+      L.split_bytes = split_region_bytes(n, 2, P::ACC);
+      off += L.split_bytes;
+    }
   }
   L.total = off;
   return L;
@@ -1409,23 +1533,32 @@ cudaError_t check_register_split(Kern* kernel) {
   return cudaSuccess;
 }
 
-// Which leaves of a single instance run on CTA pairs (256 x 256 tiles,
-// cta_group::2) rather than on single CTAs (128 x 256 tiles). Measured at
-// M = N = K = 8192 and 16384: pairs make plain BF16 (one accumulation per
-// tile) 5-10% faster; BF16x3 on pairs with 128-byte slab rows is 4% faster
-// than on single CTAs with 64-byte rows (1.90 vs 1.98 ms at 8192; with
-// 64-byte rows on pairs, or 128-byte rows in two stages on single CTAs, it
-// is not faster); FP8, which hands a tensor-memory buffer between the MMA
-// and epilogue warps every 128 K, runs 3% slower on pairs (2.2x slower
-// when the peer released buffers with a cluster-scope release). So BF16
-// and BF16x3 run on pairs, FP8 on single CTAs.
-constexpr bool pair_for_mode(int mode) { return mode == 1 || mode == 3; }
-
 // The single-instance leaf, persistent: PAIR runs clusters of 2, one cluster
 // per 256 x 256 tile at a time, as many clusters as fit on the GPU at once;
 // otherwise one CTA per SM. *grid_ctas returns the CTAs launched.
+// The tail split of a launch over `units` units: kept when this variant has
+// it, the tiles, units and K call for it and split_cap bytes hold its
+// region (its counters zeroed on the stream here), else turned off.
 template <int MODE, int EPI, bool PAIR>
-cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, int tiles, cudaStream_t s, int* grid_ctas) {
+cudaError_t tail_setup(TcParams& prm, int tiles, int units, size_t split_cap, int split_as, cudaStream_t s) {
+  using C_ = Cfg<MODE, PAIR>;
+  constexpr int RANKS = PAIR ? 2 : 1;
+  const bool variant = tail_split_variant(MODE, EPI, false) &&
+                       (split_as < 0 || tail_split_variant(MODE, split_as, false));
+  const int n = (variant && prm.split_ws)
+                    ? tail_split_tiles(tiles, units, (prm.K + C_::BK - 1) / C_::BK)
+                    : 0;
+  if (n == 0 || split_region_bytes(n, RANKS, C_::ACC) > split_cap) {
+    prm.split_ws = nullptr;
+    return cudaSuccess;
+  }
+  return cudaMemsetAsync(reinterpret_cast<uint8_t*>(prm.split_ws) + split_sums_bytes(n, RANKS, C_::ACC), 0,
+                         (size_t)n * RANKS * EPI_WARPS * sizeof(int), s);
+}
+
+template <int MODE, int EPI, bool PAIR>
+cudaError_t launch_leaf(const CUtensorMap* maps, TcParams prm, int tiles, size_t split_cap, int split_as,
+                        cudaStream_t s, int* grid_ctas, const LaunchHooks* hooks) {
   using C_ = Cfg<MODE, PAIR>;
   auto kernel = sgemm_tc<MODE, EPI, false, PAIR>;
   if constexpr (!PAIR) {
@@ -1438,9 +1571,14 @@ cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, int tiles,
     }
     const int grid = std::max(1, std::min(tiles, num_sms()));
     *grid_ctas = grid;
+    cudaError_t e = tail_setup<MODE, EPI, PAIR>(prm, tiles, grid, split_cap, split_as, s);
+    if (e != cudaSuccess) return e;
+    hook_begin(hooks, s);
     kernel<<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm,
                                                   GroupParams{nullptr, nullptr, 0});
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    hook_end(hooks, s);
+    return e;
   }
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1468,14 +1606,18 @@ cudaError_t launch_leaf(const CUtensorMap* maps, const TcParams& prm, int tiles,
   const int clusters = std::max(1, std::min(tiles, max_clusters));
   cfg.gridDim = dim3(2 * clusters);
   *grid_ctas = 2 * clusters;
-  return cudaLaunchKernelEx(&cfg, kernel, maps[0], maps[1], maps[2], maps[3], prm,
-                            GroupParams{nullptr, nullptr, 0});
+  cudaError_t e = tail_setup<MODE, EPI, PAIR>(prm, tiles, clusters, split_cap, split_as, s);
+  if (e != cudaSuccess) return e;
+  hook_begin(hooks, s);
+  e = cudaLaunchKernelEx(&cfg, kernel, maps[0], maps[1], maps[2], maps[3], prm, GroupParams{nullptr, nullptr, 0});
+  hook_end(hooks, s);
+  return e;
 }
 
 template <int MODE>
-cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStream_t s, KernelReport* rep,
-                   std::string* err, const LaunchHooks* hooks, const Epilogue& epi, const OperandPlanes& pa,
-                   const OperandPlanes& pb) {
+cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceStatus& st, cudaStream_t s,
+                   KernelReport* rep, std::string* err, const LaunchHooks* hooks, const Epilogue& epi,
+                   const OperandPlanes& pa, const OperandPlanes& pb) {
   constexpr bool PAIR = pair_for_mode(MODE);
   constexpr int TM = PAIR ? 2 * BM : BM;
   using C_ = Cfg<MODE, PAIR>;
@@ -1545,14 +1687,14 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
       maps[3] = maps[2];
     }
   }
-  TcParams prm{M, N, K, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, st.dev, epi.aux, epi.ldaux,
-               nullptr, nullptr, 0, nullptr, 0};
+  TcParams prm{M, N, K, 0, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, 0, st.dev, epi.aux, epi.ldaux,
+               nullptr, nullptr, nullptr, nullptr};
   if (epi.rows && !C_::FP8) {
     // the planes of C with rows of C as operand rows: rows = M, row length N
     const OperandLayout F = operand_layout(M, N, MODE);
     uint8_t* f = static_cast<uint8_t*>(epi.rows);
     prm.row_hi = reinterpret_cast<__nv_bfloat16*>(f + F.hi);
-    prm.row_kp = (N + 7) / 8 * 8;
+    prm.row_kp = (int)((N + 7) / 8 * 8);
     if (MODE == 3 && F.lo != align256((size_t)M * prm.row_kp * 2)) return cudaErrorInvalidValue;
   }
   if (epi.fwd && !C_::FP8) {
@@ -1561,15 +1703,20 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, const DeviceStatus& st, cudaStr
     uint8_t* f = static_cast<uint8_t*>(epi.fwd);
     prm.fwd_hi = reinterpret_cast<__nv_bfloat16*>(f + F.hi);
     prm.fwd_lo = reinterpret_cast<__nv_bfloat16*>(f + F.lo);
-    prm.fwd_kp = (M + 7) / 8 * 8;
+    prm.fwd_kp = (int)((M + 7) / 8 * 8);
   }
   const int tiles = ((M + TM - 1) / TM) * ((N + C_::TN - 1) / C_::TN);
+  // the tail split's region, when the workspace holds it (the launch decides)
+  size_t split_cap = 0;
+  if (L.split_bytes && ws_bytes >= L.split + L.split_bytes) {
+    prm.split_ws = reinterpret_cast<float*>(w + L.split);
+    split_cap = L.split_bytes;
+  }
   int grid_ctas = 0;
-  hook_begin(hooks, s);
-  if (epi.kind == 1) e = launch_leaf<MODE, 1, PAIR>(maps, prm, tiles, s, &grid_ctas);
-  else if (epi.kind == 2) e = launch_leaf<MODE, 2, PAIR>(maps, prm, tiles, s, &grid_ctas);
-  else e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, s, &grid_ctas);
-  hook_end(hooks, s);
+  const int sa_ = epi.split_as;
+  if (epi.kind == 1) e = launch_leaf<MODE, 1, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
+  else if (epi.kind == 2) e = launch_leaf<MODE, 2, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
+  else e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
   if (e != cudaSuccess) return e;
   kernels += 1;
   if (rep) {
@@ -1900,13 +2047,14 @@ cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, c
     *err = "M, N and K must each fit in 30 bits for the tensor-core tiers";
     return cudaErrorInvalidValue;
   }
-  if (ws_bytes < tc_workspace_bytes(d, tier) || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) {
+  // the planes are required; the tail split's region is used when present
+  if (ws_bytes < ws_layout(d, mode_of_tier(tier)).planes || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) {
     *err = "workspace too small or not 256-byte aligned";
     return cudaErrorInvalidValue;
   }
-  if (tier == 2) return run_tc<3>(d, ws, st, s, rep, err, hooks, epi, pa, pb);
-  if (tier == 4) return run_tc<8>(d, ws, st, s, rep, err, hooks, epi, pa, pb);
-  return run_tc<1>(d, ws, st, s, rep, err, hooks, epi, pa, pb);
+  if (tier == 2) return run_tc<3>(d, ws, ws_bytes, st, s, rep, err, hooks, epi, pa, pb);
+  if (tier == 4) return run_tc<8>(d, ws, ws_bytes, st, s, rep, err, hooks, epi, pa, pb);
+  return run_tc<1>(d, ws, ws_bytes, st, s, rep, err, hooks, epi, pa, pb);
 }
 
 OperandLayout tc_operand_layout(int tier, int64_t rows, int64_t K) {
