@@ -458,34 +458,37 @@ __device__ __forceinline__ void split_pair(float x, __nv_bfloat16& h, __nv_bfloa
   l = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// X "m-major": element (r, k) at X[r + k*ld] (rows contiguous). One 64 x 64
+// X "m-major": element (r, k) at X[r + k*ld] (rows contiguous). One TR x TK
 // tile (rows r0.., K k0..) per CTA of 256 threads, transposed through
-// shared memory so both the FP32 read and the BF16 writes are coalesced.
-template <int NPROD>
+// shared memory so both the FP32 read (TR rows of a column in a row) and
+// the BF16 writes (TK elements of a plane row in a row) are coalesced.
+template <int NPROD, int TR = 64, int TK = 64>
 __device__ __forceinline__ void split_tile_m(const float* __restrict__ X, int64_t ld, int rows, int K, int Kp,
                                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                              int64_t r0, int64_t k0) {
-  __shared__ float t[64][65];
+  static_assert(TR % 32 == 0 && TK % 8 == 0 && (TR * TK) % 2048 == 0, "tile of whole warps and 8-K groups");
+  constexpr int LOADS = TR * TK / 256, GROUPS = TR * TK / 8 / 256;
+  __shared__ float t[TK][TR + 1];
   const int tid = threadIdx.x;
-  // all 16 loads of a thread in flight before the first shared-memory store
-  float v[16];
+  // all loads of a thread in flight before the first shared-memory store
+  float v[LOADS];
 #pragma unroll
-  for (int it = 0; it < 16; ++it) {
+  for (int it = 0; it < LOADS; ++it) {
     const int e = tid + it * 256;
-    const int kk = e >> 6, rr = e & 63;
+    const int kk = e / TR, rr = e % TR;
     const int64_t gr = r0 + rr, gk = k0 + kk;
     v[it] = (gr < rows && gk < K) ? __ldcs(X + gr + gk * ld) : 0.f;
   }
 #pragma unroll
-  for (int it = 0; it < 16; ++it) {
+  for (int it = 0; it < LOADS; ++it) {
     const int e = tid + it * 256;
-    t[e >> 6][e & 63] = v[it];
+    t[e / TR][e % TR] = v[it];
   }
   __syncthreads();
 #pragma unroll
-  for (int it = 0; it < 2; ++it) {
+  for (int it = 0; it < GROUPS; ++it) {
     int e = tid + it * 256;
-    int rr = e >> 3, kc = (e & 7) * 8;
+    int rr = e / (TK / 8), kc = (e % (TK / 8)) * 8;
     int64_t gr = r0 + rr, gk = k0 + kc;
     if (gr >= rows || gk >= Kp) continue;
     __align__(16) __nv_bfloat16 h[8];
@@ -527,11 +530,19 @@ __device__ __forceinline__ void split_tile_k(const float* __restrict__ X, int64_
   }
 }
 
+// The tile of the single-operand split (the batch's pre-pass keeps 64 x 64).
+// Long reads along the contiguous rows pay more than long plane-row writes
+// (the K-adjacent tile's CTA runs soon after and completes the 32-byte
+// sectors in L2): at M = N = K = 8192 the two splits of a step took 210 us
+// with 64 x 64 tiles, 220-232 us with 128 x 64, 64 x 128 or 512 x 16,
+// 208-213 us with 256 x 16 or 128 x 32, and 197-202 us with 256 x 32.
+constexpr int SPLIT_TR = 256, SPLIT_TK = 32;
 template <int NPROD>
 __global__ void __launch_bounds__(256) split_mmajor(const float* __restrict__ X, int64_t ld, int rows, int K,
                                                     int Kp, __nv_bfloat16* __restrict__ hi,
                                                     __nv_bfloat16* __restrict__ lo) {
-  split_tile_m<NPROD>(X, ld, rows, K, Kp, hi, lo, (int64_t)blockIdx.x * 64, (int64_t)blockIdx.y * 64);
+  split_tile_m<NPROD, SPLIT_TR, SPLIT_TK>(X, ld, rows, K, Kp, hi, lo, (int64_t)blockIdx.x * SPLIT_TR,
+                                          (int64_t)blockIdx.y * SPLIT_TK);
 }
 
 // One operand of a batch and its planes; one 64 x 64 tile of one operand.
@@ -1494,7 +1505,7 @@ cudaError_t launch_split(const float* X, int64_t ld, bool mmajor, int rows, int 
                          __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
   if (rows == 0 || K == 0) return cudaSuccess;
   if (mmajor) {
-    dim3 grid((rows + 63) / 64, (Kp + 63) / 64);
+    dim3 grid((rows + SPLIT_TR - 1) / SPLIT_TR, (Kp + SPLIT_TK - 1) / SPLIT_TK);
     split_mmajor<NPROD><<<grid, 256, 0, s>>>(X, ld, rows, K, Kp, hi, lo);
   } else {
     int64_t tasks = (int64_t)rows * (Kp / 8);
