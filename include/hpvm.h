@@ -308,8 +308,10 @@ HPVM_API int hpvm_untrack_mem(hpvm_ctx* ctx, void* p);
 
 /* ---- workspace ----------------------------------------------------------
  * Device scratch the tensor-core tiers use: the operand planes of the
- * largest stage and, when stages forward planes to the next stage's B, two
- * regions for those. Bytes a launch of `root` with `args` needs: */
+ * largest stage (for a BF16 or BF16x3 stage whose last round of pair tiles
+ * splits in K halves, followed by their partial sums and arrival counters)
+ * and, when stages forward planes to the next stage's B, two regions for
+ * those. Bytes a launch of `root` with `args` needs: */
 HPVM_API int hpvm_workspace_size(hpvm_ctx* ctx, hpvm_node* root, const void* args,
                         size_t args_size, size_t* out);
 /* Use caller-owned device memory as workspace (NULL/0: the runtime
