@@ -2149,7 +2149,9 @@ extern "C" int hpvm_sgemm_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, float 
   d.beta = beta;
   d.transA = transA != 0;
   d.transB = transB != 0;
-  const size_t need = tc_workspace_bytes(d, 2);
+  // the planes must fit; the tail split runs when the rest of the array
+  // also holds its partial sums, else the leaf runs whole tiles only
+  const size_t need = ws_layout(d, 3).planes;
   if (need > kNoAllocScratchBytes || M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2) {
     char buf[200];
     snprintf(buf, sizeof buf,

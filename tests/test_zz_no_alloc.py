@@ -70,3 +70,24 @@ def test_noalloc_refuses_problems_beyond_its_scratch(cuda_device):
                                     torch.cuda.current_stream().cuda_stream)
     assert e.value.code == H.HPVM_ERR_SHAPE
     assert "scratch" in str(e.value)
+
+
+@pytest.mark.parametrize("M,N,K", [(2560, 2304, 520), (2560, 2560, 3000)])
+def test_noalloc_with_a_split_tail(cuda_device, M, N, K):
+    # Shapes whose last round of pair tiles splits in K halves on a 152-SM
+    # GB300 (90 and 100 pair tiles for 76 pairs). In the first the array
+    # also holds the split's partial sums; in the second the planes alone
+    # take 61 MB of the 64 MiB, so the call is accepted (the planes fit) and
+    # runs whole tiles. Both agree with the regular entry point.
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dfg = SgemmDFG(0)
+    try:
+        p = W.sgemm_problem(M, N, K, seed=M + K, alpha=1.25, beta=-0.5)
+        A, B, C0 = (t.cuda() for t in (p.A, p.B, p.C))
+        want = _regular(dfg, p, A, B, C0.clone())
+        got = _noalloc(p, A, B, C0.clone(), status)
+        assert int(status.item()) == 0
+        assert np.isfinite(got).all()
+        assert O.normwise_rel_err(got, want) <= TOL
+    finally:
+        dfg.close()
