@@ -299,8 +299,10 @@ HPVM_API int hpvm_graph_info(hpvm_graph* graph, hpvm_launch_info* out);
  * latest copy is the host's. A launch copies it to a device copy the
  * runtime owns when the copy there is stale and the leaf reads it (A, B;
  * C unless beta == 0), and marks C's latest copy as the device's.
- * request_mem: make the host copy of [p, p+bytes) current (waits for the
- * context's work, then copies device -> host if needed).
+ * request_mem: make the host copy of [p, p+bytes) current: waits for the
+ * launch that last wrote the region (for the whole device when that launch
+ * was captured into a CUDA graph), then copies device -> host if needed.
+ * Launches on other streams, or of other contexts, keep running meanwhile.
  * untrack_mem: forget the region and free its device copy. */
 HPVM_API int hpvm_track_mem(hpvm_ctx* ctx, void* p, int64_t bytes);
 HPVM_API int hpvm_request_mem(hpvm_ctx* ctx, void* p, int64_t bytes);

@@ -142,6 +142,10 @@ struct TrackEntry {
   int64_t bytes = 0;
   void* dev = nullptr;
   bool host_valid = true, dev_valid = false;
+  // recorded after the last launch that wrote the device copy (unset when
+  // that launch was captured into a CUDA graph)
+  cudaEvent_t written = nullptr;
+  bool written_set = false;
 };
 
 // one pushed item of a streaming graph
@@ -211,6 +215,7 @@ struct hpvm_ctx {
   // streaming graph validated at launch is not validated again per push
   // unless this moved
   uint64_t structure = 0;
+  cudaStream_t copy_stream = nullptr;  // request_mem's device -> host copies
 };
 
 // ---------------------------------------------------------------------------
@@ -775,6 +780,24 @@ int map_pointer(hpvm_ctx* ctx, const void* p, bool read, cudaStream_t s, const c
   return HPVM_OK;
 }
 
+// Records on s that the launch enqueued so far wrote t's device copy, so
+// that request_mem waits for that launch alone. Inside a stream capture no
+// event is recorded and request_mem falls back to waiting for the device.
+int mark_written(TrackEntry* t, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    t->written_set = false;
+    return HPVM_OK;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!t->written) e = cudaEventCreateWithFlags(&t->written, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(t->written, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recording the write of a tracked region");
+  t->written_set = true;
+  return HPVM_OK;
+}
+
 int grow_buffer(void** buf, size_t* have, size_t need, cudaStream_t sync_on) {
   if (need == 0 || (*buf && *have >= need)) return HPVM_OK;
   if (*buf) {
@@ -1028,6 +1051,7 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
     if (tC) {
       tC->dev_valid = true;
       tC->host_valid = false;
+      if ((rc = mark_written(tC, s)) != HPVM_OK) return rc;
     }
     if (first) {  // the first stage describes the launch
       inf->tier = tier;
@@ -1132,8 +1156,11 @@ int hpvm_cleanup(hpvm_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto* g : ctx->graphs) free_graph(g);
-    for (auto& t : ctx->tracked)
+    for (auto& t : ctx->tracked) {
       if (t.dev) cudaFree(t.dev);
+      if (t.written) cudaEventDestroy(t.written);
+    }
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
     if (ctx->status.host) cudaFreeHost(ctx->status.host);
     for (auto& pr : ctx->timed) {
@@ -1538,9 +1565,14 @@ int hpvm_request_mem(hpvm_ctx* ctx, void* p, int64_t bytes) {
   if (t->host_valid) return ok();
   if (ctx->device < 0) return fail(HPVM_ERR_NO_DEVICE, "host-only context");
   cudaSetDevice(ctx->device);
-  cudaError_t e = cudaDeviceSynchronize();
+  // wait for the launch that last wrote the region (other streams and
+  // contexts keep running), then copy on the context's own stream
+  cudaError_t e = t->written_set ? cudaEventSynchronize(t->written) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "waiting before device->host copy");
-  e = cudaMemcpy(t->host, t->dev, (size_t)t->bytes, cudaMemcpyDeviceToHost);
+  if (!ctx->copy_stream && (e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "creating the copy stream");
+  e = cudaMemcpyAsync(t->host, t->dev, (size_t)t->bytes, cudaMemcpyDeviceToHost, ctx->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->copy_stream);
   if (e != cudaSuccess) return cuda_fail(e, "device->host copy");
   t->host_valid = true;
   return ok();
@@ -1555,6 +1587,7 @@ int hpvm_untrack_mem(hpvm_ctx* ctx, void* p) {
         cudaDeviceSynchronize();
         cudaFree(ctx->tracked[i].dev);
       }
+      if (ctx->tracked[i].written) cudaEventDestroy(ctx->tracked[i].written);
       ctx->tracked.erase(ctx->tracked.begin() + (long)i);
       return ok();
     }
