@@ -145,6 +145,50 @@ def test_memory_tracker_host_buffers(cuda_device, tier):
         H.hpvm_cleanup(ctx)
 
 
+def test_memory_tracker_two_contexts_alternating(cuda_device):
+    # the double-buffered loop of the end-to-end benchmark: two contexts,
+    # each with its own pinned A, B, C and stream; step i+1 is launched
+    # before step i's C is read back (hpvm_request_mem waits for the launch
+    # that wrote C, not for the device). Every step's C against the oracle.
+    ctxs, sets = [], []
+    try:
+        for j in range(2):
+            ctx = H.hpvm_init(0)
+            ctxs.append(ctx)
+            nodes = build_sgemm_graph(ctx)
+            st = torch.cuda.Stream()
+            probs = [W.sgemm_problem(300, 260, 140, seed=40 + 2 * i + j, alpha=1.5, beta=0.5) for i in range(2)]
+            sets.append((ctx, nodes, st, probs))
+        pending = []
+        for i in range(2):
+            for j, (ctx, nodes, st, probs) in enumerate(sets):
+                p = probs[i]
+                A, B, C = (t.clone().pin_memory() for t in (p.A, p.B, p.C))
+                for t in (A, B, C):
+                    H.hpvm_track_mem(ctx, t.data_ptr(), t.numel() * 4)
+                a = make_args(p.M, p.N, p.K, A.data_ptr(), A.numel() * 4, p.lda, B.data_ptr(), B.numel() * 4,
+                              p.ldb, C.data_ptr(), C.numel() * 4, p.ldc, p.alpha, p.beta, p.transA, p.transB,
+                              H.HPVM_TIER_BF16X3)
+                g = H.hpvm_launch(ctx, nodes["root"], a, False, st.cuda_stream)
+                pending.append((ctx, g, p, (A, B, C)))
+                if len(pending) == 2:  # read back the previous step while this one runs
+                    pctx, pg, pp, (pA, pB, pC) = pending.pop(0)
+                    H.hpvm_wait(pg, 60000)
+                    H.hpvm_request_mem(pctx, pC.data_ptr(), pC.numel() * 4)
+                    got = W.col_major(pC, pp.M, pp.N, pp.ldc).double().numpy()
+                    assert O.normwise_rel_err(got, O.sgemm_f64(pp)) <= TOL[H.HPVM_TIER_BF16X3]
+                    for t in (pA, pB, pC):
+                        H.hpvm_untrack_mem(pctx, t.data_ptr())
+        for pctx, pg, pp, (pA, pB, pC) in pending:
+            H.hpvm_wait(pg, 60000)
+            H.hpvm_request_mem(pctx, pC.data_ptr(), pC.numel() * 4)
+            got = W.col_major(pC, pp.M, pp.N, pp.ldc).double().numpy()
+            assert O.normwise_rel_err(got, O.sgemm_f64(pp)) <= TOL[H.HPVM_TIER_BF16X3]
+    finally:
+        for ctx in ctxs:
+            H.hpvm_cleanup(ctx)
+
+
 def test_untracked_host_pointer_rejected(cuda_device):
     p = W.sgemm_problem(16, 16, 16, seed=1)
     ctx = H.hpvm_init(0)
