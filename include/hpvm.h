@@ -131,6 +131,17 @@ extern "C" {
 #define HPVM_LAUNCH_CACHE_B 16
 #define HPVM_LAUNCH_REUSE_B 32
 #define HPVM_LAUNCH_CACHE_C 64
+/* PLANES_ONLY (tensor tiers, fusion on, beta = 0): the caller reads this
+ * stage's result only through the planes the launch writes of it: the B
+ * planes a streaming edge forwards to the next stage, and with CACHE_C the
+ * cached row planes. The FP32 C is then not stored (it keeps its old
+ * contents), saving its write. Ignored, and C stored, where those planes are
+ * not all written (no forwarding and no CACHE_C entry, a CACHE_C entry the
+ * cache had no room for, beta != 0, an unmerged stage, FP8, or C in a
+ * tracked host region). A later launch that converts C instead of reusing
+ * the planes (hpvm_drop_planes in between, or no REUSE flag) reads the old
+ * contents. */
+#define HPVM_LAUNCH_PLANES_ONLY 128
 
 typedef struct hpvm_ctx hpvm_ctx;
 typedef struct hpvm_node hpvm_node;

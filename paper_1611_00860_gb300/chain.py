@@ -202,18 +202,20 @@ class ChainEngine:
             H.hpvm_wait(g, timeout_ms)
 
     def chain_records(self, X: torch.Tensor, Ws, outs, plane_flags: int = 0, x_flags: int = 0,
-                      out_flags: int = 0):
+                      out_flags: int = 0, mid_flags: int = 0):
         """Records of a chain graph of len(Ws) stages: stage l computes
         outs[l] = act(in_l) W_l. plane_flags (HPVM_LAUNCH_CACHE_A / REUSE_A)
         applies to the weights, the stages' A operands; x_flags
         (HPVM_LAUNCH_CACHE_B / REUSE_B) to X, the first stage's B (later
         stages take their B planes from the previous stage's epilogue);
-        out_flags (HPVM_LAUNCH_CACHE_C) to every stage's result."""
+        out_flags (HPVM_LAUNCH_CACHE_C) to every stage's result, mid_flags
+        (HPVM_LAUNCH_PLANES_ONLY) to every stage's but the last."""
         arr = (H.RootArgs * len(Ws))()
         for l in range(len(Ws)):
             src = X if l == 0 else outs[l - 1]
             arr[l] = _rm_product_args(outs[l], src, Ws[l], self.tier,
-                                      self.flags | plane_flags | out_flags | (x_flags if l == 0 else 0))
+                                      self.flags | plane_flags | out_flags | (x_flags if l == 0 else 0) |
+                                      (mid_flags if l < len(Ws) - 1 else 0))
             if l > 0:  # B arrives over the streaming edge
                 arr[l].B = None
                 arr[l].bytesB = 0
@@ -225,8 +227,12 @@ class ChainEngine:
         H_1..H_{L-1} (the tanh outputs, the chain's intermediate buffers)."""
         outs = [torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws]
         # the weights' and X's planes are made afresh (they may have changed
-        # since the last call) and kept for the recomputation in backward
-        self._run(self.chain, self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_CACHE_A, H.HPVM_LAUNCH_CACHE_B))
+        # since the last call) and kept for the recomputation in backward;
+        # without keep the intermediate results are read only through the
+        # planes forwarded to the next stage, so they are not stored
+        mid = 0 if keep else H.HPVM_LAUNCH_PLANES_ONLY
+        self._run(self.chain, self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_CACHE_A, H.HPVM_LAUNCH_CACHE_B,
+                                                 mid_flags=mid))
         return (outs[-1], outs[:-1]) if keep else outs[-1]
 
     def recompute(self, X: torch.Tensor, Ws):
@@ -255,7 +261,9 @@ class ChainEngine:
         streamed into stage j+1's B (so its planes come from stage j's
         epilogue). The weight adjoints dW_l^T = dZ_l^T H_l follow, one launch
         each (op(B) = B^T), reading the planes of dZ_l (l < L-1) and of H_l
-        (l > 0) that the adjoint and recomputing stages' epilogues cached."""
+        (l > 0) that the adjoint and recomputing stages' epilogues cached;
+        dZ_l is then read only through planes and its FP32 values are not
+        stored (HPVM_LAUNCH_PLANES_ONLY)."""
         Hs = self.recompute(X, Ws)
         L = self.layers
         rows = X.shape[0]
@@ -271,7 +279,7 @@ class ChainEngine:
             a = make_args(w_in, rows, w_out, W.data_ptr(), W.numel() * 4, w_out,
                           G.data_ptr() if j == 0 else None, G.numel() * 4 if j == 0 else 0, w_out,
                           dHs[l].data_ptr(), dHs[l].numel() * 4, w_in, 1.0, 0.0, True, False, self.tier,
-                          flags=self.flags | (cc if l > 0 else 0))
+                          flags=self.flags | (cc | (H.HPVM_LAUNCH_PLANES_ONLY if cc else 0) if l > 0 else 0))
             if l > 0:
                 a.aux, a.bytesAux, a.ldaux = Hs[l].data_ptr(), Hs[l].numel() * 4, w_in
             recs[j] = a
@@ -298,23 +306,24 @@ class ChainEngine:
         """Push every item (row-major rows x w) through the chain launched as a
         streaming graph and pop the outputs in order (hpvm_push / hpvm_pop)."""
         outs_all = [[torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws] for X in items]
-        rec0 = self.chain_records(items[0], Ws, outs_all[0])
+        mid = H.HPVM_LAUNCH_PLANES_ONLY  # only the last stage's results are returned
+        rec0 = self.chain_records(items[0], Ws, outs_all[0], mid_flags=mid)
         # items of one shape differ only in X and the stage results: later
         # items' records are the first's with those pointers replaced
-        reuse = self.chain_records(items[0], Ws, outs_all[0], H.HPVM_LAUNCH_REUSE_A)
+        reuse = self.chain_records(items[0], Ws, outs_all[0], H.HPVM_LAUNCH_REUSE_A, mid_flags=mid)
         g = H.hpvm_launch(self.ctx, self.chain, rec0, True, self._stream())
         try:
             for i, (X, outs) in enumerate(zip(items, outs_all)):
                 # the weights are the same for every item: converted once
                 if i == 0:
-                    rec = self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_CACHE_A)
+                    rec = self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_CACHE_A, mid_flags=mid)
                 elif X.shape == items[0].shape:
                     rec = type(reuse).from_buffer_copy(reuse)
                     rec[0].B = X.data_ptr()
                     for l, o in enumerate(outs):
                         rec[l].C = o.data_ptr()
                 else:
-                    rec = self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_REUSE_A)
+                    rec = self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_REUSE_A, mid_flags=mid)
                 H.hpvm_push(g, rec)
             popped = []
             for _ in items:

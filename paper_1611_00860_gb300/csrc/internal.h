@@ -76,6 +76,7 @@ struct Epilogue {
   void* fwd = nullptr;
   void* rows = nullptr;
   int split_as = -1;
+  bool planes_only = false;  // store the planes above only, not C itself
 };
 // Standalone elementwise kernel on the M x N column-major C (fp32_leaf.cu).
 cudaError_t launch_elementwise(const SgemmDesc& d, const Epilogue& e, cudaStream_t s);

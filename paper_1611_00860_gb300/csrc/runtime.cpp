@@ -1018,6 +1018,14 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
           invalidate_planes(ctx, S.d.C, S.d.ldc, S.d.M, S.d.N, 1);
         }
       }
+      // HPVM_LAUNCH_PLANES_ONLY: C is read only through the planes this
+      // stage writes, so the FP32 C is not stored. Honoured only where those
+      // planes exist for every reader the flags name (forwarded to the next
+      // stage, and the cache entry when CACHE_C asked for one), with beta = 0
+      // and C not a tracked host region; otherwise C is stored as usual.
+      if ((flags & HPVM_LAUNCH_PLANES_ONLY) && fuse && S.d.beta == 0.f && !tC && (S.epi.fwd || S.epi.rows) &&
+          (!(flags & HPVM_LAUNCH_CACHE_C) || S.epi.rows))
+        S.epi.planes_only = true;
       hpvm::Epilogue none;
       none.split_as = S.epi.kind;  // unmerged: split the tail as the merged leaf would
       cudaError_t e;

@@ -159,6 +159,8 @@ struct TcParams {
   // round's tiles, then one arrival counter per tile, CTA and epilogue warp
   // (zeroed before the launch).
   float* split_ws;
+  // 1: C itself is not stored (only the planes of it this launch writes)
+  int planes_only;
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -1280,7 +1282,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 float x = (v.beta == 0.f) ? v.alpha * acc[u0 + u] : fmaf(v.alpha, acc[u0 + u], v.beta * old[u]);
                 if (EPI == 1) x = tanhf(x);
                 if (EPI == 2) x = x * (1.f - hx[u] * hx[u]);
-                __stcs(cp + (int64_t)(u0 + u) * v.ldc, x);
+                if (GROUPED || C_::FP8 || !p.planes_only) __stcs(cp + (int64_t)(u0 + u) * v.ldc, x);
                 if (!GROUPED && !C_::FP8 && p.fwd_hi) {
                   // the next stage's operand planes of this output (a warp
                   // writes 32 consecutive K elements of one plane row)
@@ -1308,7 +1310,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (EPI == 1) x = tanhf(x);
                     if (EPI == 2) x = x * (1.f - hx[u] * hx[u]);
                     x2[h] = x;
-                    __stcs(cp + (int64_t)(u0 + u) * v.ldc, x);
+                    if (!p.planes_only) __stcs(cp + (int64_t)(u0 + u) * v.ldc, x);  // (ROWS variants only)
                     if (!GROUPED && !C_::FP8 && p.fwd_hi) {
                       // the next stage's operand planes of this output (a warp
                       // writes 32 consecutive K elements of one plane row)
@@ -1699,7 +1701,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
     }
   }
   TcParams prm{M, N, K, 0, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, 0, st.dev, epi.aux, epi.ldaux,
-               nullptr, nullptr, nullptr, nullptr};
+               nullptr, nullptr, nullptr, nullptr, 0};
   if (epi.rows && !C_::FP8) {
     // the planes of C with rows of C as operand rows: rows = M, row length N
     const OperandLayout F = operand_layout(M, N, MODE);
@@ -1708,6 +1710,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
     prm.row_kp = (int)((N + 7) / 8 * 8);
     if (MODE == 3 && F.lo != align256((size_t)M * prm.row_kp * 2)) return cudaErrorInvalidValue;
   }
+  prm.planes_only = (epi.planes_only && !C_::FP8 && (epi.fwd || epi.rows)) ? 1 : 0;
   if (epi.fwd && !C_::FP8) {
     // the planes of C as op(B) of a leaf with K = M: rows = N, row length M
     const OperandLayout F = operand_layout(N, M, MODE);

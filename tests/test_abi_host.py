@@ -341,7 +341,7 @@ def test_plane_cache_on_a_host_only_context(ctx):
     H.hpvm_drop_planes(ctx)
     assert H.hpvm_plane_cache_bytes(ctx) == 0
     flags = (H.HPVM_LAUNCH_CACHE_A, H.HPVM_LAUNCH_REUSE_A, H.HPVM_LAUNCH_CACHE_B, H.HPVM_LAUNCH_REUSE_B,
-             H.HPVM_LAUNCH_CACHE_C)
-    assert len(set(flags)) == 5 and all(f & (H.HPVM_LAUNCH_NO_EVENT | H.HPVM_LAUNCH_NO_FUSION) == 0 for f in flags)
+             H.HPVM_LAUNCH_CACHE_C, H.HPVM_LAUNCH_PLANES_ONLY)
+    assert len(set(flags)) == 6 and all(f & (H.HPVM_LAUNCH_NO_EVENT | H.HPVM_LAUNCH_NO_FUSION) == 0 for f in flags)
     with pytest.raises(H.HpvmError):
         H.hpvm_plane_cache_bytes(None)

@@ -173,6 +173,62 @@ def test_cache_c_on_a_stage_without_merged_leaf_drops_the_entry(cuda_device, tie
 
 
 @pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
+def test_planes_only_skips_the_intermediate_results(cuda_device, tier):
+    # HPVM_LAUNCH_PLANES_ONLY on every stage but the last of one chain launch:
+    # the intermediate results are read only through the planes forwarded
+    # to the next stage, so their FP32 buffers keep their old contents (NaN
+    # here) while Y equals the launch that stores them, bit for bit.
+    layers, rows, w = 3, 300, 264
+    X, Ws, _ = _inputs(1, rows, w, layers, seed=17)
+    Xd, Wd = X[0].cuda(), [W.cuda() for W in Ws]
+    eng = ChainEngine(layers, tier=tier)
+    try:
+        got = []
+        for mid in (H.HPVM_LAUNCH_PLANES_ONLY, 0):
+            outs = [torch.full((rows, w), float("nan"), device="cuda") for _ in range(layers)]
+            eng._run(eng.chain, eng.chain_records(Xd, Wd, outs, mid_flags=mid))
+            eng._drain()
+            got.append([o.cpu() for o in outs])
+        planes_only, stored = got
+        assert torch.equal(planes_only[-1], stored[-1])
+        for l in range(layers - 1):
+            assert torch.isnan(planes_only[l]).all()
+            assert torch.isfinite(stored[l]).all()
+        # forward() without keep uses the flag: the same Y as with keep
+        assert torch.equal(eng.forward(Xd, Wd).cpu(), eng.forward(Xd, Wd, keep=True)[0].cpu())
+        eng._drain()
+    finally:
+        eng.close()
+
+
+@pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
+def test_planes_only_is_ignored_where_no_planes_are_written(cuda_device, tier):
+    # a single tanh stage writes no planes of its result (no forwarding, no
+    # CACHE_C), and beta != 0 reads C: in both cases C is stored as usual
+    eng = ChainEngine(1, tier=tier)
+    try:
+        g = torch.Generator().manual_seed(3)
+        Hm = torch.randn(200, 96, generator=g).cuda()
+        Wt = (torch.randn(96, 136, generator=g) / 10).cuda()
+        out = torch.full((200, 136), float("nan"), device="cuda")
+        eng._run(eng.stage_tanh, _rm_product_args(out, Hm, Wt, tier, H.HPVM_LAUNCH_PLANES_ONLY))
+        eng._drain()
+        ref = torch.tanh(Hm.double().cpu() @ Wt.double().cpu())
+        assert O.normwise_rel_err(out.cpu().double().numpy(), ref.numpy()) <= TOL[tier]
+        # beta != 0 with CACHE_C: the row planes are written, but C is read and stored
+        C0 = torch.randn(200, 136, generator=g).cuda()
+        out2 = C0.clone()
+        a = _rm_product_args(out2, Hm, Wt, tier, H.HPVM_LAUNCH_PLANES_ONLY | H.HPVM_LAUNCH_CACHE_C)
+        a.beta = 0.5
+        eng._run(eng.stage_tanh, a)
+        eng._drain()
+        ref2 = torch.tanh(Hm.double().cpu() @ Wt.double().cpu() + 0.5 * C0.double().cpu())
+        assert O.normwise_rel_err(out2.cpu().double().numpy(), ref2.numpy()) <= TOL[tier]
+    finally:
+        eng.close()
+
+
+@pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
 @pytest.mark.parametrize("items,rows,w,layers", [(3, 24, 16, 4), (2, 300, 256, 4), (1, 7, 5, 2)])
 def test_forward_and_streaming_match_oracle(cuda_device, tier, items, rows, w, layers):
     X, Ws, _ = _inputs(items, rows, w, layers, seed=rows + w)
