@@ -17,6 +17,11 @@ sgemm leaf are sgemm leaves with the roles reversed:
 and the adjoint of the tanh leaf is the TanhGradLeaf, dZ_{l-1} =
 dH_l * (1 - H_l^2), merged into the dH product's epilogue.
 
+Results that go on only as operand planes are not stored in FP32: the
+forward's intermediates (the backward recomputes them) and the adjoint
+results dZ_l, whose planes the next adjoint stage and the weight adjoints
+read (HPVM_LAUNCH_PLANES_ONLY with the forwarded and cached planes).
+
 Argument marshalling only: every product and elementwise leaf runs in the
 library's kernels through the C-ABI. PyTorch provides memory and streams.
 """

@@ -12,6 +12,10 @@
 //  * Launch and bounded wait; streaming graphs (Section 4.5) whose items are
 //    pushed and popped, pipelined over a ring of CUDA streams.
 //  * The memory tracker of Section 3.3.
+//  * The operand plane cache (no counterpart in the paper): the BF16 / E4M3
+//    planes of an operand kept across launches (CACHE_* / REUSE_* flags),
+//    filled by a conversion or, for a stage's result, by its epilogue
+//    (CACHE_C; with PLANES_ONLY the result is kept only as planes).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -25,10 +25,14 @@
 //   sgemm_tc<MODE, EPI, GROUPED, PAIR>: persistent; warp 0 issues TMA loads,
 //       warp 1 allocates tensor memory and issues the MMAs, warps 4..11
 //       read the accumulator (tcgen05.ld) into FP32 registers and write C
-//       (with a merged elementwise leaf, EPI). Every mbarrier wait is
-//       bounded; on expiry the kernel sets a bit in the status word, drains
-//       its own copies and MMAs (bounded again), frees tensor memory and
-//       returns.
+//       (with a merged elementwise leaf, EPI), and on request the BF16
+//       planes of C a later leaf reads (forwarded to the next stage of a
+//       multi-stage launch, or C's rows into the plane cache), with or
+//       without C itself. A last round of tiles that would leave most units
+//       idle runs in K halves whose partial sums meet in the workspace
+//       (tail split). Every mbarrier wait is bounded; on expiry the kernel
+//       sets a bit in the status word, drains its own copies and MMAs
+//       (bounded again), frees tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
