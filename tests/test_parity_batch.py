@@ -78,7 +78,10 @@ def test_batch_equals_one_launch_per_instance(cuda_device, small_batch):
             s.run_problem(p, H.HPVM_TIER_BF16X3, t)
         torch.cuda.synchronize()
         for p, (_, _, Cb), (_, _, Cs) in zip(probs, dev_b, dev_s):
-            # bit for bit, NaN slack of the leading dimension included
+            # bit for bit, NaN slack of the leading dimension included (these
+            # single launches have fewer pair tiles than the GPU has pairs, so
+            # none splits its last round in K halves, which would round
+            # differently from the batch's whole tiles)
             assert torch.equal(Cb.cpu().view(torch.int32), Cs.cpu().view(torch.int32))
     finally:
         b.close()
