@@ -253,6 +253,9 @@ __device__ __forceinline__ void tma_load_2d_pair(const CUtensorMap* map, uint32_
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1)
       : "memory");
 }
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
@@ -1274,6 +1277,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             const float* hp = p.aux + row + (int64_t)col0 * p.ldaux;
 #pragma unroll
             for (int u = 0; u < CGRP; ++u) hx[u] = (u0 + u < ncols) ? __ldcs(hp + (int64_t)(u0 + u) * p.ldaux) : 0.f;
+            // the next group's H into L1 while this group is computed and
+            // stored (no registers: held one group ahead, the loads spilled;
+            // not in the FP8 leaf, which spilled with the prefetches too)
+            if (!C_::FP8 && u0 + CGRP < ACC) {
+#pragma unroll
+              for (int u = 0; u < CGRP; ++u)
+                if (u0 + CGRP + u < ncols) prefetch_l1(hp + (int64_t)(u0 + CGRP + u) * p.ldaux);
+            }
           }
           // C, the forwarded planes and, for the tanh stages (EPI != 0),
           // C's row planes. The plain leaf keeps its own loop: ptxas spills
