@@ -303,6 +303,35 @@ def test_chain_graph_lowers_on_host(ctx):
     assert H.hpvm_workspace_size(ctx, g, a) > 0
 
 
+def test_workspace_of_a_tail_split(ctx):
+    # 10 x 8 = 80 pair tiles, more than the pairs of the GPU (or of the
+    # 148-SM default without one), with a short last round: K = 520 (9 slabs
+    # of 64) splits it, and the workspace holds, after the planes, per split
+    # tile 2 K halves x 2 CTAs x 8 epilogue warps x 128 x 32 FP32 partial
+    # sums (512 KiB) and then 2 x 8 counters per tile (aligned to 256 B).
+    # With 3 slabs (K = 192), or 2 x 2 tiles, nothing splits.
+    nodes = build_sgemm_graph(ctx)
+
+    def al(x):
+        return (x + 255) // 256 * 256
+
+    def ws(M, N, K, tier):
+        a = make_args(M, N, K, 0x1000, 4 * M * K, M, 0x2000, 4 * N * K, N, 0x3000, 4 * M * N, M,
+                      1.0, 0.0, False, True, tier)
+        kp = (K + 7) // 8 * 8
+        planes = (2 if tier == H.HPVM_TIER_BF16X3 else 1) * (al(M * kp * 2) + al(N * kp * 2))
+        return H.hpvm_workspace_size(ctx, nodes["root"], a) - planes
+
+    for tier in (H.HPVM_TIER_BF16X3, H.HPVM_TIER_BF16):
+        extra = ws(2560, 2048, 520, tier)
+        n = extra // (2 * 2 * 8 * 128 * 32 * 4)
+        assert n >= 1 and extra == n * 2 * 2 * 8 * 128 * 32 * 4 + al(n * 2 * 8 * 4)
+        assert ws(2560, 2048, 192, tier) == 0
+        assert ws(512, 400, 520, tier) == 0
+    # the FP32 tiers use no workspace
+    assert ws(2560, 2048, 520, H.HPVM_TIER_FP32) == -(al(2560 * 520 * 2) + al(2048 * 520 * 2))
+
+
 def test_chain_workspace_holds_forwarded_planes(ctx):
     # A 4-stage chain whose stages read the previous stage's result as B:
     # merged, each stage's epilogue writes the next stage's B planes into one
