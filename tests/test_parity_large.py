@@ -1,7 +1,10 @@
 """Parity at the large workload (M = N = K = 8192, the launch configuration
 the benchmark times), on sampled 256 x 256 output blocks that the FP64 oracle
-computes one by one: 16 seeded block positions plus the first and the last.
-Also the column-scaled variant (column p of op(A) scaled by 2^u, u ~ U[-20,20]).
+computes one by one: 16 seeded block positions plus the first and the last,
+and two more inside the last round of pair tiles (row tiles 27-31 of column
+tiles 24-31 in the grouped tile order), which the leaf runs in K halves on a
+152-SM GB300 (tail split). Also the column-scaled variant (column p of
+op(A) scaled by 2^u, u ~ U[-20,20]).
 """
 import numpy as np
 import pytest
@@ -28,7 +31,7 @@ def dfg(cuda_device):
 @pytest.fixture(scope="module", params=[False, True], ids=["normal", "colscale"])
 def problem(request, cuda_device):
     p = W.large_dfg_problem(N, colscale=request.param)
-    blocks = W.sample_blocks(p.M, p.N, bs=256, count=16)
+    blocks = W.sample_blocks(p.M, p.N, bs=256, count=16) + [(7424, 6400), (7168, 7936)]
     refs = [O.sgemm_block_f64(p, i0, j0, 256, 256) for (i0, j0) in blocks]
     dev = tuple(t.cuda() for t in (p.A, p.B, p.C))
     yield p, blocks, refs, dev
