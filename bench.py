@@ -13,8 +13,10 @@ x 2*M*N*K, over the kernel's own CUDA-event time, against the measured dense
 BF16 peak); the plain FP32 CUDA-core DFG on the same workload; the normwise
 error of both against the FP64 oracle on sampled blocks (computed in the
 CPU-baseline leg, which times that oracle); the end-to-end figure through
-the memory tracker with host buffers; SM clocks sampled during the timed
-region; the number of kernels launched.
+the memory tracker with pinned host buffers (every step copies its A, B, C
+in and its C out; two contexts alternate so one step's copies overlap the
+other's kernels, and the one-step-at-a-time time is reported beside it);
+SM clocks sampled during the timed region; the number of kernels launched.
 
 ``--impl reference``: the FP64 oracle timed on the host cores, each step one
 256 x 256 output block of the same workload (full K), rank 0 only.
