@@ -693,7 +693,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16", "data": "synthetic",
+            "dtype": "bf16x3", "data": "synthetic",
             "config": {"workload": WORKLOAD.format(n=p.M), "M": p.M, "N": p.N, "K": p.K, "transA": "N",
                        "transB": "T", "tier": "bf16x3", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (768 MiB FP32 operands + 512 MiB split planes); no flush"},

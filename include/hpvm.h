@@ -4,12 +4,12 @@
  * Heterogeneous Parallel Systems", arXiv 1611.00860).
  *
  * The calls mirror the paper's intrinsics (Table 1 and the intrinsic list of
- * Section 3.2): a program builds a hierarchical dataflow graph (DFG) of
+ * Section 2.2): a program builds a hierarchical dataflow graph (DFG) of
  * internal nodes (which only hold child graphs), allocation leaves and
  * compute leaves, connects them with ordinary edges, binds parent inputs to
  * child inputs, then launches the graph on a CUDA stream and waits for it.
  * The runtime lowers the one graph shape it supports -- the sgemm example of
- * Section 5.1 -- onto hand-written sm_103a kernels.
+ * Section 6.1 -- onto hand-written sm_103a kernels.
  *
  * Conventions shared by every call
  *   - Every function returns HPVM_OK (0) or a negative HPVM_ERR_* code and
@@ -44,7 +44,7 @@ extern "C" {
 /* ---- status codes ----------------------------------------------------- */
 #define HPVM_OK 0
 #define HPVM_ERR_INVALID_ARG (-1)   /* null handle, bad enum, bad port number */
-#define HPVM_ERR_INVALID_GRAPH (-2) /* breaks a rule of Section 3.1/3.2 */
+#define HPVM_ERR_INVALID_GRAPH (-2) /* breaks a rule of Section 2.1/2.2 */
 #define HPVM_ERR_UNSUPPORTED (-3)   /* valid graph the runtime cannot lower */
 #define HPVM_ERR_SHAPE (-4)         /* ld < rows, buffer bytes too small, ... */
 #define HPVM_ERR_ALIGN (-5)         /* operand alignment a kernel needs */
@@ -55,28 +55,28 @@ extern "C" {
 #define HPVM_ERR_OUT_OF_MEMORY (-10)
 
 /* ---- node kinds: the node function a node runs ------------------------ */
-#define HPVM_NODE_INTERNAL 0   /* graph intrinsics only (Section 3.2) */
-#define HPVM_NODE_ALLOCATION 1 /* allocation leaf (Section 4.4): tile memory */
-#define HPVM_NODE_SGEMM_LEAF 2 /* the SgemmLeaf node function (Section 5.1);
+#define HPVM_NODE_INTERNAL 0   /* graph intrinsics only (Section 2.2) */
+#define HPVM_NODE_ALLOCATION 1 /* allocation leaf (Section 3.4): tile memory */
+#define HPVM_NODE_SGEMM_LEAF 2 /* the SgemmLeaf node function (Section 6.1);
                                   outputs 0, 1: its result C and bytesC */
 /* Elementwise leaves over a column-major M x N matrix, updated in place;
  * outputs 0, 1: the matrix and its bytes. Joined to a SgemmLeaf of the same
  * grid by one-to-one edges (SgemmLeaf out 0 -> in 0, out 1 -> in 1) they are
- * merged into it (MergeDependentNodes, Section 4.6).
+ * merged into it (MergeDependentNodes, Section 4.1).
  * TANH_LEAF inputs: 0 X, 1 bytesX, 2 ldx, 3 M, 4 N; X <- tanh(X).
  * TANH_GRAD_LEAF inputs: 0 G, 1 bytesG, 2 ldg, 3 M, 4 N, 5 H, 6 bytesH,
  * 7 ldh; G <- G * (1 - H^2) (the adjoint of tanh at the output H). */
 #define HPVM_NODE_TANH_LEAF 3
 #define HPVM_NODE_TANH_GRAD_LEAF 4
 
-/* ---- edge replication (Section 3.1) ----------------------------------- */
+/* ---- edge replication (Section 2.1) ----------------------------------- */
 #define HPVM_ONE_TO_ONE 0 /* instance i -> instance i; grids must match */
 #define HPVM_ALL_TO_ALL 1 /* every source instance -> every sink instance */
 
 /* ---- leaf precision tiers (how the runtime lowers the SgemmLeaf) ------
  * FP32_DFG: one CUDA thread per leaf instance, one CTA per internal
  *           instance, the Allocation node's tiles in shared memory (the
- *           mapping of Section 4.4 taken literally); FP32 FMA.
+ *           mapping of Section 3.4 taken literally); FP32 FMA.
  * FP32:     register-tiled FP32 CUDA-core kernel (same result definition).
  * BF16X3:   tcgen05 tensor cores, each FP32 operand split into BF16
  *           hi + lo, three products hi*hi + hi*lo + lo*hi, FP32 accumulate.
@@ -94,7 +94,7 @@ extern "C" {
 
 /* A replication extent that is not a constant but the value of input port p
  * of the parent node at run time (the example passes its own block_x,
- * block_y, grid_x, grid_y arguments to createNode2D, Section 5.1). */
+ * block_y, grid_x, grid_y arguments to createNode2D, Section 6.1). */
 #define HPVM_DIM_FROM_INPUT(p) (-1 - (int64_t)(p))
 
 /* launch flags (hpvm_sgemm_root_args.flags) */
@@ -149,7 +149,7 @@ typedef struct hpvm_edge hpvm_edge;
 typedef struct hpvm_graph hpvm_graph;
 
 /* ---- the argument record of the sgemm root ----------------------------
- * The first 88 bytes are the paper's packed %struct.RootIn (Section 5.1:
+ * The first 88 bytes are the paper's packed %struct.RootIn (Section 6.1:
  * A, bytesA, lda, B, bytesB, ldb, C, bytesC, ldc, k, alpha, beta, block_x,
  * block_y, grid_x, grid_y; the host code mallocs 88 bytes and packs them).
  * Root input port p is field p of this record for p = 0..15; the trailer
@@ -213,12 +213,12 @@ typedef struct hpvm_launch_info {
   int32_t tile_m, tile_n, tile_k;  /* output tile per CTA, K slab */
   int32_t smem_bytes;    /* dynamic shared memory of the main kernel */
   int32_t literal;       /* 1: internal instance == CTA, leaf instance ==
-                            thread (Section 4.4 mapping); 0: re-tiled */
+                            thread (Section 3.4 mapping); 0: re-tiled */
   int64_t workspace_bytes;
   int64_t h2d_bytes, d2h_bytes; /* memory-tracker copies this launch made */
 } hpvm_launch_info;
 
-/* ---- runtime set-up (llvm.hpvm.init / llvm.hpvm.cleanup, Section 5.1) --
+/* ---- runtime set-up (llvm.hpvm.init / llvm.hpvm.cleanup, Section 6.1) --
  * device >= 0: a context on that CUDA device (made current for the calling
  * thread). device < 0: a host-only context that can build and validate
  * graphs but not launch them (HPVM_ERR_NO_DEVICE from hpvm_launch). */
@@ -227,7 +227,7 @@ HPVM_API int hpvm_init(int device, hpvm_ctx** out);
  * workspace of the context, after synchronising its device. */
 HPVM_API int hpvm_cleanup(hpvm_ctx* ctx);
 
-/* ---- graph intrinsics (Table 1; Section 3.2 list) ----------------------
+/* ---- graph intrinsics (Table 1; Section 2.2 list) ----------------------
  * createNode / createNode{1,2,3}D: a child of `parent` (NULL for the root)
  * running node function `kind`, with `ndims` in 0..3 (0 = one instance) and
  * extents dims[0..ndims-1], each > 0 or HPVM_DIM_FROM_INPUT(p). Only an
@@ -238,7 +238,7 @@ HPVM_API int hpvm_create_node(hpvm_ctx* ctx, hpvm_node* parent, int kind, int nd
  * input dp of dst; both children of the same internal node; repl is
  * HPVM_ONE_TO_ONE or HPVM_ALL_TO_ALL; one-to-one needs identical grids.
  * stream != 0 makes it a streaming edge (items flow through it repeatedly,
- * Section 3.1); the lowering supports streaming edges between tile grids.
+ * Section 2.1); the lowering supports streaming edges between tile grids.
  * `out` may be NULL. */
 HPVM_API int hpvm_create_edge(hpvm_node* src, hpvm_node* dst, int repl, int sp, int dp,
                      int stream, hpvm_edge** out);
@@ -255,7 +255,7 @@ HPVM_API int hpvm_get_num_dims(hpvm_node* node, int* out);
  * the node's rank report 1. */
 HPVM_API int hpvm_get_num_node_instances(hpvm_node* node, int dim, int64_t* out);
 
-/* Check the graph under `root` against the rules of Sections 3.1-3.2:
+/* Check the graph under `root` against the rules of Sections 2.1-2.2:
  * root is a single-instance internal node; leaves have no children; edges
  * join siblings, ports are in range, one-to-one edges join equal grids, no
  * cycle of ordinary edges; every leaf input is fed exactly once. */
@@ -275,7 +275,13 @@ HPVM_API int hpvm_validate(hpvm_node* root);
  * cudaStream_t; NULL = the legacy default stream) with the argument records
  * `args` (hpvm_sgemm_root_args[], args_size >= 136). Errors found before any
  * work is enqueued (graph, shape, alignment) leave the stream untouched.
- * stream_graph != 0 launches a streaming graph (Section 4.5): it is
+ * Launches of one context share its workspace (the tensor tiers' operand
+ * planes and tail-split sums): a launch on a different stream than the
+ * previous launch that used the workspace first waits for that launch (an
+ * event), so the two do not overlap on the GPU. Inside CUDA stream capture
+ * no such wait is added: captured launches of one context must be ordered
+ * by the caller (one stream, or events of the capture).
+ * stream_graph != 0 launches a streaming graph (Section 3.5): it is
  * validated against `args` and stays alive; nothing runs until items are
  * pushed. */
 HPVM_API int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args,
@@ -284,7 +290,11 @@ HPVM_API int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args,
 /* Wait until the launched graph finished, at most timeout_ms milliseconds
  * (< 0: no limit). HPVM_ERR_TIMEOUT leaves the handle valid; any other
  * return frees it. HPVM_ERR_DEVICE_FAULT: a kernel gave up a bounded wait
- * (the results are not valid). */
+ * (the results are not valid). The status word that records such an expiry
+ * belongs to the context, not to a graph: the first hpvm_wait or hpvm_pop
+ * after the expiry reports it (and clears it), whichever graph of the
+ * context it is called for, so with several graphs in flight treat the
+ * error as "some launch of this context since the last check failed". */
 HPVM_API int hpvm_wait(hpvm_graph* graph, int64_t timeout_ms);
 /* Push one item into a streaming graph: `args` holds the item's records
  * (as for hpvm_launch). The item runs asynchronously on the next of the
@@ -305,7 +315,7 @@ HPVM_API int hpvm_pop(hpvm_graph* graph, void* out, size_t out_size, int64_t tim
 /* Copy the description of what `graph` launched into *out. */
 HPVM_API int hpvm_graph_info(hpvm_graph* graph, hpvm_launch_info* out);
 
-/* ---- memory tracker (Section 3.3) -------------------------------------
+/* ---- memory tracker (Section 2.3) -------------------------------------
  * track_mem: host region [p, p+bytes) may be named in argument records; its
  * latest copy is the host's. A launch copies it to a device copy the
  * runtime owns when the copy there is stale and the leaf reads it (A, B;
@@ -328,7 +338,10 @@ HPVM_API int hpvm_untrack_mem(hpvm_ctx* ctx, void* p);
 HPVM_API int hpvm_workspace_size(hpvm_ctx* ctx, hpvm_node* root, const void* args,
                         size_t args_size, size_t* out);
 /* Use caller-owned device memory as workspace (NULL/0: the runtime
- * allocates and caches its own). Must stay valid while launches use it. */
+ * allocates and caches its own). Must stay valid while launches use it.
+ * Launches on several streams are ordered as hpvm_launch describes; other
+ * users of the same memory (another context, the caller's own kernels) are
+ * not. */
 HPVM_API int hpvm_set_workspace(hpvm_ctx* ctx, void* dev_ptr, size_t bytes);
 /* The operand plane cache (HPVM_LAUNCH_CACHE_* / REUSE_*): its size in bytes,
  * and freeing it (after every launch that reads a cached plane has finished;
@@ -390,10 +403,18 @@ HPVM_API int hpvm_quant_fp8(const float* X, int64_t ld, int kcontig, int64_t row
  *   - It allocates nothing: no cudaMalloc, cudaFree or allocating library
  *     call. The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current) and caches it, so make
- *     the first call on each device before any stream capture.
+ *     the first call on each device before any stream capture. Under CUDA's
+ *     default lazy module loading that first lookup is also what loads the
+ *     library's kernels onto the device and so creates the 64 MiB array
+ *     there: make a first call (a small product will do) before a memory pool
+ *     reserves the device's memory, or the array may not fit. After a
+ *     cudaDeviceReset the device has a new context; the next call sees that
+ *     and looks the address up again.
  *   - Every call uses the same array, and the array keeps the contents the
- *     last call left. Nothing in it needs to start at zero: every byte a call
- *     reads, the same call writes first. Calls whose executions overlap on the
+ *     last call left. The split planes a call reads, the same call writes
+ *     first; the tail split's arrival counters (when its partial sums fit in
+ *     the array) are zeroed by a cudaMemsetAsync that the call enqueues on
+ *     its stream before the leaf kernel. Calls whose executions overlap on the
  *     GPU (concurrent streams, or several threads) race on the array and give
  *     wrong results: serialise them.
  *   - Errors: HPVM_ERR_SHAPE when the planes, 4*(M+N)*roundup(K,8) bytes with

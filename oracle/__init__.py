@@ -10,10 +10,10 @@ arithmetic of the method).
 
 Contents
   * ``sgemm``   -- the definition C <- alpha*op(A)*op(B) + beta*C in FP64
-                   (plain C triple loop, Section 5.1 SgemmLeaf), whole or on
+                   (plain C triple loop, Section 6.1 SgemmLeaf), whole or on
                    sampled blocks, and the normwise error metric.
   * ``dfg``     -- a small interpreter of the hierarchical dataflow graph
-                   (Sections 3.1-3.2, the intrinsics of Table 1) that runs the
+                   (Sections 2.1-2.2, the intrinsics of Table 1) that runs the
                    sgemm example graph node by node, leaf instances in
                    barrier-separated phases.
   * ``quant``   -- round-to-nearest-even FP32->BF16, the two-term BF16 split,

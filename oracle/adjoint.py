@@ -3,9 +3,9 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 The paper has no differentiation; these are the plain chain-rule adjoints of
-its sgemm leaf (Section 5.1) and of a chain of such leaves joined by
-elementwise tanh leaves over streaming edges (Section 3.1 streaming edges;
-Section 4.5 pipelining). A matrix product from numpy serves as a step.
+its sgemm leaf (Section 6.1) and of a chain of such leaves joined by
+elementwise tanh leaves over streaming edges (Section 2.1 streaming edges;
+Section 3.5 pipelining). A matrix product from numpy serves as a step.
 
 sgemm leaf, Y = alpha*op(A)*op(B) + beta*C, upstream gradient dY:
     d op(A) = alpha * dY * op(B)^T,   d op(B) = alpha * op(A)^T * dY,

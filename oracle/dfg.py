@@ -5,13 +5,13 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``). Pure Python, meant for
 tiny graphs; it is independent of the C-ABI graph builder of the product.
 
 Semantics followed
-  * Section 3.1: a program is a hierarchy of nodes; an internal node holds a
+  * Section 2.1: a program is a hierarchy of nodes; an internal node holds a
     child graph, a leaf node computes. A static node stands for a 1-D/2-D/3-D
     grid of independent dynamic instances. Edges are replicated either
     all-to-all (every source instance feeds every sink instance; it acts as a
     barrier between the groups) or one-to-one (instance i feeds instance i;
     the two grids must have the same rank and extents).
-  * Section 3.2 / Table 1: node functions receive their incoming edges as
+  * Section 2.2 / Table 1: node functions receive their incoming edges as
     arguments and return one value per outgoing edge. Internal node functions
     only call the graph intrinsics createNode{,1D,2D,3D}, createEdge,
     bind.input, bind.output. Leaf functions may use the query intrinsics
@@ -19,7 +19,7 @@ Semantics followed
     getNumNodeInstances.[xyz], the allocation intrinsic malloc and the
     synchronisation intrinsic barrier, which only orders the dynamic
     instances of the executing leaf that share its parent instance.
-  * Section 4.4 (tiling): memory a leaf allocates is private to the instances
+  * Section 3.4 (tiling): memory a leaf allocates is private to the instances
     of its sibling leaf created by the same dynamic instance of the parent.
 
 Barriers are modelled by writing leaf functions as Python generators: each
@@ -215,7 +215,7 @@ class Runtime:
 def _instances(dims: tuple):
     if not dims:
         return [()]
-    # x fastest, matching the linear id x + numX * y of Section 5.1
+    # x fastest, matching the linear id x + numX * y of Section 6.1
     return [tuple(reversed(t)) for t in itertools.product(*[range(d) for d in reversed(dims)])]
 
 
@@ -341,7 +341,7 @@ def launch(rt: Runtime, root_func, args: list) -> tuple:
 
 
 # ---------------------------------------------------------------------------
-# The sgemm example (Section 5.1), in this interpreter.
+# The sgemm example (Section 6.1), in this interpreter.
 #
 # Input ports of the leaf: 0 A, 1 bytesA, 2 lda, 3 B, 4 bytesB, 5 ldb, 6 C,
 # 7 bytesC, 8 ldc, 9 k, 10 alpha, 11 beta, 12 shB, 13 bytesShB (as in the
@@ -459,7 +459,7 @@ def run_sgemm_dfg(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, transA, transB,
 # Elementwise leaves and the streamed chain.
 #
 # A chain of sgemm stages joined by elementwise tanh leaves, with items fed
-# through streaming edges (Section 3.1 streaming edges; Section 4.5: a
+# through streaming edges (Section 2.1 streaming edges; Section 3.5: a
 # streaming graph's nodes stay alive and process every item pushed).
 # Row-major items X (rows x w_in) and weights W (w_in x w_out) are stored so
 # that the column-major sgemm leaf computes Y^T = W^T X^T: M = w_out,

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-The paper computes in FP32 only (Section 5.1); the FP8 tier is this
+The paper computes in FP32 only (Section 6.1); the FP8 tier is this
 project's addition. Its result is defined as the sgemm definition applied to
 the dequantised operands:
 

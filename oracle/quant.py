@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-The paper computes in FP32 only (Section 5.1). The BF16 and FP8 tiers are
+The paper computes in FP32 only (Section 6.1). The BF16 and FP8 tiers are
 this project's additions; these functions state the roundings those tiers
 use, written from the IEEE-754 formats themselves (bit fields and
 round-half-to-even), not from any library conversion:

@@ -2,9 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Follows Section 5.1 (the SgemmLeaf node of the sgemm example: arguments A,
+Follows Section 6.1 (the SgemmLeaf node of the sgemm example: arguments A,
 lda, B, ldb, C, ldc, k, alpha, beta; A and B ``in``, C ``in out`` per
-Section 3.3). Reading taken where the paper is silent: column-major storage,
+Section 2.3). Reading taken where the paper is silent: column-major storage,
 op(A) = A or A^T and op(B) = B or B^T chosen by flags (the example's own form
 is op(A) = A, op(B) = B^T), explicit M and N, and the BLAS convention that
 beta == 0 means C is not read.

@@ -5,9 +5,9 @@
  * only tests/, the smoke check and the benchmark's CPU-baseline leg use it.
  * It shares no code, header or constant with the CUDA library.
  *
- * What it computes (Section 5.1, the SgemmLeaf of the sgemm example, whose
+ * What it computes (Section 6.1, the SgemmLeaf of the sgemm example, whose
  * arguments are A, lda, B, ldb, C, ldc, k, alpha, beta with A and B read-only
- * and C read and written, Section 3.3 on in/out attributes):
+ * and C read and written, Section 2.3 on in/out attributes):
  *
  *     C[i,j] <- alpha * sum_{p<K} opA(i,p) * opB(p,j) + beta * C[i,j]
  *

@@ -6,7 +6,7 @@ each stage is a tile grid holding the sgemm example's Allocation and
 SgemmLeaf plus, between stages, a TanhLeaf joined to the SgemmLeaf by
 one-to-one edges (merged into the leaf's epilogue, MergeDependentNodes);
 stages are joined by streaming all-to-all edges that carry the result
-matrix (Sections 3.1, 4.5, 4.6).
+matrix (Sections 2.1, 3.5, 4.1).
 
 A row-major matrix is a column-major matrix of the transposed shape, so
 Z = H W is computed as the column-major sgemm Z^T = W^T H^T (M = w_out,

@@ -1,9 +1,9 @@
-// FP32 CUDA-core lowerings of the SgemmLeaf node (Section 5.1).
+// FP32 CUDA-core lowerings of the SgemmLeaf node (Section 6.1).
 //
 // Both kernels compute C <- alpha*op(A)*op(B) + beta*C with column-major
 // storage; beta == 0 means C is not read.
 //
-// sgemm_leaf_dfg: the hierarchy of Section 4.4 taken literally. The
+// sgemm_leaf_dfg: the hierarchy of Section 3.4 taken literally. The
 //   internal node SgemmInternal (a 2-D grid) becomes the CUDA grid, the
 //   replicated SgemmLeaf (a square block x block grid) becomes the CTA, the
 //   Allocation node's two block x block FP32 tiles become dynamic shared

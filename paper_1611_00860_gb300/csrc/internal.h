@@ -82,7 +82,7 @@ struct Epilogue {
 cudaError_t launch_elementwise(const SgemmDesc& d, const Epilogue& e, cudaStream_t s);
 
 // ---- FP32 CUDA-core leaves (fp32_leaf.cu) ---------------------------------
-// Literal Section 4.4 mapping: CTA (bx, by) = internal instance, thread
+// Literal Section 3.4 mapping: CTA (bx, by) = internal instance, thread
 // (tx, ty) = leaf instance, tiles of the Allocation node in shared memory.
 cudaError_t launch_fp32_dfg(const SgemmDesc& d, int block, int grid_x,
                             int grid_y, size_t tile_bytes, cudaStream_t s,

@@ -1,17 +1,17 @@
 // Host runtime of the C-ABI (include/hpvm.h).
 //
-//  * Graph builder (the paper's Graph Builder pass, Section 4.2, fed by the
+//  * Graph builder (the paper's Graph Builder pass, Section 3.2, fed by the
 //    intrinsic calls of Table 1 instead of IR) and validator (the rules of
-//    Sections 3.1-3.2).
-//  * Lowering (Sections 4.3-4.4 and the generated host code of Section 5.3):
+//    Sections 2.1-2.2).
+//  * Lowering (Sections 3.3-3.4 and the generated host code of Section 6.3):
 //    every input of a leaf is resolved by following edges and bindings up to
 //    a field of the root's argument records; the Allocation size is computed
 //    on the host before the launch; each tile-grid stage becomes one leaf
 //    kernel launch, with a dependent elementwise leaf merged into the
-//    kernel's epilogue (MergeDependentNodes, Section 4.6) or run after it.
-//  * Launch and bounded wait; streaming graphs (Section 4.5) whose items are
+//    kernel's epilogue (MergeDependentNodes, Section 4.1) or run after it.
+//  * Launch and bounded wait; streaming graphs (Section 3.5) whose items are
 //    pushed and popped, pipelined over a ring of CUDA streams.
-//  * The memory tracker of Section 3.3.
+//  * The memory tracker of Section 2.3.
 //  * The operand plane cache (no counterpart in the paper): the BF16 / E4M3
 //    planes of an operand kept across launches (CACHE_* / REUSE_* flags),
 //    filled by a conversion or, for a stage's result, by its epilogue
@@ -208,6 +208,10 @@ struct hpvm_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   bool ws_owned = false;
+  // the last launch that used the workspace: its stream and an event
+  // recorded after it (a launch on another stream waits for it)
+  cudaStream_t ws_stream = nullptr;
+  cudaEvent_t ws_event = nullptr;
   hpvm::DeviceStatus status;
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed;  // main-kernel events
@@ -1174,6 +1178,7 @@ int hpvm_cleanup(hpvm_ctx* ctx) {
     }
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
+    if (ctx->ws_event) cudaEventDestroy(ctx->ws_event);
     if (ctx->status.host) cudaFreeHost(ctx->status.host);
     for (auto& pr : ctx->timed) {
       cudaEventDestroy(pr.first);
@@ -1414,8 +1419,26 @@ int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args, size_t args_si
   }
   void* ws = nullptr;
   size_t ws_bytes = 0;
-  if ((rc = ensure_workspace(ctx, plan_workspace(P), &ws, &ws_bytes)) != HPVM_OK) return rc;
+  const size_t ws_need = plan_workspace(P);
+  if ((rc = ensure_workspace(ctx, ws_need, &ws, &ws_bytes)) != HPVM_OK) return rc;
+  // Launches of one context share its workspace. A launch on a stream other
+  // than the previous workspace user's first waits for that launch, so the
+  // two never overlap on the GPU. Inside stream capture the caller orders
+  // captured launches (an event recorded outside a capture cannot be waited
+  // on inside it), so nothing is added there.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool order_ws = ws_need > 0 && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+                        cap == cudaStreamCaptureStatusNone;
+  if (order_ws && ctx->ws_event && ctx->ws_stream != s) {
+    if ((e = cudaStreamWaitEvent(s, ctx->ws_event, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  }
   if ((rc = execute_plan(ctx, P, s, ws, ws_bytes, &g->info)) != HPVM_OK) return rc;
+  if (order_ws) {
+    if (!ctx->ws_event && (e = cudaEventCreateWithFlags(&ctx->ws_event, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventRecord(ctx->ws_event, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    ctx->ws_stream = s;
+  }
   const int flags = record_i32(P, P.stages.front().rec, kFlagsOffset);
   if (!(flags & HPVM_LAUNCH_NO_EVENT)) {
     e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);

@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05) lowerings of the SgemmLeaf node (Section 5.1) for
+// Tensor-core (tcgen05) lowerings of the SgemmLeaf node (Section 6.1) for
 // sm_103a: the BF16x3 split tier, the plain BF16 tier and the block-scaled
 // FP8 (E4M3) tier.
 //
@@ -10,7 +10,7 @@
 // tensor memory (the BF16 tier keeps hi*hi only; the FP8 tier multiplies
 // E4M3 codes and scales each 128-wide K block by its two block scales).
 //
-// Mapping of the dataflow graph (Section 4.4): one internal-node instance
+// Mapping of the dataflow graph (Section 3.4): one internal-node instance
 // (an output tile) is one CTA (128 x 256) or a pair of CTAs in a cluster
 // (256 x 256, cta_group::2); the Allocation node's tile memory is a ring of
 // STAGES shared-memory slabs filled by TMA (the paper's scratchpad tiles),
@@ -40,6 +40,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -1423,12 +1424,27 @@ bool encode_plane(CUtensorMap* map, const void* base, int rows, int K, int Kp, i
   return true;
 }
 
+// Per-device caches: kernel attributes (cudaFuncSetAttribute applies to the
+// device current when it is called), occupancy and the SM count are looked
+// up once per device and kept per device, so launches on several devices
+// of one process each see their own device's values. Entries are atomics:
+// two threads that race fill in the same value. A device numbered beyond
+// the cache (or none current) is looked up at every call.
+constexpr int kMaxDevices = 64;
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  return dev;
+}
+inline bool cached_device(int dev) { return dev >= 0 && dev < kMaxDevices; }
+
 int num_sms() {
-  static int n = 0;
+  static std::atomic<int> cache[kMaxDevices];
+  const int dev = current_device();
+  int n = cached_device(dev) ? cache[dev].load(std::memory_order_relaxed) : 0;
   if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    if (dev < 0 || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    if (cached_device(dev)) cache[dev].store(n, std::memory_order_relaxed);
   }
   return n;
 }
@@ -1589,13 +1605,14 @@ cudaError_t launch_leaf(const CUtensorMap* maps, TcParams prm, int tiles, size_t
                         cudaStream_t s, int* grid_ctas, const LaunchHooks* hooks) {
   using C_ = Cfg<MODE, PAIR>;
   auto kernel = sgemm_tc<MODE, EPI, false, PAIR>;
+  const int dev = current_device();
   if constexpr (!PAIR) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<bool> attr_set[kMaxDevices];
+    if (!cached_device(dev) || !attr_set[dev].load(std::memory_order_acquire)) {
       cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
       if (e == cudaSuccess) e = check_register_split(kernel);
       if (e != cudaSuccess) return e;
-      attr_set = true;
+      if (cached_device(dev)) attr_set[dev].store(true, std::memory_order_release);
     }
     const int grid = std::max(1, std::min(tiles, num_sms()));
     *grid_ctas = grid;
@@ -1619,7 +1636,8 @@ cudaError_t launch_leaf(const CUtensorMap* maps, TcParams prm, int tiles, size_t
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  static int max_clusters = 0;
+  static std::atomic<int> max_clusters_of[kMaxDevices];
+  int max_clusters = cached_device(dev) ? max_clusters_of[dev].load(std::memory_order_acquire) : 0;
   if (max_clusters == 0) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
     if (e == cudaSuccess) e = check_register_split(kernel);
@@ -1630,6 +1648,7 @@ cudaError_t launch_leaf(const CUtensorMap* maps, TcParams prm, int tiles, size_t
     if (e != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
     max_clusters = n;
+    if (cached_device(dev)) max_clusters_of[dev].store(n, std::memory_order_release);
   }
   const int clusters = std::max(1, std::min(tiles, max_clusters));
   cfg.gridDim = dim3(2 * clusters);
@@ -2113,13 +2132,33 @@ constexpr size_t kNoAllocScratchBytes = HPVM_NOALLOC_SCRATCH_BYTES;
 // it gets the address through cudaGetSymbolAddress (see noalloc_scratch).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device (with that device current) and cached. Returns nullptr and a
-// message on failure.
+// The calling thread's current CUDA context (the driver's cuCtxGetCurrent,
+// reached through the runtime's entry-point query), or null.
+CUcontext current_context() {
+  using Fn = CUresult (*)(CUcontext*);
+  static Fn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<Fn>(f);
+  });
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+// Device address of g_noalloc_scratch on the current device, looked up with
+// that device current and cached per device together with the context it
+// belongs to. A device reset (cudaDeviceReset) gives the device a new
+// context, in which the array has a new address: the lookup is then made
+// again. Returns nullptr and a message on failure.
 void* noalloc_scratch(std::string* err) {
-  constexpr int kMaxDevices = 64;
   static std::mutex mu;
   static void* addr[kMaxDevices] = {nullptr};
+  static CUcontext owner[kMaxDevices] = {nullptr};
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -2127,14 +2166,17 @@ void* noalloc_scratch(std::string* err) {
     return nullptr;
   }
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  const CUcontext ctx = current_context();
+  if (!addr[dev] || !ctx || ctx != owner[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
+      addr[dev] = nullptr;
       *err = std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e);
       return nullptr;
     }
     addr[dev] = p;
+    owner[dev] = current_context();  // the lookup made the device's context current if it was not
   }
   return addr[dev];
 }

@@ -1,4 +1,4 @@
-"""The sgemm dataflow graph of Section 5.1, built through the C-ABI, and a
+"""The sgemm dataflow graph of Section 6.1, built through the C-ABI, and a
 launcher that passes PyTorch CUDA tensors to it.
 
 Argument marshalling only: the graph is built with the intrinsic calls of

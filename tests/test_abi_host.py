@@ -101,7 +101,7 @@ def test_plan():
     assert H.hpvm_plan_sgemm(H.HPVM_TIER_FP32, 0, 0, 0)[2:] == (1, 1)
 
 
-# ---- graph rules (Sections 3.1-3.2) ------------------------------------------
+# ---- graph rules (Sections 2.1-2.2) ------------------------------------------
 
 def test_root_must_be_single_internal(ctx):
     with pytest.raises(H.HpvmError) as e:

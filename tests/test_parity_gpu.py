@@ -49,7 +49,7 @@ def test_small_workload(dfg, tier):
     err = O.normwise_rel_err(got, O.sgemm_f64(p))
     assert err <= TOL[tier], err
     if tier == H.HPVM_TIER_FP32_DFG:
-        # Section 4.4 mapping: internal grid 8 x 6 = CTAs, 16 x 16 leaf = threads,
+        # Section 3.4 mapping: internal grid 8 x 6 = CTAs, 16 x 16 leaf = threads,
         # the Allocation's two 16 x 16 FP32 tiles = 2 KB of shared memory
         assert (info["grid_x"], info["grid_y"], info["block_threads"]) == (8, 6, 256)
         assert info["smem_bytes"] == 2 * 16 * 16 * 4 and info["literal"] == 1
@@ -115,7 +115,7 @@ def test_literal_mapping_other_leaf_sizes(dfg):
 @pytest.mark.parametrize("tier", [H.HPVM_TIER_FP32, H.HPVM_TIER_BF16X3])
 def test_memory_tracker_host_buffers(cuda_device, tier):
     # host arrays registered with track_mem; the launch copies them in, and
-    # request_mem brings C back (Section 3.3)
+    # request_mem brings C back (Section 2.3)
     p = W.sgemm_problem(260, 190, 75, seed=9, alpha=1.5, beta=0.5)
     ref = O.sgemm_f64(p)
     A, B, C = (t.clone().pin_memory() for t in (p.A, p.B, p.C))

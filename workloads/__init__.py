@@ -8,12 +8,12 @@ seeded ``torch.Generator`` so the oracle and the CUDA path see bit-identical
 FP32 inputs.
 
 Storage convention (the paper's sgemm leaf takes BLAS-style ``lda/ldb/ldc``
-arguments, Section 5.1): matrices are column-major. A matrix with ``rows`` rows
+arguments, Section 6.1): matrices are column-major. A matrix with ``rows`` rows
 and ``cols`` columns and leading dimension ``ld >= rows`` is a flat FP32
 buffer of ``ld * cols`` elements whose element (r, c) sits at ``r + c * ld``.
 The helpers below return such flat buffers together with their shapes.
 
-Workload shapes (the sgemm example of Section 5.1 at the sizes the
+Workload shapes (the sgemm example of Section 6.1 at the sizes the
 measurement plan fixes):
   * small DFG:  M=128, N=96, K=160, alpha=1.5, beta=0.5, A,B,C ~ U[-1,1];
   * large DFG:  M=N=K=8192, A,B,C ~ N(0,1), alpha=beta=1; variant "colscale"
