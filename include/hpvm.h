@@ -81,6 +81,19 @@ extern "C" {
  * BF16X3:   tcgen05 tensor cores, each FP32 operand split into BF16
  *           hi + lo, three products hi*hi + hi*lo + lo*hi, FP32 accumulate.
  * BF16:     tcgen05 tensor cores, operands rounded to BF16, FP32 accumulate.
+ * BF16X6:   tcgen05 tensor cores, each FP32 operand split into three BF16
+ *           parts hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid)
+ *           (hi + mid + lo == x for every x of normal FP32 range, beyond
+ *           2^-110 or so in magnitude), six products lo*hi + hi*lo + mid*mid
+ *           + mid*hi + hi*mid + hi*hi (the three dropped ones are below 2^-25
+ *           of hi*hi), FP32 accumulate. Twice the tensor work of BF16X3, for
+ *           inputs on which two BF16 parts are not enough: a result dominated
+ *           by a few rows and columns of large magnitude (say log-normal row
+ *           scales) inherits the 2^-17 relative error of the two-part split
+ *           in its few dominant elements, and BF16X3 can then miss 5e-6
+ *           normwise even in exact arithmetic. Plain epilogue only: a merged
+ *           elementwise leaf runs as its own kernel, and the plane cache
+ *           flags CACHE_C / PLANES_ONLY and forwarded planes do not apply.
  * FP8:      tcgen05 kind::f8f6f4, op(A) and op(B) quantised to E4M3 with one
  *           FP32 scale per 128 x 128 block (scale = amax/448, round to
  *           nearest even, saturating); each 128-wide K block's product is
@@ -91,6 +104,7 @@ extern "C" {
 #define HPVM_TIER_BF16X3 2
 #define HPVM_TIER_BF16 3
 #define HPVM_TIER_FP8 4
+#define HPVM_TIER_BF16X6 5
 
 /* A replication extent that is not a constant but the value of input port p
  * of the parent node at run time (the example passes its own block_x,
@@ -381,6 +395,12 @@ HPVM_API int hpvm_kernel_timing(hpvm_ctx* ctx, double* total_ms, int64_t* launch
  *   Kq = roundup(K, 16) and zero codes for K <= k < Kq. */
 HPVM_API int hpvm_split_bf16(const float* X, int64_t ld, int kcontig, int64_t rows, int64_t K,
                              void* hi, void* lo, void* cuda_stream);
+/* hpvm_split3_bf16: the BF16X6 tier's pre-pass, three planes of rows*Kp
+ *   BF16 values (Kp = roundup(K, 8), zeros for K <= k < Kp):
+ *   hi[r*Kp + k] = bf16_rn(Y(r,k)), mid[...] = bf16_rn(Y(r,k) - hi) and
+ *   lo[...] = bf16_rn(Y(r,k) - hi - mid), both differences exact in FP32. */
+HPVM_API int hpvm_split3_bf16(const float* X, int64_t ld, int kcontig, int64_t rows, int64_t K,
+                              void* hi, void* mid, void* lo, void* cuda_stream);
 HPVM_API int hpvm_quant_fp8(const float* X, int64_t ld, int kcontig, int64_t rows, int64_t K,
                             void* q, float* scales, void* cuda_stream);
 

@@ -11,6 +11,10 @@ round-half-to-even), not from any library conversion:
     round to nearest, ties to even; NaN stays NaN.
   * split_bf16(x): hi = bf16_rn(x), lo = bf16_rn(x - hi), the difference
     taken in FP32 (exact, since hi is within one BF16 half-ulp of x).
+  * split3_bf16(x): hi = bf16_rn(x), mid = bf16_rn(x - hi),
+    lo = bf16_rn(x - hi - mid), both differences in FP32 (exact: x - hi has
+    at most 16 significant bits and x - hi - mid at most 8, so lo holds it
+    and hi + mid + lo == x).
   * e4m3_rn_sat(x): FP32 -> OCP FP8 E4M3 (bias 7, largest finite 448,
     smallest subnormal 2^-9, no infinities), round to nearest even,
     saturating to +-448.
@@ -42,6 +46,17 @@ def split_bf16(x) -> tuple[np.ndarray, np.ndarray]:
     hi = bf16_rn(f)
     lo = bf16_rn((f - hi).astype(np.float32))
     return hi, lo
+
+
+def split3_bf16(x) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Three-term BF16 split: x = hi + mid + lo with hi = bf16(x),
+    mid = bf16(x - hi), lo = bf16(x - hi - mid)."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    hi = bf16_rn(f)
+    r = (f - hi).astype(np.float32)
+    mid = bf16_rn(r)
+    lo = bf16_rn((r - mid).astype(np.float32))
+    return hi, mid, lo
 
 
 def e4m3_rn_sat(x) -> np.ndarray:

@@ -9,6 +9,7 @@ from . import _lib  # noqa: F401  (loads libhpvm_gb300.so or raises)
 from ._lib import (  # noqa: F401
     HPVM_TIER_BF16,
     HPVM_TIER_BF16X3,
+    HPVM_TIER_BF16X6,
     HPVM_TIER_FP32,
     HPVM_TIER_FP32_DFG,
     HPVM_TIER_FP8,
@@ -20,6 +21,7 @@ TIERS = {
     "fp32_dfg": HPVM_TIER_FP32_DFG,
     "fp32": HPVM_TIER_FP32,
     "bf16x3": HPVM_TIER_BF16X3,
+    "bf16x6": HPVM_TIER_BF16X6,
     "bf16": HPVM_TIER_BF16,
     "fp8": HPVM_TIER_FP8,
 }

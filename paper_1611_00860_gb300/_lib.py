@@ -44,6 +44,7 @@ HPVM_TIER_FP32 = 1
 HPVM_TIER_BF16X3 = 2
 HPVM_TIER_BF16 = 3
 HPVM_TIER_FP8 = 4
+HPVM_TIER_BF16X6 = 5
 
 HPVM_LAUNCH_NO_EVENT = 1
 HPVM_LAUNCH_NO_FUSION = 2
@@ -151,6 +152,7 @@ def _load() -> ctypes.CDLL:
         "hpvm_set_kernel_timing": (I, [P, I]),
         "hpvm_kernel_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "hpvm_split_bf16": (I, [P, I64, I, I64, I64, P, P, P]),
+        "hpvm_split3_bf16": (I, [P, I64, I, I64, I64, P, P, P, P]),
         "hpvm_quant_fp8": (I, [P, I64, I, I64, I64, P, P, P]),
         "hpvm_sgemm_bf16x3_noalloc": (I, [I64, I64, I64, ctypes.c_float, P, I64, P, I64,
                                           ctypes.c_float, P, I64, I, I, P, P]),
@@ -329,6 +331,12 @@ def hpvm_split_bf16(X: int, ld: int, kcontig: bool, rows: int, K: int, hi: int,
                     lo: int | None, cuda_stream: int = 0) -> None:
     _check(LIB.hpvm_split_bf16(X, int(ld), int(bool(kcontig)), int(rows), int(K), hi, lo,
                                cuda_stream or None))
+
+
+def hpvm_split3_bf16(X: int, ld: int, kcontig: bool, rows: int, K: int, hi: int, mid: int,
+                     lo: int, cuda_stream: int = 0) -> None:
+    _check(LIB.hpvm_split3_bf16(X, int(ld), int(bool(kcontig)), int(rows), int(K), hi, mid, lo,
+                                cuda_stream or None))
 
 
 def hpvm_quant_fp8(X: int, ld: int, kcontig: bool, rows: int, K: int, q: int, scales: int,

@@ -93,8 +93,9 @@ cudaError_t launch_fp32_tiled(const SgemmDesc& d, cudaStream_t s,
 void fp32_tiled_tile(int* tm, int* tn);
 
 // ---- tensor-core leaves (tc_leaf.cu) --------------------------------------
-// tier: 2 = BF16x3 split, 3 = BF16, 4 = FP8. `epi` is fused into the
-// leaf's epilogue (after alpha*acc + beta*C).
+// tier: 2 = BF16x3 split, 3 = BF16, 4 = FP8, 5 = BF16x6 split (plain
+// epilogue only). `epi` is fused into the leaf's epilogue (after
+// alpha*acc + beta*C).
 size_t tc_workspace_bytes(const SgemmDesc& d, int tier);
 // Returns a cudaError_t; on a host-side precondition failure returns
 // cudaErrorInvalidValue and fills *err.
@@ -110,6 +111,7 @@ struct OperandPlanes {
 };
 struct OperandLayout {
   size_t hi = 0, lo = 0, scales = 0, total = 0;
+  size_t lo2 = 0;  // BF16x6: the third part's plane
 };
 OperandLayout tc_operand_layout(int tier, int64_t rows, int64_t K);
 cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes,

@@ -667,7 +667,7 @@ int32_t record_i32(const Plan& P, int rec, size_t off) {
 }
 
 int check_stage_tier(const Stage& S, int tier) {
-  if (tier < HPVM_TIER_FP32_DFG || tier > HPVM_TIER_FP8) return fail(HPVM_ERR_INVALID_ARG, "unknown tier %d", tier);
+  if (tier < HPVM_TIER_FP32_DFG || tier > HPVM_TIER_BF16X6) return fail(HPVM_ERR_INVALID_ARG, "unknown tier %d", tier);
   if (tier == HPVM_TIER_FP32_DFG) {
     if (S.block_x != S.block_y)
       return fail(HPVM_ERR_UNSUPPORTED, "the FP32_DFG lowering needs a square leaf grid (got %lld x %lld)",
@@ -684,7 +684,7 @@ int check_stage_tier(const Stage& S, int tier) {
 }
 
 size_t workspace_need(const Stage& S, int tier) {
-  if (tier == HPVM_TIER_BF16X3 || tier == HPVM_TIER_BF16 || tier == HPVM_TIER_FP8)
+  if (tier == HPVM_TIER_BF16X3 || tier == HPVM_TIER_BF16 || tier == HPVM_TIER_FP8 || tier == HPVM_TIER_BF16X6)
     return hpvm::tc_workspace_bytes(S.d, tier);
   return 0;
 }
@@ -978,10 +978,11 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
         ctx->timed.emplace_back(hooks.main_begin, hooks.main_end);
       }
       // MergeDependentNodes: the tensor-core leaves take the elementwise
-      // leaf into their epilogue; the FP32 leaves (or HPVM_LAUNCH_NO_FUSION)
-      // run it as its own kernel after the sgemm leaf.
+      // leaf into their epilogue; the FP32 leaves, the BF16X6 leaf (built
+      // with the plain epilogue only) and HPVM_LAUNCH_NO_FUSION run it as
+      // its own kernel after the sgemm leaf.
       const bool tensor = tier >= HPVM_TIER_BF16X3;
-      const bool fuse = tensor && !(flags & HPVM_LAUNCH_NO_FUSION);
+      const bool fuse = tensor && tier != HPVM_TIER_BF16X6 && !(flags & HPVM_LAUNCH_NO_FUSION);
       // operand plane cache (A's rows are contiguous unless transposed, B's
       // N rows only when transposed: the layouts the conversions read)
       hpvm::OperandPlanes pa, pb;
@@ -1133,7 +1134,7 @@ void free_graph(hpvm_graph* g) {
 extern "C" {
 
 const char* hpvm_last_error(void) { return g_last_error.c_str(); }
-int hpvm_version(void) { return 200; }
+int hpvm_version(void) { return 201; }
 
 int hpvm_init(int device, hpvm_ctx** out) {
   if (!out) return fail(HPVM_ERR_INVALID_ARG, "out is NULL");
@@ -1324,7 +1325,8 @@ int hpvm_plan_sgemm(int tier, int64_t M, int64_t N, int64_t K, int32_t* block_x,
     case HPVM_TIER_FP32: hpvm::fp32_tiled_tile(&tm, &tn); break;
     case HPVM_TIER_BF16X3:
     case HPVM_TIER_BF16:
-    case HPVM_TIER_FP8: hpvm::tc_tile(tier, &tm, &tn); break;
+    case HPVM_TIER_FP8:
+    case HPVM_TIER_BF16X6: hpvm::tc_tile(tier, &tm, &tn); break;
     default: return fail(HPVM_ERR_INVALID_ARG, "unknown tier %d", tier);
   }
   *block_x = tm;

@@ -9,6 +9,11 @@
 // hi*hi + hi*lo + lo*hi on the tensor cores into one FP32 accumulator in
 // tensor memory (the BF16 tier keeps hi*hi only; the FP8 tier multiplies
 // E4M3 codes and scales each 128-wide K block by its two block scales).
+// The BF16x6 tier splits each operand into three parts, hi, mid =
+// bf16_rn(x - hi) and lo = bf16_rn(x - hi - mid), whose sum is x itself
+// for every FP32 x away from the subnormal range, and sums the six
+// products whose size is at least 2^-17 of hi*hi (lo*hi, hi*lo, mid*mid,
+// mid*hi, hi*mid, hi*hi): the dropped ones are below 2^-25.
 //
 // Mapping of the dataflow graph (Section 3.4): one internal-node instance
 // (an output tile) is one CTA (128 x 256) or a pair of CTAs in a cluster
@@ -19,7 +24,8 @@
 //
 // Kernels
 //   split_mmajor / split_kmajor / split_batch: FP32 op(X) -> K-major BF16
-//       hi (and lo) planes, rows of Kp = roundup(K, 8) elements.
+//       hi (and lo, and for BF16x6 a third) planes, rows of Kp =
+//       roundup(K, 8) elements.
 //   quant_fp8: FP32 op(X) -> E4M3 codes and one FP32 scale per 128 x 128
 //       block.
 //   sgemm_tc<MODE, EPI, GROUPED, PAIR>: persistent; warp 0 issues TMA loads,
@@ -81,8 +87,9 @@ constexpr int FP8_BLOCK = 128;      // FP8 scale block (rows x K) of each operan
 // status bits (DeviceStatus word)
 constexpr int ST_PRODUCER = 1, ST_MMA = 2, ST_EPILOGUE = 4, ST_DRAIN = 8, ST_SELFTEST = 16, ST_CONFIG = 32;
 
-// Leaf modes: 3 = BF16x3 split (hi*hi + hi*lo + lo*hi), 1 = BF16, 8 = FP8
-// E4M3 with one FP32 scale per 128 x 128 block of each operand.
+// Leaf modes: 3 = BF16x3 split (hi*hi + hi*lo + lo*hi), 6 = BF16x6 (three
+// BF16 parts per operand, six products), 1 = BF16, 8 = FP8 E4M3 with one
+// FP32 scale per 128 x 128 block of each operand.
 // PAIR: two CTAs of a cluster share one 256 x 256 tile (tcgen05 cta_group::2):
 // each stages its own 128 rows of A and 128 of the tile's 256 rows of B, so
 // per CTA a stage holds a third less and the operand traffic from L2 and the
@@ -90,14 +97,17 @@ constexpr int ST_PRODUCER = 1, ST_MMA = 2, ST_EPILOGUE = 4, ST_DRAIN = 8, ST_SEL
 template <int MODE, bool PAIR = false>
 struct Cfg {
   static constexpr bool FP8 = MODE == 8;
-  static constexpr int PLANES = MODE == 3 ? 2 : 1;
+  static constexpr int PLANES = MODE == 3 ? 2 : MODE == 6 ? 3 : 1;
   static constexpr int ELEM_BYTES = FP8 ? 1 : 2;
   // One K slab row in shared memory: 128 bytes (128-byte swizzle), so a
   // slab carries 4 K steps and the per-slab handshake is paid once per 4.
   // BF16x3 on a single CTA (the batch) keeps 64-byte rows (64-byte swizzle):
   // its 4 planes of 384 rows would leave two 96 KiB stages; on a pair each
-  // CTA stages 256 rows and three 64 KiB stages fit.
-  static constexpr int ROW_BYTES = (MODE == 3 && !PAIR) ? 64 : 128;
+  // CTA stages 256 rows and three 64 KiB stages fit. BF16x6 (on pairs)
+  // takes 64-byte rows: six 128-row planes per stage in four 48 KiB stages,
+  // 2 K steps x 6 products = 12 MMAs per slab, as BF16x3 has per 128-byte
+  // slab.
+  static constexpr int ROW_BYTES = ((MODE == 3 && !PAIR) || MODE == 6) ? 64 : 128;
   static constexpr uint32_t A_SLAB = BM * ROW_BYTES;  // bytes of one A plane slab
   // Tile columns and tensor-memory buffers, and the split of a tile's
   // columns between the two epilogue warps of a lane quarter (multiples of
@@ -124,8 +134,11 @@ struct Cfg {
   // tensor-memory drains per K; longer chunks then wait on the TMA ring).
   // FP8: exactly one 128-element scale block, multiplied by its two block
   // scales when it is added. Plain BF16 (bound 1e-2) accumulates all of K
-  // in tensor memory: one chunk per tile, read out once.
-  static constexpr int KC_SLABS = MODE == 1 ? (1 << 24) : (MODE == 3 ? 192 : 128) / BK;
+  // in tensor memory: one chunk per tile, read out once. BF16x6: 96
+  // elements, 6 K steps x 6 products = 36 MMAs a chunk as BF16x3 has in 192
+  // (the truncation grows with the MMAs a chunk accumulates, and the drains
+  // per MMA stay as frequent).
+  static constexpr int KC_SLABS = MODE == 1 ? (1 << 24) : (MODE == 3 ? 192 : MODE == 6 ? 96 : 128) / BK;
   static constexpr uint32_t STAGE_BYTES = PLANES * (A_SLAB + B_SLAB);
   static constexpr int STAGES = (int)((SMEM_BUDGET - 1536) / STAGE_BYTES) > 8
                                     ? 8 : (int)((SMEM_BUDGET - 1536) / STAGE_BYTES);
@@ -133,6 +146,7 @@ struct Cfg {
   static_assert(2 * STAGES * 8 + 2 * NBUF * 8 + 8 <= 512, "barrier area");
   static_assert(MODE != 8 || KC_SLABS * BK == FP8_BLOCK, "FP8: one chunk per scale block");
   static_assert(MODE != 3 || KC_SLABS * BK == 192, "BF16x3: chunks of 192 K elements");
+  static_assert(MODE != 6 || (KC_SLABS * BK == 96 && PAIR), "BF16x6: chunks of 96 K elements, on pairs");
 };
 
 // Kept within 120 bytes: ptxas spills the epilogue of the plain leaf once
@@ -467,6 +481,20 @@ __device__ __forceinline__ void split_pair(float x, __nv_bfloat16& h, __nv_bfloa
   h = __float2bfloat16_rn(x);
   l = __float2bfloat16_rn(x - __bfloat162float(h));
 }
+// Three parts: x - hi is exact in FP32 (at most 16 significant bits), and so
+// is (x - hi) - mid (at most 8), which lo then holds exactly.
+__device__ __forceinline__ void split_three(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  const float r = x - __bfloat162float(h);
+  m = __float2bfloat16_rn(r);
+  l = __float2bfloat16_rn(r - __bfloat162float(m));
+}
+// NPROD: 1 = hi only, 3 = hi and lo, 6 = hi, mid (in lo) and lo (in lo2)
+template <int NPROD>
+__device__ __forceinline__ void split_elem(float x, __nv_bfloat16& h, __nv_bfloat16& l, __nv_bfloat16& l2) {
+  if constexpr (NPROD == 6) split_three(x, h, l, l2);
+  else split_pair(x, h, l);
+}
 
 // X "m-major": element (r, k) at X[r + k*ld] (rows contiguous). One TR x TK
 // tile (rows r0.., K k0..) per CTA of 256 threads, transposed through
@@ -475,7 +503,7 @@ __device__ __forceinline__ void split_pair(float x, __nv_bfloat16& h, __nv_bfloa
 template <int NPROD, int TR = 64, int TK = 64>
 __device__ __forceinline__ void split_tile_m(const float* __restrict__ X, int64_t ld, int rows, int K, int Kp,
                                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                                             int64_t r0, int64_t k0) {
+                                             __nv_bfloat16* __restrict__ lo2, int64_t r0, int64_t k0) {
   static_assert(TR % 32 == 0 && TK % 8 == 0 && (TR * TK) % 2048 == 0, "tile of whole warps and 8-K groups");
   constexpr int LOADS = TR * TK / 256, GROUPS = TR * TK / 8 / 256;
   __shared__ float t[TK][TR + 1];
@@ -503,10 +531,12 @@ __device__ __forceinline__ void split_tile_m(const float* __restrict__ X, int64_
     if (gr >= rows || gk >= Kp) continue;
     __align__(16) __nv_bfloat16 h[8];
     __align__(16) __nv_bfloat16 l[8];
+    __align__(16) __nv_bfloat16 l2[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) split_pair(t[kc + u][rr], h[u], l[u]);
+    for (int u = 0; u < 8; ++u) split_elem<NPROD>(t[kc + u][rr], h[u], l[u], l2[u]);
     *reinterpret_cast<uint4*>(hi + gr * Kp + gk) = *reinterpret_cast<const uint4*>(h);
-    if (NPROD == 3) *reinterpret_cast<uint4*>(lo + gr * Kp + gk) = *reinterpret_cast<const uint4*>(l);
+    if (NPROD >= 3) *reinterpret_cast<uint4*>(lo + gr * Kp + gk) = *reinterpret_cast<const uint4*>(l);
+    if (NPROD == 6) *reinterpret_cast<uint4*>(lo2 + gr * Kp + gk) = *reinterpret_cast<const uint4*>(l2);
   }
 }
 
@@ -515,7 +545,7 @@ __device__ __forceinline__ void split_tile_m(const float* __restrict__ X, int64_
 template <int NPROD>
 __device__ __forceinline__ void split_tile_k(const float* __restrict__ X, int64_t ld, int rows, int K, int Kp,
                                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                                             int64_t r0, int64_t k0) {
+                                             __nv_bfloat16* __restrict__ lo2, int64_t r0, int64_t k0) {
   // both passes' 16 loads in flight before the first conversion
   float v[2][8];
 #pragma unroll
@@ -533,10 +563,12 @@ __device__ __forceinline__ void split_tile_k(const float* __restrict__ X, int64_
     if (r >= rows || k >= Kp) continue;
     __align__(16) __nv_bfloat16 h[8];
     __align__(16) __nv_bfloat16 l[8];
+    __align__(16) __nv_bfloat16 l2[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) split_pair(v[it][u], h[u], l[u]);
+    for (int u = 0; u < 8; ++u) split_elem<NPROD>(v[it][u], h[u], l[u], l2[u]);
     *reinterpret_cast<uint4*>(hi + r * Kp + k) = *reinterpret_cast<const uint4*>(h);
-    if (NPROD == 3) *reinterpret_cast<uint4*>(lo + r * Kp + k) = *reinterpret_cast<const uint4*>(l);
+    if (NPROD >= 3) *reinterpret_cast<uint4*>(lo + r * Kp + k) = *reinterpret_cast<const uint4*>(l);
+    if (NPROD == 6) *reinterpret_cast<uint4*>(lo2 + r * Kp + k) = *reinterpret_cast<const uint4*>(l2);
   }
 }
 
@@ -550,8 +582,8 @@ constexpr int SPLIT_TR = 256, SPLIT_TK = 32;
 template <int NPROD>
 __global__ void __launch_bounds__(256) split_mmajor(const float* __restrict__ X, int64_t ld, int rows, int K,
                                                     int Kp, __nv_bfloat16* __restrict__ hi,
-                                                    __nv_bfloat16* __restrict__ lo) {
-  split_tile_m<NPROD, SPLIT_TR, SPLIT_TK>(X, ld, rows, K, Kp, hi, lo, (int64_t)blockIdx.x * SPLIT_TR,
+                                                    __nv_bfloat16* __restrict__ lo, __nv_bfloat16* __restrict__ lo2) {
+  split_tile_m<NPROD, SPLIT_TR, SPLIT_TK>(X, ld, rows, K, Kp, hi, lo, lo2, (int64_t)blockIdx.x * SPLIT_TR,
                                           (int64_t)blockIdx.y * SPLIT_TK);
 }
 
@@ -573,15 +605,15 @@ __global__ void __launch_bounds__(256) split_batch(const SplitOp* __restrict__ o
                                                    const SplitTile* __restrict__ tiles) {
   const SplitTile t = tiles[blockIdx.x];
   const SplitOp o = ops[t.op];
-  if (o.mmajor) split_tile_m<NPROD>(o.X, o.ld, o.rows, o.K, o.Kp, o.hi, o.lo, t.r0, t.k0);
-  else split_tile_k<NPROD>(o.X, o.ld, o.rows, o.K, o.Kp, o.hi, o.lo, t.r0, t.k0);
+  if (o.mmajor) split_tile_m<NPROD>(o.X, o.ld, o.rows, o.K, o.Kp, o.hi, o.lo, nullptr, t.r0, t.k0);
+  else split_tile_k<NPROD>(o.X, o.ld, o.rows, o.K, o.Kp, o.hi, o.lo, nullptr, t.r0, t.k0);
 }
 
 // X "k-major": element (r, k) at X[k + r*ld] (K contiguous).
 template <int NPROD>
 __global__ void __launch_bounds__(256) split_kmajor(const float* __restrict__ X, int64_t ld, int rows, int K,
                                                     int Kp, __nv_bfloat16* __restrict__ hi,
-                                                    __nv_bfloat16* __restrict__ lo) {
+                                                    __nv_bfloat16* __restrict__ lo, __nv_bfloat16* __restrict__ lo2) {
   const int64_t chunks = Kp / 8;
   const int64_t total = (int64_t)rows * chunks;
   for (int64_t task = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; task < total;
@@ -590,10 +622,12 @@ __global__ void __launch_bounds__(256) split_kmajor(const float* __restrict__ X,
     const float* src = X + r * ld + k;
     __align__(16) __nv_bfloat16 h[8];
     __align__(16) __nv_bfloat16 l[8];
+    __align__(16) __nv_bfloat16 l2[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) split_pair((k + u < K) ? src[u] : 0.f, h[u], l[u]);
+    for (int u = 0; u < 8; ++u) split_elem<NPROD>((k + u < K) ? src[u] : 0.f, h[u], l[u], l2[u]);
     *reinterpret_cast<uint4*>(hi + r * Kp + k) = *reinterpret_cast<const uint4*>(h);
-    if (NPROD == 3) *reinterpret_cast<uint4*>(lo + r * Kp + k) = *reinterpret_cast<const uint4*>(l);
+    if (NPROD >= 3) *reinterpret_cast<uint4*>(lo + r * Kp + k) = *reinterpret_cast<const uint4*>(l);
+    if (NPROD == 6) *reinterpret_cast<uint4*>(lo2 + r * Kp + k) = *reinterpret_cast<const uint4*>(l2);
   }
 }
 
@@ -761,7 +795,7 @@ struct GroupParams {
 
 // What one tile needs: its instance's operands and result, and where it sits.
 struct TileView {
-  const CUtensorMap* tm[4];
+  const CUtensorMap* tm[4];  // A hi, A lo, B hi, B lo (BF16x6's third planes: the kernel's tmA_lo2, tmB_lo2)
   float* C;
   int64_t ldc;
   int M, N, K, bn, m0, n0;
@@ -786,13 +820,15 @@ template <int MODE, int EPI, bool GROUPED, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1)
     sgemm_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+             const __grid_constant__ CUtensorMap tmA_lo2, const __grid_constant__ CUtensorMap tmB_lo2,
              TcParams p, GroupParams gp) {
   static_assert(!(GROUPED && PAIR), "batches run on single CTAs");
+  static_assert(MODE != 6 || (!GROUPED && EPI == 0), "BF16x6: single instances, plain epilogue");
   using C_ = Cfg<MODE, PAIR>;
   constexpr int CG = PAIR ? 2 : 1;
   constexpr int TM = PAIR ? 2 * BM : BM;  // tile rows (one CTA, or the pair)
   constexpr int S = C_::STAGES;
-  constexpr int NPROD = MODE == 3 ? 3 : 1;
+  constexpr int NPROD = MODE == 3 ? 3 : MODE == 6 ? 6 : 1;
   constexpr int BK = C_::BK, MMA_K = C_::MMA_K, KC_SLABS = C_::KC_SLABS;
   if (PAIR && cluster_nctarank() != 2) {
     // launched without its cluster: nothing was set up yet, so just report
@@ -894,11 +930,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     return v;
   };
 
-  // stage s: [A hi][A lo][B hi][B lo] (lo planes only for NPROD == 3)
-  auto a_hi = [&](int s) { return smem + s * C_::STAGE_BYTES; };
-  auto a_lo = [&](int s) { return smem + s * C_::STAGE_BYTES + C_::A_SLAB; };
-  auto b_hi = [&](int s) { return smem + s * C_::STAGE_BYTES + C_::PLANES * C_::A_SLAB; };
-  auto b_lo = [&](int s) { return smem + s * C_::STAGE_BYTES + C_::PLANES * C_::A_SLAB + C_::B_SLAB; };
+  // stage s: the PLANES planes of A, then those of B ([A hi][A lo][A lo2]
+  // [B hi][B lo][B lo2]; lo planes for NPROD 3 and 6, lo2 for 6)
+  auto a_pl = [&](int s, int i) { return smem + s * C_::STAGE_BYTES + i * C_::A_SLAB; };
+  auto b_pl = [&](int s, int i) { return smem + s * C_::STAGE_BYTES + C_::PLANES * C_::A_SLAB + i * C_::B_SLAB; };
+  auto a_hi = [&](int s) { return a_pl(s, 0); };
+  auto b_hi = [&](int s) { return b_pl(s, 0); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -973,15 +1010,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (leader) mbar_expect_tx(&full[s], 2 * bytes);
             const uint32_t bar = mapa_rank(smem_u32(&full[s]), 0);
             tma_load_2d_pair(v.tm[0], bar, a_hi(s), k, ma);
-            if (NPROD == 3) tma_load_2d_pair(v.tm[1], bar, a_lo(s), k, ma);
+            if (NPROD >= 3) tma_load_2d_pair(v.tm[1], bar, a_pl(s, 1), k, ma);
+            if constexpr (NPROD == 6) tma_load_2d_pair(&tmA_lo2, bar, a_pl(s, 2), k, ma);
             tma_load_2d_pair(v.tm[2], bar, b_hi(s), k, nb);
-            if (NPROD == 3) tma_load_2d_pair(v.tm[3], bar, b_lo(s), k, nb);
+            if (NPROD >= 3) tma_load_2d_pair(v.tm[3], bar, b_pl(s, 1), k, nb);
+            if constexpr (NPROD == 6) tma_load_2d_pair(&tmB_lo2, bar, b_pl(s, 2), k, nb);
           } else {
             mbar_expect_tx(&full[s], bytes);
             tma_load_2d(v.tm[0], &full[s], a_hi(s), k, ma);
-            if (NPROD == 3) tma_load_2d(v.tm[1], &full[s], a_lo(s), k, ma);
+            if (NPROD >= 3) tma_load_2d(v.tm[1], &full[s], a_pl(s, 1), k, ma);
+            if constexpr (NPROD == 6) tma_load_2d(&tmA_lo2, &full[s], a_pl(s, 2), k, ma);
             tma_load_2d(v.tm[2], &full[s], b_hi(s), k, nb);
-            if (NPROD == 3) tma_load_2d(v.tm[3], &full[s], b_lo(s), k, nb);
+            if (NPROD >= 3) tma_load_2d(v.tm[3], &full[s], b_pl(s, 1), k, nb);
+            if constexpr (NPROD == 6) tma_load_2d(&tmB_lo2, &full[s], b_pl(s, 2), k, nb);
           }
           issued = it + 1;
         }
@@ -1027,8 +1068,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t ah = smem_u32(a_hi(s)), al = smem_u32(a_lo(s));
-            const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_lo(s));
+            const uint32_t ah = smem_u32(a_hi(s)), al = smem_u32(a_pl(s, 1));
+            const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_pl(s, 1));
 #pragma unroll
             for (int kk = 0; kk < BK / MMA_K; ++kk) {
               const uint32_t off = kk * MMA_K * C_::ELEM_BYTES;  // bytes along the slab row
@@ -1038,6 +1079,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                 umma_e4m3<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, acc);
               } else if (NPROD == 3) {
                 umma_bf16<CG>(dst, sdesc_k<RB>(al + off), sdesc_k<RB>(bh + off), idesc, acc);
+                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bl + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, 1u);
+              } else if constexpr (NPROD == 6) {
+                const uint32_t al2 = smem_u32(a_pl(s, 2)), bl2 = smem_u32(b_pl(s, 2));
+                // smallest first: lo*hi, hi*lo, mid*mid (2^-17 of hi*hi),
+                // mid*hi, hi*mid (2^-9), hi*hi (the lo planes hold mid, the
+                // lo2 planes lo)
+                umma_bf16<CG>(dst, sdesc_k<RB>(al2 + off), sdesc_k<RB>(bh + off), idesc, acc);
+                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bl2 + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_k<RB>(al + off), sdesc_k<RB>(bl + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_k<RB>(al + off), sdesc_k<RB>(bh + off), idesc, 1u);
                 umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bl + off), idesc, 1u);
                 umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, 1u);
               } else {
@@ -1461,13 +1513,14 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // and epilogue warps every 128 K, runs 3% slower on pairs (2.2x slower
 // when the peer released buffers with a cluster-scope release). So BF16
 // and BF16x3 run on pairs, FP8 on single CTAs.
-constexpr bool pair_for_mode(int mode) { return mode == 1 || mode == 3; }
+constexpr bool pair_for_mode(int mode) { return mode == 1 || mode == 3 || mode == 6; }
 
 // Workspace layout of a mode: operand planes (and FP8 block scales), then
 // the tail split's region where the pairs' tiles call for one.
 struct WsLayout {
   int64_t Kp = 0;  // row stride of the planes, in elements (16-byte rows)
   size_t a_hi = 0, a_lo = 0, b_hi = 0, b_lo = 0, sa = 0, sb = 0, total = 0;
+  size_t a_lo2 = 0, b_lo2 = 0;  // BF16x6: the third parts
   int nkb = 0;     // FP8: scale blocks along K
   size_t planes = 0;                   // end of the planes: the least a launch needs
   size_t split = 0, split_bytes = 0;   // the tail split's partial sums and counters
@@ -1488,9 +1541,11 @@ WsLayout ws_layout(const SgemmDesc& d, int mode) {
   const size_t ap = align256((size_t)d.M * L.Kp * eb), bp = align256((size_t)d.N * L.Kp * eb);
   size_t off = 0;
   L.a_hi = off; off += ap;
-  if (mode == 3) { L.a_lo = off; off += ap; }
+  if (mode == 3 || mode == 6) { L.a_lo = off; off += ap; }
+  if (mode == 6) { L.a_lo2 = off; off += ap; }
   L.b_hi = off; off += bp;
-  if (mode == 3) { L.b_lo = off; off += bp; }
+  if (mode == 3 || mode == 6) { L.b_lo = off; off += bp; }
+  if (mode == 6) { L.b_lo2 = off; off += bp; }
   if (mode == 8) {
     L.nkb = (int)((d.K + FP8_BLOCK - 1) / FP8_BLOCK);
     L.sa = off; off += align256((size_t)((d.M + FP8_BLOCK - 1) / FP8_BLOCK) * L.nkb * 4);
@@ -1500,9 +1555,11 @@ WsLayout ws_layout(const SgemmDesc& d, int mode) {
   if (pair_for_mode(mode)) {
     // the tail split's region, for the pairs the GPU runs at once
     using P = Cfg<1, true>;
-    static_assert(Cfg<3, true>::BK == P::BK && Cfg<3, true>::ACC == P::ACC, "one split layout for both tiers");
+    static_assert(Cfg<3, true>::BK == P::BK && Cfg<3, true>::ACC == P::ACC && Cfg<6, true>::ACC == P::ACC,
+                  "one split layout for the pair tiers");
+    const int bk = mode == 6 ? Cfg<6, true>::BK : P::BK;  // the K slab the leaf counts in
     const int64_t tiles = ((d.M + 2 * BM - 1) / (2 * BM)) * ((d.N + P::TN - 1) / P::TN);
-    const int n = tiles <= INT32_MAX ? tail_split_tiles((int)tiles, num_sms() / 2, (int)((d.K + P::BK - 1) / P::BK)) : 0;
+    const int n = tiles <= INT32_MAX ? tail_split_tiles((int)tiles, num_sms() / 2, (int)((d.K + bk - 1) / bk)) : 0;
     if (n > 0) {
       L.split = off;
       L.split_bytes = split_region_bytes(n, 2, P::ACC);
@@ -1521,8 +1578,12 @@ OperandLayout operand_layout(int64_t rows, int64_t K, int mode) {
   const int64_t Kp = (K + 16 / eb - 1) / (16 / eb) * (16 / eb);
   const size_t plane = align256((size_t)rows * Kp * eb);
   size_t off = plane;
-  if (mode == 3) {
+  if (mode == 3 || mode == 6) {
     L.lo = off;
+    off += plane;
+  }
+  if (mode == 6) {
+    L.lo2 = off;
     off += plane;
   }
   if (mode == 8) {
@@ -1535,16 +1596,16 @@ OperandLayout operand_layout(int64_t rows, int64_t K, int mode) {
 
 template <int NPROD>
 cudaError_t launch_split(const float* X, int64_t ld, bool mmajor, int rows, int K, int Kp,
-                         __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
+                         __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2, cudaStream_t s) {
   if (rows == 0 || K == 0) return cudaSuccess;
   if (mmajor) {
     dim3 grid((rows + SPLIT_TR - 1) / SPLIT_TR, (Kp + SPLIT_TK - 1) / SPLIT_TK);
-    split_mmajor<NPROD><<<grid, 256, 0, s>>>(X, ld, rows, K, Kp, hi, lo);
+    split_mmajor<NPROD><<<grid, 256, 0, s>>>(X, ld, rows, K, Kp, hi, lo, lo2);
   } else {
     int64_t tasks = (int64_t)rows * (Kp / 8);
     int64_t blocks = (tasks + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    split_kmajor<NPROD><<<(unsigned)blocks, 256, 0, s>>>(X, ld, rows, K, Kp, hi, lo);
+    split_kmajor<NPROD><<<(unsigned)blocks, 256, 0, s>>>(X, ld, rows, K, Kp, hi, lo, lo2);
   }
   return cudaGetLastError();
 }
@@ -1619,7 +1680,7 @@ cudaError_t launch_leaf(const CUtensorMap* maps, TcParams prm, int tiles, size_t
     cudaError_t e = tail_setup<MODE, EPI, PAIR>(prm, tiles, grid, split_cap, split_as, s);
     if (e != cudaSuccess) return e;
     hook_begin(hooks, s);
-    kernel<<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], prm,
+    kernel<<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], prm,
                                                   GroupParams{nullptr, nullptr, 0});
     e = cudaGetLastError();
     hook_end(hooks, s);
@@ -1656,7 +1717,8 @@ cudaError_t launch_leaf(const CUtensorMap* maps, TcParams prm, int tiles, size_t
   cudaError_t e = tail_setup<MODE, EPI, PAIR>(prm, tiles, clusters, split_cap, split_as, s);
   if (e != cudaSuccess) return e;
   hook_begin(hooks, s);
-  e = cudaLaunchKernelEx(&cfg, kernel, maps[0], maps[1], maps[2], maps[3], prm, GroupParams{nullptr, nullptr, 0});
+  e = cudaLaunchKernelEx(&cfg, kernel, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], prm,
+                         GroupParams{nullptr, nullptr, 0});
   hook_end(hooks, s);
   return e;
 }
@@ -1668,8 +1730,12 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
   constexpr bool PAIR = pair_for_mode(MODE);
   constexpr int TM = PAIR ? 2 * BM : BM;
   using C_ = Cfg<MODE, PAIR>;
-  constexpr int NPROD = MODE == 3 ? 3 : 1;
+  constexpr int NPROD = MODE == 3 ? 3 : MODE == 6 ? 6 : 1;
   const int M = (int)d.M, N = (int)d.N, K = (int)d.K;
+  if (MODE == 6 && (epi.kind != 0 || epi.fwd || epi.rows)) {
+    *err = "the BF16X6 tier runs the plain sgemm leaf (no merged elementwise leaf, no forwarded planes)";
+    return cudaErrorInvalidValue;
+  }
   const WsLayout L = ws_layout(d, MODE);
   const int Kp = (int)L.Kp;
   uint8_t* w = static_cast<uint8_t*>(ws);
@@ -1677,6 +1743,8 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
   void* al = w + L.a_lo;
   void* bh = w + L.b_hi;
   void* bl = w + L.b_lo;
+  void* al2 = w + L.a_lo2;
+  void* bl2 = w + L.b_lo2;
   float* sa = reinterpret_cast<float*>(w + L.sa);
   float* sb = reinterpret_cast<float*>(w + L.sb);
   if (pa.base) {  // op(A)'s planes live in the plane cache
@@ -1684,6 +1752,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
     uint8_t* b = static_cast<uint8_t*>(pa.base);
     ah = b + O.hi;
     al = b + O.lo;
+    al2 = b + O.lo2;
     sa = reinterpret_cast<float*>(b + O.scales);
   }
   if (pb.base) {
@@ -1691,6 +1760,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
     uint8_t* b = static_cast<uint8_t*>(pb.base);
     bh = b + O.hi;
     bl = b + O.lo;
+    bl2 = b + O.lo2;
     sb = reinterpret_cast<float*>(b + O.scales);
   }
   int kernels = 0;
@@ -1702,7 +1772,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
         e = launch_quant(d.A, d.lda, !d.transA, M, K, Kp, static_cast<uint8_t*>(ah), sa, L.nkb, s);
       else
         e = launch_split<NPROD>(d.A, d.lda, !d.transA, M, K, Kp, static_cast<__nv_bfloat16*>(ah),
-                                static_cast<__nv_bfloat16*>(al), s);
+                                static_cast<__nv_bfloat16*>(al), static_cast<__nv_bfloat16*>(al2), s);
       if (e != cudaSuccess) return e;
       if (pa.converted) cudaEventRecord(pa.converted, s);
       kernels += 1;
@@ -1712,26 +1782,35 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
         e = launch_quant(d.B, d.ldb, d.transB != 0, N, K, Kp, static_cast<uint8_t*>(bh), sb, L.nkb, s);
       else
         e = launch_split<NPROD>(d.B, d.ldb, d.transB != 0, N, K, Kp, static_cast<__nv_bfloat16*>(bh),
-                                static_cast<__nv_bfloat16*>(bl), s);
+                                static_cast<__nv_bfloat16*>(bl), static_cast<__nv_bfloat16*>(bl2), s);
       if (e != cudaSuccess) return e;
       if (pb.converted) cudaEventRecord(pb.converted, s);
       kernels += 1;
     }
   }
-  alignas(64) CUtensorMap maps[4];
+  // A hi, A lo, B hi, B lo, A lo2, B lo2 (planes a mode does not have repeat hi)
+  alignas(64) CUtensorMap maps[6];
   memset(maps, 0, sizeof maps);
   if (K > 0) {
     // a CTA loads 128 rows of A and B_ROWS of B (PAIR: 128 of the tile's 256)
     if (!encode_plane(&maps[0], ah, M, K, Kp, BM, C_::ELEM_BYTES, C_::ROW_BYTES, err) ||
         !encode_plane(&maps[2], bh, N, K, Kp, C_::B_ROWS, C_::ELEM_BYTES, C_::ROW_BYTES, err))
       return cudaErrorInvalidValue;
-    if (NPROD == 3) {
+    if (NPROD >= 3) {
       if (!encode_plane(&maps[1], al, M, K, Kp, BM, 2, C_::ROW_BYTES, err) ||
           !encode_plane(&maps[3], bl, N, K, Kp, C_::B_ROWS, 2, C_::ROW_BYTES, err))
         return cudaErrorInvalidValue;
     } else {
       maps[1] = maps[0];
       maps[3] = maps[2];
+    }
+    if (NPROD == 6) {
+      if (!encode_plane(&maps[4], al2, M, K, Kp, BM, 2, C_::ROW_BYTES, err) ||
+          !encode_plane(&maps[5], bl2, N, K, Kp, C_::B_ROWS, 2, C_::ROW_BYTES, err))
+        return cudaErrorInvalidValue;
+    } else {
+      maps[4] = maps[0];
+      maps[5] = maps[2];
     }
   }
   TcParams prm{M, N, K, 0, d.C, d.ldc, d.alpha, d.beta, sa, sb, L.nkb, 0, st.dev, epi.aux, epi.ldaux,
@@ -1762,9 +1841,13 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
   }
   int grid_ctas = 0;
   const int sa_ = epi.split_as;
-  if (epi.kind == 1) e = launch_leaf<MODE, 1, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
-  else if (epi.kind == 2) e = launch_leaf<MODE, 2, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
-  else e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
+  if constexpr (MODE == 6) {
+    e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
+  } else {
+    if (epi.kind == 1) e = launch_leaf<MODE, 1, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
+    else if (epi.kind == 2) e = launch_leaf<MODE, 2, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
+    else e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
+  }
   if (e != cudaSuccess) return e;
   kernels += 1;
   if (rep) {
@@ -1779,7 +1862,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
   return cudaSuccess;
 }
 
-int mode_of_tier(int tier) { return tier == 2 ? 3 : tier == 4 ? 8 : 1; }
+int mode_of_tier(int tier) { return tier == 2 ? 3 : tier == 4 ? 8 : tier == 5 ? 6 : 1; }
 
 // ---- batches of independent instances ----------------------------------------
 template <int MODE>
@@ -1794,14 +1877,15 @@ cudaError_t launch_batch_kernels(const TcBatch& b, const DeviceStatus& st, cudaS
     if (e != cudaSuccess) return e;
   }
   if (b.num_tiles == 0) return cudaSuccess;
-  alignas(64) CUtensorMap unused[4];
+  alignas(64) CUtensorMap unused[6];
   memset(unused, 0, sizeof unused);
   TcParams prm{};
   prm.status = st.dev;
   GroupParams gp{static_cast<const GroupInst*>(b.d_insts), static_cast<const GroupTile*>(b.d_tiles), b.num_tiles};
   hook_begin(hooks, s);
   sgemm_tc<MODE, 0, true, false>
-      <<<b.grid, THREADS, C_::SMEM_BYTES, s>>>(unused[0], unused[1], unused[2], unused[3], prm, gp);
+      <<<b.grid, THREADS, C_::SMEM_BYTES, s>>>(unused[0], unused[1], unused[2], unused[3], unused[4], unused[5], prm,
+                                               gp);
   hook_end(hooks, s);
   return cudaGetLastError();
 }
@@ -2102,6 +2186,7 @@ cudaError_t launch_tc(const SgemmDesc& d, int tier, void* ws, size_t ws_bytes, c
   }
   if (tier == 2) return run_tc<3>(d, ws, ws_bytes, st, s, rep, err, hooks, epi, pa, pb);
   if (tier == 4) return run_tc<8>(d, ws, ws_bytes, st, s, rep, err, hooks, epi, pa, pb);
+  if (tier == 5) return run_tc<6>(d, ws, ws_bytes, st, s, rep, err, hooks, epi, pa, pb);
   return run_tc<1>(d, ws, ws_bytes, st, s, rep, err, hooks, epi, pa, pb);
 }
 
@@ -2247,9 +2332,27 @@ extern "C" int hpvm_split_bf16(const float* X, int64_t ld, int kcontig, int64_t 
   const int Kp = (int)((K + 7) / 8 * 8);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = lo ? launch_split<3>(X, ld, !kcontig, (int)rows, (int)K, Kp, static_cast<__nv_bfloat16*>(hi),
-                                       static_cast<__nv_bfloat16*>(lo), s)
+                                       static_cast<__nv_bfloat16*>(lo), nullptr, s)
                      : launch_split<1>(X, ld, !kcontig, (int)rows, (int)K, Kp, static_cast<__nv_bfloat16*>(hi),
-                                       nullptr, s);
+                                       nullptr, nullptr, s);
+  if (e != cudaSuccess) return set_last_error(HPVM_ERR_CUDA, cudaGetErrorString(e));
+  return set_last_error(HPVM_OK, "");
+}
+
+extern "C" int hpvm_split3_bf16(const float* X, int64_t ld, int kcontig, int64_t rows, int64_t K, void* hi,
+                                void* mid, void* lo, void* cuda_stream) {
+  using namespace hpvm;
+  if (rows < 0 || K < 0 || rows > INT32_MAX / 2 || K > INT32_MAX / 2)
+    return set_last_error(HPVM_ERR_SHAPE, "rows and K must be in [0, 2^30)");
+  if (rows == 0 || K == 0) return set_last_error(HPVM_OK, "");
+  if (!X || !hi || !mid || !lo) return set_last_error(HPVM_ERR_INVALID_ARG, "X, hi, mid or lo is NULL");
+  if (ld < (kcontig ? K : rows)) return set_last_error(HPVM_ERR_SHAPE, "ld is smaller than the contiguous extent");
+  if ((reinterpret_cast<uintptr_t>(hi) | reinterpret_cast<uintptr_t>(mid) | reinterpret_cast<uintptr_t>(lo)) & 15u)
+    return set_last_error(HPVM_ERR_ALIGN, "hi, mid and lo must be 16-byte aligned");
+  const int Kp = (int)((K + 7) / 8 * 8);
+  cudaError_t e = launch_split<6>(X, ld, !kcontig, (int)rows, (int)K, Kp, static_cast<__nv_bfloat16*>(hi),
+                                  static_cast<__nv_bfloat16*>(mid), static_cast<__nv_bfloat16*>(lo),
+                                  static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return set_last_error(HPVM_ERR_CUDA, cudaGetErrorString(e));
   return set_last_error(HPVM_OK, "");
 }

@@ -97,3 +97,32 @@ def test_block_quant():
                 big = np.abs(cb) >= 2.0 ** -6
                 rel = np.abs(rec - blk)[big] / np.abs(blk)[big]
                 assert rel.max() <= 2.0 ** -4 * (1 + 1e-6)
+
+
+def test_split3_properties():
+    g = torch.Generator().manual_seed(4)
+    # magnitudes over 2^-100 .. 2^100 (far from BF16's subnormal range)
+    x = (torch.randn(200000, generator=g) *
+         torch.exp2(torch.randint(-100, 100, (200000,), generator=g).float())).numpy()
+    hi, mid, lo = Q.split3_bf16(x)
+    for t in (hi, mid, lo):
+        assert not (t.view(np.uint32) & 0xFFFF).any()  # BF16 values
+    # the three parts carry x exactly: 8 + 8 + 8 significant bits with
+    # nearest rounding cover FP32's 24
+    total = hi.astype(np.float64) + mid.astype(np.float64) + lo.astype(np.float64)
+    assert np.array_equal(total, x.astype(np.float64))
+    # hi is the BF16 rounding of x (PyTorch's cast), mid is at most half an
+    # ulp of hi, lo at most half an ulp of mid
+    assert np.array_equal(hi, torch.from_numpy(x).to(torch.bfloat16).float().numpy())
+    assert (np.abs(mid) <= 2.0 ** -8 * np.abs(hi)).all()
+    assert (np.abs(lo) <= 2.0 ** -8 * np.abs(mid)).all()
+    # the first two parts are the two-term split
+    h2, l2 = Q.split_bf16(x)
+    assert np.array_equal(h2, hi) and np.array_equal(l2, mid)
+    # values with at most 8 (16) significant bits need one (two) parts
+    b = Q.bf16_rn(x)
+    hb, mb, lb = Q.split3_bf16(b)
+    assert np.array_equal(hb, b) and not mb.any() and not lb.any()
+    c = (x.view(np.uint32) & np.uint32(0xFFFFFF00)).view(np.float32)  # 16 bits
+    hc, mc, lc = Q.split3_bf16(c)
+    assert not lc.any() and np.array_equal(hc.astype(np.float64) + mc, c.astype(np.float64))

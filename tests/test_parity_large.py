@@ -18,7 +18,8 @@ from paper_1611_00860_gb300.sgemm import SgemmDFG
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 N = 8192
-TOL = {H.HPVM_TIER_FP32: 5e-6, H.HPVM_TIER_BF16X3: 5e-6, H.HPVM_TIER_BF16: 1e-2}
+TOL = {H.HPVM_TIER_FP32: 5e-6, H.HPVM_TIER_BF16X3: 5e-6, H.HPVM_TIER_BF16: 1e-2,
+       H.HPVM_TIER_BF16X6: 5e-6}
 
 
 @pytest.fixture(scope="module")
