@@ -70,3 +70,23 @@ def test_lognormal_rows_need_three_parts():
     e6 = O.normwise_rel_err(S.split_block_f64(p, 0, 0, 256, 256, "bf16x6"), ref)
     assert e3 > 5e-6, e3
     assert e6 <= 5e-8, e6
+
+
+def test_small_products_can_exceed_the_bound_in_exact_arithmetic():
+    # A 24 x 16 product with K = 16 (the chain's small copy): 384 outputs of
+    # 16-term dot products. The normwise error of BF16x3's three products is
+    # about 4.4e-6 on average but spreads with so few terms: over 400 seeded
+    # N(0,1) draws it exceeds 5e-6 in several; at 128 x 128 with K = 128 it
+    # stays near 4.4e-6.
+    def err(a, b):
+        ah, al = (t.astype(np.float64) for t in Q.split_bf16(a))
+        bh, bl = (t.astype(np.float64) for t in Q.split_bf16(b))
+        ex = a.astype(np.float64) @ b.astype(np.float64).T
+        return np.linalg.norm(ah @ bh.T + ah @ bl.T + al @ bh.T - ex) / np.linalg.norm(ex)
+    rng = np.random.default_rng(9)
+    small = [err(rng.standard_normal((24, 16)).astype(np.float32),
+                 (rng.standard_normal((16, 16)) / 4).astype(np.float32)) for _ in range(400)]
+    assert np.median(small) < 5e-6 and sum(e > 5e-6 for e in small) >= 5
+    big = [err(rng.standard_normal((128, 128)).astype(np.float32),
+               (rng.standard_normal((128, 128)) / np.sqrt(128)).astype(np.float32)) for _ in range(10)]
+    assert max(big) < 4.8e-6
