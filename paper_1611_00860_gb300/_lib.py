@@ -54,6 +54,7 @@ HPVM_LAUNCH_CACHE_B = 16
 HPVM_LAUNCH_REUSE_B = 32
 HPVM_LAUNCH_CACHE_C = 64
 HPVM_LAUNCH_PLANES_ONLY = 128
+HPVM_LAUNCH_SEPARATE_SPLIT = 256
 HPVM_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 HPVM_ROOTIN_PAPER_BYTES = 88
 HPVM_SGEMM_ROOT_ARGS_BYTES = 136

@@ -77,6 +77,9 @@ struct Epilogue {
   void* rows = nullptr;
   int split_as = -1;
   bool planes_only = false;  // store the planes above only, not C itself
+  // run the operand split as its own kernels even where the BF16x3 leaf
+  // would write the planes itself (the same planes, bit for bit)
+  bool separate_split = false;
 };
 // Standalone elementwise kernel on the M x N column-major C (fp32_leaf.cu).
 cudaError_t launch_elementwise(const SgemmDesc& d, const Epilogue& e, cudaStream_t s);

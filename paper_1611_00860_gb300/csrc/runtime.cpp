@@ -1037,6 +1037,7 @@ int execute_plan(hpvm_ctx* ctx, const Plan& P, cudaStream_t s, void* ws, size_t 
         S.epi.planes_only = true;
       hpvm::Epilogue none;
       none.split_as = S.epi.kind;  // unmerged: split the tail as the merged leaf would
+      S.epi.separate_split = none.separate_split = (flags & HPVM_LAUNCH_SEPARATE_SPLIT) != 0;
       cudaError_t e;
       switch (tier) {
         case HPVM_TIER_FP32_DFG:

@@ -71,7 +71,7 @@ constexpr int THREADS = EPI_WARP0 * 32 + EPI_WARPS * 32;  // 3 warpgroups
 constexpr int LAUNCH_REGS = 168;
 // The split per leaf variant: ptxas's spills (-Xptxas -v) for 40/232 and
 // 48/224 differ by variant, and each takes the one that spills least.
-template <int MODE, int EPI, bool PAIR>
+template <int MODE, int EPI, bool PAIR, bool CONVERT = false>
 struct RegSplit {
   static constexpr int EPI_R = (MODE == 8 || (MODE == 3 && EPI == 2)) ? 224 : 232;
   static constexpr int CTRL_R = EPI_R == 224 ? 48 : 40;
@@ -85,7 +85,8 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per bounded wait
 constexpr int FP8_BLOCK = 128;      // FP8 scale block (rows x K) of each operand
 
 // status bits (DeviceStatus word)
-constexpr int ST_PRODUCER = 1, ST_MMA = 2, ST_EPILOGUE = 4, ST_DRAIN = 8, ST_SELFTEST = 16, ST_CONFIG = 32;
+constexpr int ST_PRODUCER = 1, ST_MMA = 2, ST_EPILOGUE = 4, ST_DRAIN = 8, ST_SELFTEST = 16, ST_CONFIG = 32,
+              ST_CONVERT = 64;
 
 // Leaf modes: 3 = BF16x3 split (hi*hi + hi*lo + lo*hi), 6 = BF16x6 (three
 // BF16 parts per operand, six products), 1 = BF16, 8 = FP8 E4M3 with one
@@ -182,6 +183,39 @@ struct TcParams {
   int planes_only;
 };
 
+// In-leaf operand conversion (the BF16x3 leaf on pairs, op(A) and op(B)^T
+// with their rows contiguous, as in the example's NT form): instead of two
+// split launches before the leaf, the leaf's two idle control warps write
+// the split planes. The operands are cut into chunks of 128 rows (one CTA's
+// share of a pair tile) by one 64-element K slab; the warps of all CTAs
+// take chunks from a global counter in the order the tiles first need them
+// (the rounds of the grouped tile order; within a round, slab by slab
+// across the round's row blocks), stage each chunk's FP32 values through
+// shared memory in four TMA pieces of 32 rows, write the hi and lo planes,
+// and release a per-chunk flag. The producer acquires the flags of the two
+// chunks a slab reads before its TMA loads. Chunks are claimed only by
+// running CTAs and converting one waits on nothing else, so every claimed
+// chunk is finished; all waits are bounded.
+constexpr int CV_ROWS = 128;    // rows of a chunk
+constexpr int CV_BK = 64;       // K elements of a chunk (the leaf's slab)
+constexpr int CV_PIECE = 32;    // rows of a staged piece
+constexpr int CV_PIECES = CV_ROWS / CV_PIECE;
+constexpr uint32_t CV_PIECE_BYTES = CV_PIECE * CV_BK * 4;  // 8 KiB of FP32
+constexpr int CV_WARPS = 2;     // warps 2 and 3
+constexpr int CV_MAX_ROUNDS = 64;
+constexpr int CV_TAB = 5;       // per round: A blocks [lo, hi), B blocks [lo, hi), first chunk
+constexpr uint32_t CV_SMEM = CV_WARPS * 2 * CV_PIECE_BYTES + (CV_MAX_ROUNDS + 1) * CV_TAB * 4;
+struct ConvParams {
+  CUtensorMap src[2];  // FP32 op(A) and op(B)^T, rows contiguous: box of 32 rows x 64 K
+  __nv_bfloat16* hi[2];
+  __nv_bfloat16* lo[2];
+  int* flags;          // one per chunk: A's (block * num_kb + slab), then B's
+  int* claim;          // the next chunk to convert
+  int rows[2];         // M, N
+  int blocks[2];       // ceil(rows / 128)
+  int Kp, num_kb;
+};
+
 // ---- PTX helpers -----------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -246,6 +280,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
         if (peer_abort) st_cluster_u32(peer_abort, 1);
         return false;
       }
+    }
+  }
+}
+// The same bounded wait for a whole warp, with one outcome for every lane:
+// all lanes poll the barrier, and lane 0 alone decides to give up (abort
+// raised, or the limit passed), so the warp never splits between the two
+// outcomes.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                               int* status, int code) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t n = 1;; ++n) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    if ((n & 63u) == 0) {
+      int give_up = 0;
+      if (lane == 0) {
+        if (*abort_flag) {
+          give_up = 1;
+        } else if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+          if (status) atomicOr_system(status, code);
+          *abort_flag = 1;
+          give_up = 1;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, give_up, 0)) return false;
     }
   }
 }
@@ -762,6 +821,151 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Wait until *flag is nonzero (a chunk of planes written by a converter
+// warp), bounded as mbar_wait is; then order the TMA loads that follow
+// after the converter's writes.
+__device__ __forceinline__ bool flag_wait(const int* flag, volatile int* abort_flag, int* status, int code,
+                                          uint32_t peer_abort) {
+  if (ld_acquire_gpu(flag) == 0) {
+    const uint64_t t0 = globaltimer();
+    for (uint32_t n = 1;; ++n) {
+      if (ld_acquire_gpu(flag) != 0) break;
+      if ((n & 15u) == 0) {
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+          if (status) atomicOr_system(status, code);
+          *abort_flag = 1;
+          if (peer_abort) st_cluster_u32(peer_abort, 1);
+          return false;
+        }
+      }
+    }
+  }
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  return true;
+}
+
+// One converter warp of the in-leaf conversion (see ConvParams). tab: the
+// round table (R at [CV_MAX_ROUNDS * CV_TAB], round r's A blocks [lo, hi),
+// B blocks [lo, hi) and first chunk at [r * CV_TAB ...], the chunk total at
+// [R * CV_TAB + 4]); bar, buf: this warp's two piece barriers and staging
+// buffers. Claims chunks until none is left or the kernel aborts.
+__device__ __forceinline__ void cv_convert(const ConvParams& cv, const int* tab, uint64_t* bar, uint8_t* buf,
+                                        int lane, volatile int* abort_flag, int* status) {
+  const int R = tab[CV_MAX_ROUNDS * CV_TAB];
+  const int total = tab[R * CV_TAB + 4];
+  int r = 0;  // round cursor (a warp's claims only increase)
+  struct Piece {
+    int op, blk, kb, j;
+  };
+  // claim a chunk (lane 0; the whole warp gets it) and place its first piece
+  auto next_chunk = [&](Piece& q) -> bool {
+    int c = total;
+    if (lane == 0 && !*abort_flag) c = atomicAdd(cv.claim, 1);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= total) return false;
+    while (r + 1 < R && c >= tab[(r + 1) * CV_TAB + 4]) ++r;
+    const int* e = tab + r * CV_TAB;
+    const int na = e[1] - e[0], n = na + (e[3] - e[2]);
+    const int i = c - e[4];
+    const int b = i % n;
+    q.kb = i / n;
+    q.op = b < na ? 0 : 1;
+    q.blk = q.op ? e[2] + (b - na) : e[0] + b;
+    q.j = 0;
+    return true;
+  };
+  // TMA load of a piece (32 rows x 64 K of FP32) into buffer b; every
+  // lane's reads of that buffer are complete (the caller syncs the warp)
+  auto issue = [&](const Piece& q, int b) {
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar[b], CV_PIECE_BYTES);
+      tma_load_2d(&cv.src[q.op], &bar[b], buf + b * CV_PIECE_BYTES, q.blk * CV_ROWS + q.j * CV_PIECE,
+                  q.kb * CV_BK);
+    }
+  };
+  Piece cur, nxt;
+  if (!next_chunk(cur)) return;
+  issue(cur, 0);
+  int b = 0;
+  // per buffer (bit b): the parity of its next phase, and whether a load was
+  // issued into it and not yet waited for
+  uint32_t ph = 0u, inflight = 1u;
+  for (;;) {
+    bool has_next;
+    if (cur.j + 1 < CV_PIECES) {
+      nxt = cur;
+      ++nxt.j;
+      has_next = !*abort_flag;
+    } else {
+      has_next = next_chunk(nxt);
+    }
+    __syncwarp();  // the piece converted last (buffer b ^ 1) is read by every lane
+    if (has_next) {
+      issue(nxt, b ^ 1);
+      inflight |= 1u << (b ^ 1);
+    }
+    if (!mbar_wait_warp(&bar[b], (ph >> b) & 1u, abort_flag, status, ST_CONVERT)) break;
+    inflight &= ~(1u << b);
+    ph ^= 1u << b;
+    // lane l: row l of the piece; the stage holds element (row i, k) at k * 32 + i
+    const float* st = reinterpret_cast<const float*>(buf + b * CV_PIECE_BYTES);
+    const int row = cur.blk * CV_ROWS + cur.j * CV_PIECE + lane;
+    if (row < cv.rows[cur.op]) {
+      __nv_bfloat16* hrow = cv.hi[cur.op] + (int64_t)row * cv.Kp;
+      __nv_bfloat16* lrow = cv.lo[cur.op] + (int64_t)row * cv.Kp;
+#pragma unroll
+      for (int g = 0; g < CV_BK / 8; ++g) {
+        const int k0 = cur.kb * CV_BK + g * 8;
+        if (k0 < cv.Kp) {
+          __align__(16) __nv_bfloat16 h[8];
+          __align__(16) __nv_bfloat16 l[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) split_pair(st[(g * 8 + u) * CV_PIECE + lane], h[u], l[u]);
+          *reinterpret_cast<uint4*>(hrow + k0) = *reinterpret_cast<const uint4*>(h);
+          *reinterpret_cast<uint4*>(lrow + k0) = *reinterpret_cast<const uint4*>(l);
+        }
+      }
+    }
+    if (cur.j + 1 == CV_PIECES) {
+      // the chunk's planes are written: make them visible to the TMA loads
+      // of other CTAs, then release its flag
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      __threadfence();
+      __syncwarp();
+      if (lane == 0)
+        st_release_gpu(cv.flags + (int64_t)((cur.op ? cv.blocks[0] : 0) + cur.blk) * cv.num_kb + cur.kb, 1);
+    }
+    if (!has_next) break;
+    cur = nxt;
+    b ^= 1;
+  }
+  // leaving early (an abort, or a piece that never arrived): wait (bounded)
+  // for this warp's loads still in flight before the CTA may exit
+  __syncwarp();
+  if (lane == 0) {
+    for (int bb = 0; bb < 2; ++bb) {
+      if (!((inflight >> bb) & 1u)) continue;
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&bar[bb], (ph >> bb) & 1u)) {
+        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+          if (status) atomicOr_system(status, ST_DRAIN);
+          break;
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
 
 // One instance of a batch of independent sgemm DFGs (device memory): its
 // four operand-plane tensor maps (64-byte aligned), its result, and the tile
@@ -816,13 +1020,17 @@ struct TileView {
 //   warp 1      tensor-memory allocation; MMA issuer (leader only)
 //   warps 2, 3  idle (they complete the control warpgroup)
 //   warps 4-11  epilogue (both CTAs: each drains its own 128 rows)
-template <int MODE, int EPI, bool GROUPED, bool PAIR>
+// CONVERT: warps 2 and 3 write the operand planes (see ConvParams) and the
+// producer waits for each slab's chunks.
+template <int MODE, int EPI, bool GROUPED, bool PAIR, bool CONVERT = false>
 __global__ void __launch_bounds__(THREADS, 1)
     sgemm_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
              const __grid_constant__ CUtensorMap tmA_lo2, const __grid_constant__ CUtensorMap tmB_lo2,
-             TcParams p, GroupParams gp) {
+             TcParams p, GroupParams gp, const __grid_constant__ ConvParams cv) {
   static_assert(!(GROUPED && PAIR), "batches run on single CTAs");
+  static_assert(!CONVERT || (MODE == 3 && PAIR && !GROUPED && Cfg<MODE, PAIR>::BK == CV_BK),
+                "in-leaf conversion: the BF16x3 leaf on pairs, one chunk per slab");
   static_assert(MODE != 6 || (!GROUPED && EPI == 0), "BF16x6: single instances, plain epilogue");
   using C_ = Cfg<MODE, PAIR>;
   constexpr int CG = PAIR ? 2 : 1;
@@ -843,6 +1051,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* tempty = tfull + C_::NBUF;  // [NBUF] epilogue -> MMA: buffer b read out
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + C_::NBUF);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // CONVERT: two piece barriers per converter warp (in the barrier area),
+  // their staging buffers and the chunk order's round table after it
+  uint64_t* cvbar = reinterpret_cast<uint64_t*>(smem + S * C_::STAGE_BYTES + 256);
+  uint8_t* cvbuf = smem + S * C_::STAGE_BYTES + 512;
+  int* cvtab = reinterpret_cast<int*>(cvbuf + CV_WARPS * 2 * CV_PIECE_BYTES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = PAIR ? cluster_ctarank() : 0u;  // CTA within the pair
@@ -947,6 +1160,34 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&tempty[b], PAIR ? 2 * EPI_WARPS : EPI_WARPS);  // PAIR: both CTAs' epilogues
     }
     *abort_flag = 0;
+    if constexpr (CONVERT) {
+      for (int b = 0; b < 2 * CV_WARPS; ++b) mbar_init(&cvbar[b], 1);
+      // Round r of the grouped order runs tiles [r U, (r + 1) U) (U units).
+      // Row tile rt is first used by tile rt * gn0 (group 0), column tile
+      // ct by tile (ct / GROUP_N) * GROUP_N * tiles_m + ct % GROUP_N: round
+      // r converts the 128-row blocks of the row and column tiles first used
+      // in it (the last round: all the rest).
+      const int U = num_units;
+      const int gn0 = min(GROUP_N, tiles_n);
+      const int R = max(1, min(CV_MAX_ROUNDS, (num_tiles + U - 1) / U));
+      int ct = 0, base = 0;
+      for (int r = 0; r < R; ++r) {
+        const bool last = r + 1 == R;
+        const int rt_lo = min(tiles_m, (r * U + gn0 - 1) / gn0);
+        const int rt_hi = last ? tiles_m : min(tiles_m, ((r + 1) * U + gn0 - 1) / gn0);
+        const int ct_lo = ct;
+        while (ct < tiles_n && (last || (ct / GROUP_N) * GROUP_N * tiles_m + ct % GROUP_N < (r + 1) * U)) ++ct;
+        int* e = cvtab + r * CV_TAB;
+        e[0] = min(cv.blocks[0], 2 * rt_lo);
+        e[1] = min(cv.blocks[0], 2 * rt_hi);
+        e[2] = min(cv.blocks[1], 2 * ct_lo);
+        e[3] = min(cv.blocks[1], 2 * ct);
+        e[4] = base;
+        base += ((e[1] - e[0]) + (e[3] - e[2])) * cv.num_kb;
+      }
+      cvtab[R * CV_TAB + 4] = base;  // the total: every chunk once
+      cvtab[CV_MAX_ROUNDS * CV_TAB] = R;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -977,7 +1218,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp < EPI_WARP0) {
     // control warpgroup: its registers go to the epilogue warpgroups
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RegSplit<MODE, EPI, PAIR>::CTRL_R));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RegSplit<MODE, EPI, PAIR, CONVERT>::CTRL_R));
     if (warp == 0 && lane == 0) {
       // ---- producer: TMA loads of the operand slabs into the ring. PAIR:
       // this CTA's 128 rows of A and its half of B's rows; both CTAs' loads
@@ -1006,6 +1247,16 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           const int k = kb * BK;
+          if constexpr (CONVERT) {
+            // the chunks of this CTA's A rows and B rows for slab kb
+            if ((ma < p.M && !flag_wait(cv.flags + (int64_t)(ma / CV_ROWS) * cv.num_kb + kb, abort_flag,
+                                        p.status, ST_PRODUCER | ST_CONVERT, peer_abort)) ||
+                (nb < p.N && !flag_wait(cv.flags + (int64_t)(cv.blocks[0] + nb / CV_ROWS) * cv.num_kb + kb,
+                                        abort_flag, p.status, ST_PRODUCER | ST_CONVERT, peer_abort))) {
+              go = false;
+              break;
+            }
+          }
           if constexpr (PAIR) {
             if (leader) mbar_expect_tx(&full[s], 2 * bytes);
             const uint32_t bar = mapa_rank(smem_u32(&full[s]), 0);
@@ -1103,6 +1354,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           umma_commit<CG>(&tfull[buf]);  // chunk complete in buffer buf (both CTAs)
         }
       }
+    } else if (CONVERT && (warp == 2 || warp == 3)) {
+      // ---- converter: chunks in claim order, four 32-row pieces each, two
+      // staging buffers (the next piece's TMA load in flight while this one
+      // is converted); lane l converts row l of a piece
+      const int w = warp - 2;
+      if constexpr (CONVERT)
+        cv_convert(cv, cvtab, cvbar + 2 * w, cvbuf + w * 2 * CV_PIECE_BYTES, lane, abort_flag, p.status);
     }
     __syncwarp();
     tc_fence_before();
@@ -1151,7 +1409,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                      : "memory");
     }
   } else {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RegSplit<MODE, EPI, PAIR>::EPI_R));
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RegSplit<MODE, EPI, PAIR, CONVERT>::EPI_R));
     // ---- epilogue: every chunk, tensor memory -> FP32 registers (round to
     // nearest); at the end of a tile, registers -> C, coalesced per column.
     // PAIR: this CTA's tensor memory holds rows rank*128 .. +127 of the tile.
@@ -1490,6 +1748,31 @@ int current_device() {
 }
 inline bool cached_device(int dev) { return dev >= 0 && dev < kMaxDevices; }
 
+// FP32 operand with rows contiguous (element (r, k) at X[r + k * ld]) for
+// the in-leaf conversion: a box of 32 rows x 64 K, no swizzle (the
+// converter reads the staged piece column by column).
+bool encode_fp32_rows(CUtensorMap* map, const float* X, int64_t ld, int rows, int K, std::string* err) {
+  auto enc = get_encoder();
+  if (!enc) {
+    *err = "cuTensorMapEncodeTiled is not available from the driver";
+    return false;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)K};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)CV_PIECE, (cuuint32_t)CV_BK};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for a %d x %d FP32 operand", (int)r, rows, K);
+    *err = buf;
+    return false;
+  }
+  return true;
+}
+
 int num_sms() {
   static std::atomic<int> cache[kMaxDevices];
   const int dev = current_device();
@@ -1524,6 +1807,7 @@ struct WsLayout {
   int nkb = 0;     // FP8: scale blocks along K
   size_t planes = 0;                   // end of the planes: the least a launch needs
   size_t split = 0, split_bytes = 0;   // the tail split's partial sums and counters
+  size_t conv = 0, conv_bytes = 0;     // BF16x3: the in-leaf conversion's chunk flags and counter
 };
 
 // Bytes of a tail split of n tiles: per tile, K half, CTA and epilogue warp
@@ -1565,6 +1849,15 @@ WsLayout ws_layout(const SgemmDesc& d, int mode) {
       L.split_bytes = split_region_bytes(n, 2, P::ACC);
       off += L.split_bytes;
     }
+  }
+  if (mode == 3) {
+    // one flag per 128-row block and 64-element slab of each operand, then
+    // the claim counter
+    const int64_t kb = (d.K + CV_BK - 1) / CV_BK;
+    const int64_t nflags = ((d.M + CV_ROWS - 1) / CV_ROWS + (d.N + CV_ROWS - 1) / CV_ROWS) * kb;
+    L.conv = off;
+    L.conv_bytes = align256((size_t)(nflags + 1) * sizeof(int));
+    off += L.conv_bytes;
   }
   L.total = off;
   return L;
@@ -1661,13 +1954,48 @@ cudaError_t tail_setup(TcParams& prm, int tiles, int units, size_t split_cap, in
                          (size_t)n * RANKS * EPI_WARPS * sizeof(int), s);
 }
 
-template <int MODE, int EPI, bool PAIR>
-cudaError_t launch_leaf(const CUtensorMap* maps, TcParams prm, int tiles, size_t split_cap, int split_as,
-                        cudaStream_t s, int* grid_ctas, const LaunchHooks* hooks) {
-  using C_ = Cfg<MODE, PAIR>;
-  auto kernel = sgemm_tc<MODE, EPI, false, PAIR>;
+// The pairs a launch of this leaf variant runs at once (the clusters the
+// GPU holds), looked up per device; sets the kernel's attributes first.
+template <int MODE, int EPI, bool CONVERT>
+cudaError_t pair_units(int* units) {
+  using C_ = Cfg<MODE, true>;
+  auto kernel = sgemm_tc<MODE, EPI, false, true, CONVERT>;
+  constexpr uint32_t smem = C_::SMEM_BYTES + (CONVERT ? CV_SMEM : 0);
   const int dev = current_device();
+  static std::atomic<int> max_clusters_of[kMaxDevices];
+  int n = cached_device(dev) ? max_clusters_of[dev].load(std::memory_order_acquire) : 0;
+  if (n == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = check_register_split(kernel);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * num_sms());
+    e = cudaOccupancyMaxActiveClusters(&n, kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    if (cached_device(dev)) max_clusters_of[dev].store(n, std::memory_order_release);
+  }
+  *units = n;
+  return cudaSuccess;
+}
+
+template <int MODE, int EPI, bool PAIR, bool CONVERT = false>
+cudaError_t launch_leaf(const CUtensorMap* maps, TcParams prm, int tiles, size_t split_cap, int split_as,
+                        cudaStream_t s, int* grid_ctas, const LaunchHooks* hooks, const ConvParams& cvp) {
+  using C_ = Cfg<MODE, PAIR>;
+  static_assert(!CONVERT || PAIR, "in-leaf conversion on pairs");
+  auto kernel = sgemm_tc<MODE, EPI, false, PAIR, CONVERT>;
   if constexpr (!PAIR) {
+    const int dev = current_device();
     static std::atomic<bool> attr_set[kMaxDevices];
     if (!cached_device(dev) || !attr_set[dev].load(std::memory_order_acquire)) {
       cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
@@ -1681,46 +2009,35 @@ cudaError_t launch_leaf(const CUtensorMap* maps, TcParams prm, int tiles, size_t
     if (e != cudaSuccess) return e;
     hook_begin(hooks, s);
     kernel<<<grid, THREADS, C_::SMEM_BYTES, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], prm,
-                                                  GroupParams{nullptr, nullptr, 0});
+                                                  GroupParams{nullptr, nullptr, 0}, cvp);
     e = cudaGetLastError();
     hook_end(hooks, s);
     return e;
-  }
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = C_::SMEM_BYTES;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  static std::atomic<int> max_clusters_of[kMaxDevices];
-  int max_clusters = cached_device(dev) ? max_clusters_of[dev].load(std::memory_order_acquire) : 0;
-  if (max_clusters == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
-    if (e == cudaSuccess) e = check_register_split(kernel);
+  } else {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = C_::SMEM_BYTES + (CONVERT ? CV_SMEM : 0);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int max_clusters = 0;
+    if (cudaError_t e = pair_units<MODE, EPI, CONVERT>(&max_clusters); e != cudaSuccess) return e;
+    const int clusters = std::max(1, std::min(tiles, max_clusters));
+    cfg.gridDim = dim3(2 * clusters);
+    *grid_ctas = 2 * clusters;
+    cudaError_t e = tail_setup<MODE, EPI, PAIR>(prm, tiles, clusters, split_cap, split_as, s);
     if (e != cudaSuccess) return e;
-    cfg.gridDim = dim3(2 * num_sms());
-    int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, kernel, &cfg);
-    if (e != cudaSuccess) return e;
-    if (n < 1) return cudaErrorInvalidConfiguration;
-    max_clusters = n;
-    if (cached_device(dev)) max_clusters_of[dev].store(n, std::memory_order_release);
+    hook_begin(hooks, s);
+    e = cudaLaunchKernelEx(&cfg, kernel, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], prm,
+                           GroupParams{nullptr, nullptr, 0}, cvp);
+    hook_end(hooks, s);
+    return e;
   }
-  const int clusters = std::max(1, std::min(tiles, max_clusters));
-  cfg.gridDim = dim3(2 * clusters);
-  *grid_ctas = 2 * clusters;
-  cudaError_t e = tail_setup<MODE, EPI, PAIR>(prm, tiles, clusters, split_cap, split_as, s);
-  if (e != cudaSuccess) return e;
-  hook_begin(hooks, s);
-  e = cudaLaunchKernelEx(&cfg, kernel, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], prm,
-                         GroupParams{nullptr, nullptr, 0});
-  hook_end(hooks, s);
-  return e;
 }
 
 template <int MODE>
@@ -1765,7 +2082,47 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
   }
   int kernels = 0;
   cudaError_t e = cudaSuccess;
-  if (K > 0) {
+  const int tiles = ((M + TM - 1) / TM) * ((N + C_::TN - 1) / C_::TN);
+  // In-leaf conversion (ConvParams): the plain BF16x3 leaf writing its own
+  // planes into the workspace, for operands whose rows are contiguous and
+  // TMA-readable (16-byte aligned base and leading dimension), on launches
+  // that fill the GPU with at least 32 pair tiles and whose grouped order
+  // has at most CV_MAX_ROUNDS rounds.
+  ConvParams cvp;
+  memset(&cvp, 0, sizeof cvp);
+  bool convert = false;
+  if constexpr (MODE == 3) {
+    int units = 0;
+    convert = !epi.separate_split && epi.kind == 0 && !epi.fwd && !epi.rows && !pa.base && !pb.base && K > 0 &&
+              !d.transA && d.transB && (reinterpret_cast<uintptr_t>(d.A) & 15u) == 0 &&
+              (reinterpret_cast<uintptr_t>(d.B) & 15u) == 0 && d.lda % 4 == 0 && d.ldb % 4 == 0 && tiles >= 32 &&
+              L.conv_bytes && ws_bytes >= L.conv + L.conv_bytes;
+    if (convert) {
+      if ((e = pair_units<3, 0, true>(&units)) != cudaSuccess) return e;
+      const int U = std::max(1, std::min(tiles, units));
+      convert = (tiles + U - 1) / U <= CV_MAX_ROUNDS;
+    }
+    if (convert) {
+      if (!encode_fp32_rows(&cvp.src[0], d.A, d.lda, M, K, err) ||
+          !encode_fp32_rows(&cvp.src[1], d.B, d.ldb, N, K, err))
+        return cudaErrorInvalidValue;
+      cvp.hi[0] = static_cast<__nv_bfloat16*>(ah);
+      cvp.lo[0] = static_cast<__nv_bfloat16*>(al);
+      cvp.hi[1] = static_cast<__nv_bfloat16*>(bh);
+      cvp.lo[1] = static_cast<__nv_bfloat16*>(bl);
+      cvp.rows[0] = M;
+      cvp.rows[1] = N;
+      cvp.blocks[0] = (M + CV_ROWS - 1) / CV_ROWS;
+      cvp.blocks[1] = (N + CV_ROWS - 1) / CV_ROWS;
+      cvp.Kp = Kp;
+      cvp.num_kb = (K + CV_BK - 1) / CV_BK;
+      cvp.flags = reinterpret_cast<int*>(w + L.conv);
+      cvp.claim = cvp.flags + (int64_t)(cvp.blocks[0] + cvp.blocks[1]) * cvp.num_kb;
+      // every flag and the claim counter start at zero in each launch
+      if ((e = cudaMemsetAsync(w + L.conv, 0, L.conv_bytes, s)) != cudaSuccess) return e;
+    }
+  }
+  if (K > 0 && !convert) {
     // op(A) rows are contiguous when A is not transposed; op(B)'s N rows when B is
     if (!pa.ready) {
       if (C_::FP8)
@@ -1832,7 +2189,6 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
     prm.fwd_lo = reinterpret_cast<__nv_bfloat16*>(f + F.lo);
     prm.fwd_kp = (int)((M + 7) / 8 * 8);
   }
-  const int tiles = ((M + TM - 1) / TM) * ((N + C_::TN - 1) / C_::TN);
   // the tail split's region, when the workspace holds it (the launch decides)
   size_t split_cap = 0;
   if (L.split_bytes && ws_bytes >= L.split + L.split_bytes) {
@@ -1842,11 +2198,18 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
   int grid_ctas = 0;
   const int sa_ = epi.split_as;
   if constexpr (MODE == 6) {
-    e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
+    e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks, cvp);
   } else {
-    if (epi.kind == 1) e = launch_leaf<MODE, 1, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
-    else if (epi.kind == 2) e = launch_leaf<MODE, 2, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
-    else e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks);
+    if (convert) {
+      if constexpr (MODE == 3) e = launch_leaf<3, 0, true, true>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas,
+                                                                  hooks, cvp);
+    } else if (epi.kind == 1) {
+      e = launch_leaf<MODE, 1, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks, cvp);
+    } else if (epi.kind == 2) {
+      e = launch_leaf<MODE, 2, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks, cvp);
+    } else {
+      e = launch_leaf<MODE, 0, PAIR>(maps, prm, tiles, split_cap, sa_, s, &grid_ctas, hooks, cvp);
+    }
   }
   if (e != cudaSuccess) return e;
   kernels += 1;
@@ -1855,7 +2218,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
     rep->grid_x = grid_ctas; rep->grid_y = 1; rep->grid_z = 1;
     rep->block_threads = THREADS;
     rep->tile_m = TM; rep->tile_n = C_::TN; rep->tile_k = C_::BK;
-    rep->smem_bytes = (int)C_::SMEM_BYTES;
+    rep->smem_bytes = (int)(C_::SMEM_BYTES + (convert ? CV_SMEM : 0));
     rep->literal = 0;
     rep->workspace_bytes = (int64_t)L.total;
   }
@@ -1885,7 +2248,7 @@ cudaError_t launch_batch_kernels(const TcBatch& b, const DeviceStatus& st, cudaS
   hook_begin(hooks, s);
   sgemm_tc<MODE, 0, true, false>
       <<<b.grid, THREADS, C_::SMEM_BYTES, s>>>(unused[0], unused[1], unused[2], unused[3], unused[4], unused[5], prm,
-                                               gp);
+                                               gp, ConvParams{});
   hook_end(hooks, s);
   return cudaGetLastError();
 }

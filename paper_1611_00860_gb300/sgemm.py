@@ -137,10 +137,10 @@ class SgemmDFG:
         self.wait(g, timeout_ms)
         return self.last_info
 
-    def run_problem(self, p, tier, dev_tensors=None, block=None, grid=None, timeout_ms=60000):
+    def run_problem(self, p, tier, dev_tensors=None, block=None, grid=None, timeout_ms=60000, flags=0):
         """Run a ``workloads.SgemmProblem`` whose A, B, C were moved to the device
         (``dev_tensors`` = (A, B, C) CUDA tensors; C is updated in place)."""
         A, B, C = dev_tensors
         return self(p.M, p.N, p.K, A, p.lda, B, p.ldb, C, p.ldc, p.alpha, p.beta,
                     p.transA, p.transB, tier=tier, block=block, grid=grid,
-                    timeout_ms=timeout_ms)
+                    timeout_ms=timeout_ms, flags=flags)
