@@ -156,15 +156,16 @@ extern "C" {
  * the planes (hpvm_drop_planes in between, or no REUSE flag) reads the old
  * contents. */
 #define HPVM_LAUNCH_PLANES_ONLY 128
-/* SEPARATE_SPLIT: the plain BF16X3 leaf normally writes its operands'
- * planes itself when both operands have their rows contiguous (op(A) = A,
- * op(B) = B^T, the example's form), 16-byte aligned with leading dimensions
- * that are multiples of 4, and the launch has at least 32 tiles of 256 x
- * 256: the leaf's two otherwise idle control warps convert 128-row chunks
- * of FP32 in the order the tiles first need them, and each slab's loads
- * wait for its chunks (one kernel instead of three; the planes and the
- * result are the same bit for bit). This flag runs the split as its own
- * kernels instead. */
+/* SEPARATE_SPLIT: the plain BF16X3 leaf normally converts most of its
+ * operands itself when both have their rows contiguous (op(A) = A, op(B) =
+ * B^T, the example's form), 16-byte aligned with leading dimensions that
+ * are multiples of 4, and the first round of 256 x 256 tiles reads at most
+ * half of their rows (large launches, e.g. 8192^3): the split kernels then
+ * convert only the first round's rows, and the leaf's two otherwise idle
+ * control warps convert the rest chunk by chunk while the leaf runs, each
+ * slab's loads waiting for its chunks (the planes and the result are the
+ * same bit for bit). This flag runs the split of every row as its own
+ * kernels before the leaf instead. */
 #define HPVM_LAUNCH_SEPARATE_SPLIT 256
 
 typedef struct hpvm_ctx hpvm_ctx;

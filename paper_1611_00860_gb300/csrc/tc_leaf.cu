@@ -195,7 +195,12 @@ struct TcParams {
 // and release a per-chunk flag. The producer acquires the flags of the two
 // chunks a slab reads before its TMA loads. Chunks are claimed only by
 // running CTAs and converting one waits on nothing else, so every claimed
-// chunk is finished; all waits are bounded.
+// chunk is finished; all waits are bounded. The first round's blocks, which
+// every pair needs at once from the first slab on, are split by the split
+// kernel before the launch (pre): converting them inside the leaf held its
+// first round back (GB300, 8192: leaf 1.93-2.09 ms against 1.73-1.92 ms
+// with every block ready), while the later rounds' blocks are converted
+// long before they are read.
 constexpr int CV_ROWS = 128;    // rows of a chunk
 constexpr int CV_BK = 64;       // K elements of a chunk (the leaf's slab)
 constexpr int CV_PIECE = 32;    // rows of a staged piece
@@ -209,11 +214,14 @@ struct ConvParams {
   CUtensorMap src[2];  // FP32 op(A) and op(B)^T, rows contiguous: box of 32 rows x 64 K
   __nv_bfloat16* hi[2];
   __nv_bfloat16* lo[2];
-  int* flags;          // one per chunk: A's (block * num_kb + slab), then B's
+  int* flags;          // one per chunk: A's (block * kb_stride + slab), then B's
+  int* done;           // per block (A's, then B's): its chunks converted so far
   int* claim;          // the next chunk to convert
   int rows[2];         // M, N
   int blocks[2];       // ceil(rows / 128)
   int Kp, num_kb;
+  int kb_stride;       // num_kb rounded up to 4: a block's flags, 16-byte aligned
+  int pre[2];          // blocks [0, pre) of each operand: converted before the launch
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -826,6 +834,25 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// four consecutive flags (16-byte aligned) as a 4-bit mask of the nonzero ones
+__device__ __forceinline__ uint32_t ld_relaxed_mask4(const int* p) {
+  int a, b, c, d;
+  asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+               : "l"(p)
+               : "memory");
+  return (a != 0 ? 1u : 0u) | (b != 0 ? 2u : 0u) | (c != 0 ? 4u : 0u) | (d != 0 ? 8u : 0u);
+}
+// acquire for what relaxed loads observed, extended to the TMA (async
+// proxy) loads that follow
+__device__ __forceinline__ void fence_acquire_for_tma() {
+  asm volatile("fence.acq_rel.gpu;\n\tfence.proxy.async.global;" ::: "memory");
+}
 __device__ __forceinline__ void st_release_gpu(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -917,22 +944,28 @@ __device__ __forceinline__ void cv_convert(const ConvParams& cv, const int* tab,
     if (!mbar_wait_warp(&bar[b], (ph >> b) & 1u, abort_flag, status, ST_CONVERT)) break;
     inflight &= ~(1u << b);
     ph ^= 1u << b;
-    // lane l: row l of the piece; the stage holds element (row i, k) at k * 32 + i
+    // The stage holds element (row i, k) at k * 32 + i. Lane l converts K
+    // elements 8 (l % 8) .. + 7 of rows l / 8 + 4 t (t = 0..7), so each
+    // store instruction writes four whole 128-byte plane rows (eight lanes a
+    // row) instead of 32 partial ones; its shared-memory reads conflict
+    // eight ways, which costs little next to the leaf's own traffic.
     const float* st = reinterpret_cast<const float*>(buf + b * CV_PIECE_BYTES);
-    const int row = cur.blk * CV_ROWS + cur.j * CV_PIECE + lane;
-    if (row < cv.rows[cur.op]) {
-      __nv_bfloat16* hrow = cv.hi[cur.op] + (int64_t)row * cv.Kp;
-      __nv_bfloat16* lrow = cv.lo[cur.op] + (int64_t)row * cv.Kp;
-#pragma unroll
-      for (int g = 0; g < CV_BK / 8; ++g) {
-        const int k0 = cur.kb * CV_BK + g * 8;
-        if (k0 < cv.Kp) {
+    const int g8 = (lane & 7) * 8;
+    const int k0 = cur.kb * CV_BK + g8;
+    if (k0 < cv.Kp) {
+      __nv_bfloat16* hp = cv.hi[cur.op] + k0;
+      __nv_bfloat16* lp = cv.lo[cur.op] + k0;
+#pragma unroll 1
+      for (int t = 0; t < CV_PIECE / 4; ++t) {
+        const int r = (lane >> 3) + 4 * t;
+        const int row = cur.blk * CV_ROWS + cur.j * CV_PIECE + r;
+        if (row < cv.rows[cur.op]) {
           __align__(16) __nv_bfloat16 h[8];
           __align__(16) __nv_bfloat16 l[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) split_pair(st[(g * 8 + u) * CV_PIECE + lane], h[u], l[u]);
-          *reinterpret_cast<uint4*>(hrow + k0) = *reinterpret_cast<const uint4*>(h);
-          *reinterpret_cast<uint4*>(lrow + k0) = *reinterpret_cast<const uint4*>(l);
+          for (int u = 0; u < 8; ++u) split_pair(st[(g8 + u) * CV_PIECE + r], h[u], l[u]);
+          *reinterpret_cast<uint4*>(hp + (int64_t)row * cv.Kp) = *reinterpret_cast<const uint4*>(h);
+          *reinterpret_cast<uint4*>(lp + (int64_t)row * cv.Kp) = *reinterpret_cast<const uint4*>(l);
         }
       }
     }
@@ -942,8 +975,11 @@ __device__ __forceinline__ void cv_convert(const ConvParams& cv, const int* tab,
       asm volatile("fence.proxy.async.global;" ::: "memory");
       __threadfence();
       __syncwarp();
-      if (lane == 0)
-        st_release_gpu(cv.flags + (int64_t)((cur.op ? cv.blocks[0] : 0) + cur.blk) * cv.num_kb + cur.kb, 1);
+      if (lane == 0) {
+        const int blk = (cur.op ? cv.blocks[0] : 0) + cur.blk;
+        st_release_gpu(cv.flags + (int64_t)blk * cv.kb_stride + cur.kb, 1);
+        asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(cv.done + blk) : "memory");
+      }
     }
     if (!has_next) break;
     cur = nxt;
@@ -1178,10 +1214,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int ct_lo = ct;
         while (ct < tiles_n && (last || (ct / GROUP_N) * GROUP_N * tiles_m + ct % GROUP_N < (r + 1) * U)) ++ct;
         int* e = cvtab + r * CV_TAB;
-        e[0] = min(cv.blocks[0], 2 * rt_lo);
         e[1] = min(cv.blocks[0], 2 * rt_hi);
-        e[2] = min(cv.blocks[1], 2 * ct_lo);
+        e[0] = min(e[1], max(cv.pre[0], 2 * rt_lo));
         e[3] = min(cv.blocks[1], 2 * ct);
+        e[2] = min(e[3], max(cv.pre[1], 2 * ct_lo));
         e[4] = base;
         base += ((e[1] - e[0]) + (e[3] - e[2])) * cv.num_kb;
       }
@@ -1239,6 +1275,23 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int ma = v.m0 + (int)rank * BM;
         const int nb = v.n0 + (int)rank * C_::B_ROWS;
         const int kb_hi = TAIL ? v.kb1 : (v.K + BK - 1) / BK;
+        // CONVERT: whether every chunk of this CTA's A block, and of its B
+        // block, is ready (split before the launch, or all converted): such
+        // an operand needs no flag checks in this tile; for the other, the
+        // flags of slabs [grp, grp + 4) seen set (bit per slab)
+        bool done_a = true, done_b = true;
+        int grp = -4;
+        uint32_t ready_a = 0xFu, ready_b = 0xFu;
+        const int* flag_a = nullptr;
+        const int* flag_b = nullptr;
+        if constexpr (CONVERT) {
+          const int ba = ma / CV_ROWS, bb = cv.blocks[0] + nb / CV_ROWS;
+          flag_a = cv.flags + (int64_t)ba * cv.kb_stride;
+          flag_b = cv.flags + (int64_t)bb * cv.kb_stride;
+          done_a = ma >= p.M || ba < cv.pre[0] || ld_relaxed_gpu(cv.done + ba) == cv.num_kb;
+          done_b = nb >= p.N || nb / CV_ROWS < cv.pre[1] || ld_relaxed_gpu(cv.done + bb) == cv.num_kb;
+          if (done_a && done_b) fence_acquire_for_tma();
+        }
         for (int kb = TAIL ? v.kb0 : 0; kb < kb_hi; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1;
@@ -1249,12 +1302,23 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int k = kb * BK;
           if constexpr (CONVERT) {
             // the chunks of this CTA's A rows and B rows for slab kb
-            if ((ma < p.M && !flag_wait(cv.flags + (int64_t)(ma / CV_ROWS) * cv.num_kb + kb, abort_flag,
-                                        p.status, ST_PRODUCER | ST_CONVERT, peer_abort)) ||
-                (nb < p.N && !flag_wait(cv.flags + (int64_t)(cv.blocks[0] + nb / CV_ROWS) * cv.num_kb + kb,
-                                        abort_flag, p.status, ST_PRODUCER | ST_CONVERT, peer_abort))) {
-              go = false;
-              break;
+            if (!(done_a && done_b)) {
+              if ((kb & ~3) != grp) {
+                grp = kb & ~3;
+                ready_a = done_a ? 0xFu : ld_relaxed_mask4(flag_a + grp);
+                ready_b = done_b ? 0xFu : ld_relaxed_mask4(flag_b + grp);
+              }
+              const uint32_t bit = 1u << (kb & 3);
+              if (((ready_a & bit) == 0 &&
+                   !flag_wait(flag_a + kb, abort_flag, p.status, ST_PRODUCER | ST_CONVERT, peer_abort)) ||
+                  ((ready_b & bit) == 0 &&
+                   !flag_wait(flag_b + kb, abort_flag, p.status, ST_PRODUCER | ST_CONVERT, peer_abort))) {
+                go = false;
+                break;
+              }
+              ready_a |= bit;
+              ready_b |= bit;
+              fence_acquire_for_tma();
             }
           }
           if constexpr (PAIR) {
@@ -1851,12 +1915,13 @@ WsLayout ws_layout(const SgemmDesc& d, int mode) {
     }
   }
   if (mode == 3) {
-    // one flag per 128-row block and 64-element slab of each operand, then
-    // the claim counter
-    const int64_t kb = (d.K + CV_BK - 1) / CV_BK;
-    const int64_t nflags = ((d.M + CV_ROWS - 1) / CV_ROWS + (d.N + CV_ROWS - 1) / CV_ROWS) * kb;
+    // one flag per 128-row block and 64-element slab of each operand (a
+    // block's row of flags padded to 4), one count per block, and the claim
+    // counter
+    const int64_t kb4 = ((d.K + CV_BK - 1) / CV_BK + 3) / 4 * 4;
+    const int64_t blocks = (d.M + CV_ROWS - 1) / CV_ROWS + (d.N + CV_ROWS - 1) / CV_ROWS;
     L.conv = off;
-    L.conv_bytes = align256((size_t)(nflags + 1) * sizeof(int));
+    L.conv_bytes = align256((size_t)(blocks * kb4 + blocks + 1) * sizeof(int));
     off += L.conv_bytes;
   }
   L.total = off;
@@ -2097,10 +2162,20 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
               !d.transA && d.transB && (reinterpret_cast<uintptr_t>(d.A) & 15u) == 0 &&
               (reinterpret_cast<uintptr_t>(d.B) & 15u) == 0 && d.lda % 4 == 0 && d.ldb % 4 == 0 && tiles >= 32 &&
               L.conv_bytes && ws_bytes >= L.conv + L.conv_bytes;
+    int pre_rows[2] = {0, 0};
     if (convert) {
       if ((e = pair_units<3, 0, true>(&units)) != cudaSuccess) return e;
       const int U = std::max(1, std::min(tiles, units));
-      convert = (tiles + U - 1) / U <= CV_MAX_ROUNDS;
+      // the first round's row tiles (rt * gn0 < U) and column tiles (first
+      // used by a tile < U), as rows of op(A) and of op(B)^T
+      const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + C_::TN - 1) / C_::TN;
+      const int gn0 = std::min(GROUP_N, tiles_n);
+      int ct = 0;
+      while (ct < tiles_n && (ct / GROUP_N) * GROUP_N * tiles_m + ct % GROUP_N < U) ++ct;
+      pre_rows[0] = std::min(M, std::min(tiles_m, (U + gn0 - 1) / gn0) * TM);
+      pre_rows[1] = std::min(N, ct * C_::TN);
+      // worth it only when later rounds hold most of the operands
+      convert = (tiles + U - 1) / U <= CV_MAX_ROUNDS && 2 * ((int64_t)pre_rows[0] + pre_rows[1]) <= (int64_t)M + N;
     }
     if (convert) {
       if (!encode_fp32_rows(&cvp.src[0], d.A, d.lda, M, K, err) ||
@@ -2116,10 +2191,22 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
       cvp.blocks[1] = (N + CV_ROWS - 1) / CV_ROWS;
       cvp.Kp = Kp;
       cvp.num_kb = (K + CV_BK - 1) / CV_BK;
+      cvp.kb_stride = (cvp.num_kb + 3) / 4 * 4;
       cvp.flags = reinterpret_cast<int*>(w + L.conv);
-      cvp.claim = cvp.flags + (int64_t)(cvp.blocks[0] + cvp.blocks[1]) * cvp.num_kb;
+      cvp.done = cvp.flags + (int64_t)(cvp.blocks[0] + cvp.blocks[1]) * cvp.kb_stride;
+      cvp.claim = cvp.done + (cvp.blocks[0] + cvp.blocks[1]);
+      cvp.pre[0] = (pre_rows[0] + CV_ROWS - 1) / CV_ROWS;
+      cvp.pre[1] = (pre_rows[1] + CV_ROWS - 1) / CV_ROWS;
       // every flag and the claim counter start at zero in each launch
       if ((e = cudaMemsetAsync(w + L.conv, 0, L.conv_bytes, s)) != cudaSuccess) return e;
+      // the first round's rows by the split kernel, before the leaf
+      if ((e = launch_split<3>(d.A, d.lda, true, pre_rows[0], K, Kp, static_cast<__nv_bfloat16*>(ah),
+                               static_cast<__nv_bfloat16*>(al), nullptr, s)) != cudaSuccess)
+        return e;
+      if ((e = launch_split<3>(d.B, d.ldb, true, pre_rows[1], K, Kp, static_cast<__nv_bfloat16*>(bh),
+                               static_cast<__nv_bfloat16*>(bl), nullptr, s)) != cudaSuccess)
+        return e;
+      kernels += 2;
     }
   }
   if (K > 0 && !convert) {

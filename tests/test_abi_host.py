@@ -90,7 +90,8 @@ def test_workspace_size_on_host(ctx):
     # BF16x3: hi and lo planes of both operands, then one flag per 128-row
     # block and 64-element slab of each operand and a counter (the leaf's
     # own conversion of its operands)
-    flags = (-(-300 // 128) + -(-200 // 128)) * -(-100 // 64) + 1
+    blocks = -(-300 // 128) + -(-200 // 128)
+    flags = blocks * 4 + blocks + 1  # 2 slabs, a block's flags padded to 4
     assert H.hpvm_workspace_size(ctx, nodes["root"], a) == 2 * (al(300 * kp * 2) + al(200 * kp * 2)) + al(4 * flags)
     a.tier = H.HPVM_TIER_BF16
     assert H.hpvm_workspace_size(ctx, nodes["root"], a) == al(300 * kp * 2) + al(200 * kp * 2)
@@ -324,8 +325,9 @@ def test_workspace_of_a_tail_split(ctx):
                       1.0, 0.0, False, True, tier)
         kp = (K + 7) // 8 * 8
         planes = (2 if tier == H.HPVM_TIER_BF16X3 else 1) * (al(M * kp * 2) + al(N * kp * 2))
-        if tier == H.HPVM_TIER_BF16X3:  # the in-leaf conversion's flags and counter (last)
-            planes += al(4 * ((-(-M // 128) + -(-N // 128)) * -(-K // 64) + 1))
+        if tier == H.HPVM_TIER_BF16X3:  # the in-leaf conversion's flags, counts and counter (last)
+            blocks = -(-M // 128) + -(-N // 128)
+            planes += al(4 * (blocks * ((-(-K // 64) + 3) // 4 * 4) + blocks + 1))
         return H.hpvm_workspace_size(ctx, nodes["root"], a) - planes
 
     for tier in (H.HPVM_TIER_BF16X3, H.HPVM_TIER_BF16):
@@ -360,8 +362,8 @@ def test_chain_workspace_holds_forwarded_planes(ctx):
 
     for tier, planes in ((H.HPVM_TIER_BF16, 1), (H.HPVM_TIER_BF16X3, 2)):
         stage = planes * (al(w * w * 2) + al(rows * w * 2))  # A (64 x 64) and B (48 x 64) planes
-        if tier == H.HPVM_TIER_BF16X3:  # the in-leaf conversion's flags (one block and slab each) and counter
-            stage += al(4 * ((1 + 1) * 1 + 1))
+        if tier == H.HPVM_TIER_BF16X3:  # the in-leaf conversion's flags (padded to 4 a block), counts, counter
+            stage += al(4 * ((1 + 1) * 4 + 2 + 1))
         region = planes * al(rows * w * 2)                    # C as the next B: 48 rows of 64
         assert H.hpvm_workspace_size(ctx, root, records(tier, 0)) == al(stage) + 2 * al(region)
         assert H.hpvm_workspace_size(ctx, root, records(tier, H.HPVM_LAUNCH_NO_FUSION)) == stage
