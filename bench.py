@@ -361,7 +361,7 @@ def chain_section(args, H, W, torch, local, world, barrier):
         dt = time.perf_counter() - t0
     dt = max_over_ranks(dt * 1e3, dev) * 1e-3
     out["streamed_forward"] = {"value": fwd * world / dt / 1e12, "ms_per_batch": dt * 1e3,
-                               "items": items, "path": "hpvm_launch(stream_graph=1) + 64 x hpvm_push + 64 x hpvm_pop"}
+                               "items": items, "path": "hpvm_launch(stream_graph=1) + hpvm_stream_coalesce(32) + 64 x hpvm_push + 64 x hpvm_pop"}
     eng.close()
     del Xd, Gd, Wd
     torch.cuda.empty_cache()

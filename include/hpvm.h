@@ -337,6 +337,27 @@ HPVM_API int hpvm_push(hpvm_graph* graph, const void* args, size_t args_size);
  * streaming graph waits for every item still queued and frees the graph. */
 HPVM_API int hpvm_pop(hpvm_graph* graph, void* out, size_t out_size, int64_t timeout_ms);
 
+/* Run up to `items` (>= 1) pushed items of a streaming graph as one
+ * launch (no counterpart in the paper; its pipelined stages of Section 3.5
+ * process items one at a time). With items > 1, hpvm_push queues an item
+ * and enqueues nothing until `items` are queued; hpvm_pop of a queued item
+ * and hpvm_wait launch whatever is queued. Queued items that share every
+ * record field but the first stage's B, the last stage's C and their N
+ * (the rows of the items: B is K x N with ldb = K, op(B) = B, C is M x N
+ * with ldc = M), with beta = 0, no auxiliary matrix and device pointers,
+ * run as one launch over the sum of their N: their B operands are used in
+ * place when they lie side by side in memory (in push order), else copied
+ * side by side into the slot's workspace; each stage runs once; the last
+ * result is written in place when the items' C lie side by side, else
+ * copied back to each item's C (the intermediate results of such a launch
+ * go to the workspace, not to the items' buffers). Others run one launch
+ * each. A push into a coalescing graph only queues the item (its records
+ * are checked when its group is launched, and a bad record is reported by
+ * the push, pop or wait that launches it). Each output is the same K sum as in a launch of its
+ * item alone, bit for bit, except where the wider launch splits its last
+ * round of tiles in K halves (many tiles, a short last round) and adds the
+ * halves. 1 (the default) launches every item when it is pushed. */
+HPVM_API int hpvm_stream_coalesce(hpvm_graph* graph, int items);
 /* Copy the description of what `graph` launched into *out. */
 HPVM_API int hpvm_graph_info(hpvm_graph* graph, hpvm_launch_info* out);
 

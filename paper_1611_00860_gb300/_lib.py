@@ -142,6 +142,7 @@ def _load() -> ctypes.CDLL:
         "hpvm_push": (I, [P, P, SZ]),
         "hpvm_pop": (I, [P, P, SZ, I64]),
         "hpvm_graph_info": (I, [P, ctypes.POINTER(LaunchInfo)]),
+        "hpvm_stream_coalesce": (I, [P, I]),
         "hpvm_track_mem": (I, [P, P, I64]),
         "hpvm_request_mem": (I, [P, P, I64]),
         "hpvm_untrack_mem": (I, [P, P]),
@@ -269,6 +270,10 @@ def hpvm_pop(graph: int, out=None, timeout_ms: int = -1) -> None:
 
 def hpvm_wait(graph: int, timeout_ms: int = -1) -> None:
     _check(LIB.hpvm_wait(graph, int(timeout_ms)))
+
+
+def hpvm_stream_coalesce(graph: int, items: int) -> None:
+    _check(LIB.hpvm_stream_coalesce(graph, int(items)))
 
 
 def hpvm_graph_info(graph: int) -> LaunchInfo:

@@ -27,6 +27,9 @@ library's kernels through the C-ABI. PyTorch provides memory and streams.
 """
 from __future__ import annotations
 
+import ctypes
+
+import numpy as np
 import torch
 
 from . import _lib as H
@@ -307,37 +310,66 @@ class ChainEngine:
         return dHs[0], dWs
 
     # -- streaming -----------------------------------------------------------------
-    def stream_forward(self, items, Ws, timeout_ms: int = 600000):
+    def stream_forward(self, items, Ws, timeout_ms: int = 600000, coalesce: int = 32):
         """Push every item (row-major rows x w) through the chain launched as a
-        streaming graph and pop the outputs in order (hpvm_push / hpvm_pop)."""
-        outs_all = [[torch.empty(X.shape[0], W.shape[1], device=X.device) for W in Ws] for X in items]
+        streaming graph and pop the outputs in order (hpvm_push / hpvm_pop).
+        ``coalesce`` items at a time run as one launch (hpvm_stream_coalesce):
+        an item alone fills a fraction of the GPU (4096 x 256 results are 16
+        tiles of 256 x 256)."""
+        L = self.layers
+        n = len(items)
+        # each stage's results of all items in one tensor (item after item):
+        # a coalesced launch writes them in place; item i's rows start at
+        # starts[i] (pointers computed, views made only where needed)
+        starts = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum([X.shape[0] for X in items], out=starts[1:])
+        stage_out = [torch.empty(int(starts[-1]), W.shape[1], device=items[0].device) for W in Ws]
+
+        def outs_of(i):
+            return [o[int(starts[i]):int(starts[i + 1])] for o in stage_out]
+
+        outs0 = outs_of(0)
         mid = H.HPVM_LAUNCH_PLANES_ONLY  # only the last stage's results are returned
-        rec0 = self.chain_records(items[0], Ws, outs_all[0], mid_flags=mid)
-        # items of one shape differ only in X and the stage results: later
-        # items' records are the first's with those pointers replaced
-        reuse = self.chain_records(items[0], Ws, outs_all[0], H.HPVM_LAUNCH_REUSE_A, mid_flags=mid)
-        g = H.hpvm_launch(self.ctx, self.chain, rec0, True, self._stream())
+        # every item's records in one array: the first item's converts the
+        # weights into the plane cache, later items reuse those planes; items
+        # of the first item's shape differ only in X and the stage results
+        size = ctypes.sizeof(H.RootArgs) * L
+        recs = (H.RootArgs * (L * n))()
+        first = self.chain_records(items[0], Ws, outs0, H.HPVM_LAUNCH_CACHE_A, mid_flags=mid)
+        reuse = self.chain_records(items[0], Ws, outs0, H.HPVM_LAUNCH_REUSE_A, mid_flags=mid)
+        same = np.array([i for i, X in enumerate(items) if i > 0 and X.shape == items[0].shape], dtype=np.int64)
+        raw = np.frombuffer(recs, dtype=np.uint8).reshape(n, size)
+        if same.size:
+            # the template copied to those items at once, then their X (B of
+            # stage 0) and stage results (C of every stage) patched in
+            raw[same] = np.frombuffer(reuse, dtype=np.uint8)
+            b_off, c_off = H.RootArgs.B.offset, H.RootArgs.C.offset
+            as_bytes = lambda p: np.ascontiguousarray(p, dtype="<i8").view(np.uint8).reshape(-1, 8)
+            raw[same, b_off:b_off + 8] = as_bytes([items[i].data_ptr() for i in same])
+            rec_bytes = ctypes.sizeof(H.RootArgs)
+            for l in range(L):
+                o = l * rec_bytes + c_off
+                ptrs = stage_out[l].data_ptr() + starts[same] * (stage_out[l].shape[1] * 4)
+                raw[same, o:o + 8] = as_bytes(ptrs)
+        for i, X in enumerate(items):
+            if i == 0 or X.shape != items[0].shape:
+                src = first if i == 0 else self.chain_records(X, Ws, outs_of(i), H.HPVM_LAUNCH_REUSE_A, mid_flags=mid)
+                ctypes.memmove(ctypes.addressof(recs) + i * size, ctypes.addressof(src), size)
+        g = H.hpvm_launch(self.ctx, self.chain, self.chain_records(items[0], Ws, outs0, mid_flags=mid),
+                          True, self._stream())
         try:
-            for i, (X, outs) in enumerate(zip(items, outs_all)):
-                # the weights are the same for every item: converted once
-                if i == 0:
-                    rec = self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_CACHE_A, mid_flags=mid)
-                elif X.shape == items[0].shape:
-                    rec = type(reuse).from_buffer_copy(reuse)
-                    rec[0].B = X.data_ptr()
-                    for l, o in enumerate(outs):
-                        rec[l].C = o.data_ptr()
-                else:
-                    rec = self.chain_records(X, Ws, outs, H.HPVM_LAUNCH_REUSE_A, mid_flags=mid)
-                H.hpvm_push(g, rec)
+            H.hpvm_stream_coalesce(g, coalesce)
+            for i in range(len(items)):
+                H.hpvm_push(g, (H.RootArgs * L).from_buffer(recs, i * size))
             popped = []
+            rec = (H.RootArgs * L)()
             for _ in items:
-                rec = (H.RootArgs * self.layers)()
                 H.hpvm_pop(g, rec, timeout_ms)
-                popped.append(rec[self.layers - 1].C)
+                popped.append(rec[L - 1].C)
         finally:
             H.hpvm_wait(g, timeout_ms)
-        results = [outs[-1] for outs in outs_all]
+        last = stage_out[-1]
+        results = [last[int(starts[i]):int(starts[i + 1])] for i in range(n)]
         assert popped == [r.data_ptr() for r in results]
         return results
 

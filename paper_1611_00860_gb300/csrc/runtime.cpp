@@ -152,10 +152,12 @@ struct TrackEntry {
   bool written_set = false;
 };
 
-// one pushed item of a streaming graph
+// one pushed item of a streaming graph (launched: enqueued on a stream;
+// not yet when it waits to run together with later items)
 struct StreamItem {
   std::vector<uint8_t> record;
   cudaEvent_t done = nullptr;
+  bool launched = false;
 };
 
 struct hpvm_graph {
@@ -171,7 +173,9 @@ struct hpvm_graph {
   std::vector<size_t> slot_ws_bytes;
   std::deque<StreamItem> items;
   std::vector<cudaEvent_t> spare_events;  // events of popped items, reused
-  uint64_t pushed = 0;
+  uint64_t pushed = 0;    // items pushed (slot of the next per-item launch)
+  uint64_t launches = 0;  // launches made for items (one per item, or per coalesced group)
+  int coalesce = 1;       // queued items run as one launch once this many wait
   uint64_t validated = ~uint64_t(0);  // the context's structure version validated at launch
 };
 
@@ -224,6 +228,12 @@ struct hpvm_ctx {
   // unless this moved
   uint64_t structure = 0;
   cudaStream_t copy_stream = nullptr;  // request_mem's device -> host copies
+  // streams and slot workspaces of finished streaming graphs, kept for the
+  // next streaming graph (a streaming graph per batch of items would
+  // otherwise create streams and allocate workspace every time)
+  std::vector<cudaStream_t> spare_streams;
+  std::vector<std::pair<void*, size_t>> spare_ws;
+  std::vector<cudaEvent_t> spare_events;
 };
 
 // ---------------------------------------------------------------------------
@@ -1113,17 +1123,215 @@ int check_status(hpvm_ctx* ctx) {
   return HPVM_OK;
 }
 
-void free_graph(hpvm_graph* g) {
+// ---- streaming: items run one launch each, or several as one launch ----------
+cudaEvent_t take_event(hpvm_graph* g) {
+  cudaEvent_t ev = nullptr;
+  if (!g->spare_events.empty()) {
+    ev = g->spare_events.back();
+    g->spare_events.pop_back();
+  } else if (!g->ctx->spare_events.empty()) {
+    ev = g->ctx->spare_events.back();
+    g->ctx->spare_events.pop_back();
+  } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    ev = nullptr;
+  }
+  return ev;
+}
+
+// One item on the next stream of the ring.
+int launch_item(hpvm_graph* g, StreamItem& it) {
+  hpvm_ctx* ctx = g->ctx;
+  Plan P;
+  int rc = lower_graph(g->root, it.record.data(), it.record.size(), &P, g->validated == ctx->structure);
+  if (rc != HPVM_OK) return rc;
+  const int slot = (int)(g->launches % g->slots.size());
+  cudaStream_t s = g->slots[slot];
+  if ((rc = grow_buffer(&g->slot_ws[slot], &g->slot_ws_bytes[slot], plan_workspace(P), s)) != HPVM_OK) return rc;
+  hpvm_launch_info inf;
+  if ((rc = execute_plan(ctx, P, s, g->slot_ws[slot], g->slot_ws_bytes[slot], &inf)) != HPVM_OK) return rc;
+  if (!it.done && !(it.done = take_event(g))) return fail(HPVM_ERR_CUDA, "cudaEventCreate failed");
+  cudaEventRecord(it.done, s);
+  it.launched = true;
+  g->info = inf;
+  g->launches++;
+  return HPVM_OK;
+}
+
+// Whether items can run as one launch: the same records but for stage 0's
+// B (each item's own, K x N_j column-major with ldb = K, op(B) = B), the
+// last stage's C (each item's own, ldc = M) and the items' N; every stage
+// with beta = 0 (C is not read) and no auxiliary matrix, every pointer on
+// the device; the plane-cache flags may differ only in CACHE_A / REUSE_A
+// (the items share A: the group converts it if any item asks for it), and
+// none may cache B or C. Then the stages run once over N = sum N_j: the items' B
+// operands copied side by side into one matrix, every stage's result into
+// one matrix (two alternating), the last one copied back out to the
+// items' C.
+bool coalescible(hpvm_ctx* ctx, const std::vector<StreamItem*>& batch, int nrec) {
+  using R = hpvm_sgemm_root_args;
+  if (batch.size() < 2 || nrec < 1) return false;
+  const R* r0 = reinterpret_cast<const R*>(batch[0]->record.data());
+  for (auto* it : batch) {
+    if ((int)(it->record.size() / sizeof(R)) != nrec) return false;
+    const R* r = reinterpret_cast<const R*>(it->record.data());
+    for (int l = 0; l < nrec; ++l) {
+      const R& a = r0[l];
+      const R& b = r[l];
+      if (b.beta != 0.f || b.aux || b.A != a.A || b.lda != a.lda || b.M != a.M || b.k != a.k ||
+          b.transA != a.transA || b.transB != a.transB || b.tier != a.tier ||
+          ((b.flags ^ a.flags) & ~(HPVM_LAUNCH_CACHE_A | HPVM_LAUNCH_REUSE_A)) ||
+          (b.flags & (HPVM_LAUNCH_CACHE_B | HPVM_LAUNCH_REUSE_B | HPVM_LAUNCH_CACHE_C)) ||
+          b.alpha != a.alpha || b.block_x != a.block_x || b.block_y != a.block_y || b.grid_x != a.grid_x ||
+          b.N != r[0].N || b.N <= 0 || b.ldc != b.M || !b.C)
+        return false;
+      if (l > 0 && b.B) return false;  // later stages read the previous stage's result
+      int64_t off;
+      if (find_tracked(ctx, b.C, &off)) return false;
+    }
+    int64_t off;
+    if (!r[0].B || r[0].transB || r[0].ldb != r[0].k || find_tracked(ctx, r[0].B, &off)) return false;
+  }
+  return true;
+}
+
+int launch_coalesced(hpvm_graph* g, std::vector<StreamItem*>& batch) {
+  using R = hpvm_sgemm_root_args;
+  hpvm_ctx* ctx = g->ctx;
+  const int nrec = (int)(batch[0]->record.size() / sizeof(R));
+  std::vector<R> rec(nrec);
+  memcpy(rec.data(), batch[0]->record.data(), nrec * sizeof(R));
+  for (int l = 0; l < nrec; ++l)  // A converted into the cache if any item asks for it
+    for (auto* it : batch)
+      if (reinterpret_cast<const R*>(it->record.data())[l].flags & HPVM_LAUNCH_CACHE_A) {
+        rec[l].flags = (rec[l].flags & ~HPVM_LAUNCH_REUSE_A) | HPVM_LAUNCH_CACHE_A;
+        break;
+      }
+  std::vector<int64_t> off(batch.size() + 1, 0);
+  for (size_t j = 0; j < batch.size(); ++j)
+    off[j + 1] = off[j] + reinterpret_cast<const R*>(batch[j]->record.data())[0].N;
+  const int64_t N = off.back();
+  const int64_t K0 = rec[0].k;
+  int64_t Mmax = 0;
+  for (auto& r : rec) Mmax = std::max<int64_t>(Mmax, r.M);
+  // The items' first operands, or their last results, that already lie side
+  // by side in memory (say views of one batch tensor) are used in place;
+  // otherwise they are gathered into (returned from) the workspace.
+  auto adjacent = [&](int l, bool c) {
+    const float* base = c ? reinterpret_cast<const R*>(batch[0]->record.data())[l].C
+                          : reinterpret_cast<const R*>(batch[0]->record.data())[l].B;
+    const int64_t ld = c ? rec[l].M : K0;
+    for (size_t j = 1; j < batch.size(); ++j) {
+      const R& r = reinterpret_cast<const R*>(batch[j]->record.data())[l];
+      if ((c ? r.C : r.B) != base + off[j] * ld) return false;
+    }
+    return true;
+  };
+  const bool b_in_place = adjacent(0, false), c_in_place = adjacent(nrec - 1, true);
+  const size_t xbytes = b_in_place ? 0 : align256((size_t)K0 * N * 4), cbytes = align256((size_t)Mmax * N * 4);
+  // the combined records: N summed, the tile grid along N to match, stage
+  // 0's B and every stage's C in the scratch matrices (pointers set once the
+  // workspace is placed)
+  auto fill = [&](uint8_t* scratch) {
+    for (int l = 0; l < nrec; ++l) {
+      R& r = rec[l];
+      r.N = (int32_t)N;
+      r.grid_y = (int32_t)((N + r.block_y - 1) / r.block_y);
+      r.C = reinterpret_cast<float*>(scratch + xbytes + (l & 1) * cbytes);
+      r.bytesC = (int64_t)r.M * N * 4;
+    }
+    if (c_in_place) rec[nrec - 1].C = reinterpret_cast<const R*>(batch[0]->record.data())[nrec - 1].C;
+    rec[0].B = b_in_place ? reinterpret_cast<const R*>(batch[0]->record.data())[0].B
+                          : reinterpret_cast<float*>(scratch);
+    rec[0].bytesB = K0 * N * 4;
+  };
+  fill(reinterpret_cast<uint8_t*>(uintptr_t(256)));
+  Plan P;
+  int rc = lower_graph(g->root, rec.data(), nrec * sizeof(R), &P, g->validated == ctx->structure);
+  if (rc != HPVM_OK) return rc;
+  const size_t wsb = align256(plan_workspace(P));
+  const int slot = (int)(g->launches % g->slots.size());
+  cudaStream_t s = g->slots[slot];
+  if ((rc = grow_buffer(&g->slot_ws[slot], &g->slot_ws_bytes[slot], wsb + xbytes + 2 * cbytes, s)) != HPVM_OK)
+    return rc;
+  uint8_t* scratch = static_cast<uint8_t*>(g->slot_ws[slot]) + wsb;
+  fill(scratch);
+  if ((rc = lower_graph(g->root, rec.data(), nrec * sizeof(R), &P, true)) != HPVM_OK) return rc;
+  cudaError_t e;
+  for (size_t j = 0; j < batch.size() && !b_in_place; ++j) {
+    const R& r = reinterpret_cast<const R*>(batch[j]->record.data())[0];
+    if ((e = cudaMemcpyAsync(scratch + off[j] * K0 * 4, r.B, (size_t)(off[j + 1] - off[j]) * K0 * 4,
+                             cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "gathering the items' operands");
+  }
+  hpvm_launch_info inf;
+  if ((rc = execute_plan(ctx, P, s, g->slot_ws[slot], wsb, &inf)) != HPVM_OK) return rc;
+  const R& last = rec[nrec - 1];
+  for (size_t j = 0; j < batch.size() && !c_in_place; ++j) {
+    const R& r = reinterpret_cast<const R*>(batch[j]->record.data())[nrec - 1];
+    if ((e = cudaMemcpyAsync(r.C, reinterpret_cast<const uint8_t*>(last.C) + off[j] * last.M * 4,
+                             (size_t)(off[j + 1] - off[j]) * last.M * 4, cudaMemcpyDeviceToDevice, s)) !=
+        cudaSuccess)
+      return cuda_fail(e, "returning the items' results");
+  }
+  for (auto* it : batch) {
+    if (!it->done && !(it->done = take_event(g))) return fail(HPVM_ERR_CUDA, "cudaEventCreate failed");
+    cudaEventRecord(it->done, s);
+    it->launched = true;
+  }
+  g->info = inf;
+  g->launches++;
+  return HPVM_OK;
+}
+
+// Launch every queued item: groups of up to g->coalesce items that can run
+// as one launch do, the others one by one.
+int flush_items(hpvm_graph* g) {
+  std::vector<StreamItem*> waiting;
+  for (auto& it : g->items)
+    if (!it.launched) waiting.push_back(&it);
+  size_t i = 0;
+  while (i < waiting.size()) {
+    const size_t n = std::min<size_t>(waiting.size() - i, (size_t)std::max(1, g->coalesce));
+    std::vector<StreamItem*> batch(waiting.begin() + i, waiting.begin() + i + n);
+    int rc;
+    const int nrec = (int)(batch[0]->record.size() / sizeof(hpvm_sgemm_root_args));
+    if (n > 1 && coalescible(g->ctx, batch, nrec)) {
+      rc = launch_coalesced(g, batch);
+    } else {
+      rc = HPVM_OK;
+      for (auto* it : batch)
+        if ((rc = launch_item(g, *it)) != HPVM_OK) break;
+    }
+    if (rc != HPVM_OK) return rc;
+    i += n;
+  }
+  return HPVM_OK;
+}
+
+// keep: hand the streams, slot workspaces and events to the context for
+// the next streaming graph (after the graph's work is done); otherwise
+// destroy them
+void free_graph(hpvm_graph* g, bool keep = false) {
+  hpvm_ctx* ctx = g->ctx;
   if (g->done) cudaEventDestroy(g->done);
   for (auto& it : g->items)
     if (it.done) cudaEventDestroy(it.done);
-  for (auto ev : g->spare_events) cudaEventDestroy(ev);
-  for (size_t i = 0; i < g->slots.size(); ++i) {
+  for (auto ev : g->spare_events) {
+    if (keep) ctx->spare_events.push_back(ev);
+    else cudaEventDestroy(ev);
+  }
+  // (last slot first: the next graph, taking them from the back, gets each
+  // slot's workspace back in the same slot, sized for the same work)
+  for (size_t i = g->slots.size(); i-- > 0;) {
     if (g->slots[i]) {
       cudaStreamSynchronize(g->slots[i]);
-      cudaStreamDestroy(g->slots[i]);
+      if (keep) ctx->spare_streams.push_back(g->slots[i]);
+      else cudaStreamDestroy(g->slots[i]);
     }
-    if (g->slot_ws[i]) cudaFree(g->slot_ws[i]);
+    if (g->slot_ws[i]) {
+      if (keep) ctx->spare_ws.emplace_back(g->slot_ws[i], g->slot_ws_bytes[i]);
+      else cudaFree(g->slot_ws[i]);
+    }
   }
   delete g;
 }
@@ -1179,6 +1387,9 @@ int hpvm_cleanup(hpvm_ctx* ctx) {
       if (t.written) cudaEventDestroy(t.written);
     }
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (auto st : ctx->spare_streams) cudaStreamDestroy(st);
+    for (auto& w : ctx->spare_ws) cudaFree(w.first);
+    for (auto ev : ctx->spare_events) cudaEventDestroy(ev);
     if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
     if (ctx->ws_event) cudaEventDestroy(ctx->ws_event);
     if (ctx->status.host) cudaFreeHost(ctx->status.host);
@@ -1408,12 +1619,20 @@ int hpvm_launch(hpvm_ctx* ctx, hpvm_node* root, const void* args, size_t args_si
     g->slot_ws.assign(kStreamSlots, nullptr);
     g->slot_ws_bytes.assign(kStreamSlots, 0);
     for (int i = 0; i < kStreamSlots; ++i) {
-      if ((e = cudaStreamCreateWithFlags(&g->slots[i], cudaStreamNonBlocking)) != cudaSuccess) {
+      if (!ctx->spare_streams.empty()) {
+        g->slots[i] = ctx->spare_streams.back();
+        ctx->spare_streams.pop_back();
+      } else if ((e = cudaStreamCreateWithFlags(&g->slots[i], cudaStreamNonBlocking)) != cudaSuccess) {
         cudaEventDestroy(start);
         free_graph(g.release());
         return cuda_fail(e, "cudaStreamCreate");
       }
       cudaStreamWaitEvent(g->slots[i], start, 0);
+      if (!ctx->spare_ws.empty()) {
+        g->slot_ws[i] = ctx->spare_ws.back().first;
+        g->slot_ws_bytes[i] = ctx->spare_ws.back().second;
+        ctx->spare_ws.pop_back();
+      }
     }
     cudaEventDestroy(start);
     *out = g.get();
@@ -1463,28 +1682,31 @@ int hpvm_push(hpvm_graph* g, const void* args, size_t args_size) {
   hpvm_ctx* ctx = g->ctx;
   if (!ctx->graphs.count(g)) return fail(HPVM_ERR_INVALID_ARG, "unknown or finished graph handle");
   if (!g->streaming) return fail(HPVM_ERR_INVALID_ARG, "push needs a graph launched as a streaming graph");
-  Plan P;
-  int rc = lower_graph(g->root, args, args_size, &P, g->validated == ctx->structure);
-  if (rc != HPVM_OK) return rc;
+  int rc;
+  if (g->coalesce <= 1 || g->validated != ctx->structure) {
+    // the structure is validated again when it changed since the last check;
+    // a coalescing graph lowers its records when their group is launched
+    Plan P;
+    if ((rc = lower_graph(g->root, args, args_size, &P, g->validated == ctx->structure)) != HPVM_OK) return rc;
+    g->validated = ctx->structure;
+  } else if (!args || args_size < kRecBytes) {
+    return fail(HPVM_ERR_INVALID_ARG, "argument record too small (%zu < %zu bytes)", args_size, kRecBytes);
+  }
   cudaSetDevice(ctx->device);
-  const int slot = (int)(g->pushed % g->slots.size());
-  cudaStream_t s = g->slots[slot];
-  if ((rc = grow_buffer(&g->slot_ws[slot], &g->slot_ws_bytes[slot], plan_workspace(P), s)) != HPVM_OK) return rc;
-  hpvm_launch_info inf;
-  if ((rc = execute_plan(ctx, P, s, g->slot_ws[slot], g->slot_ws_bytes[slot], &inf)) != HPVM_OK) return rc;
   StreamItem it;
   it.record.assign(static_cast<const uint8_t*>(args), static_cast<const uint8_t*>(args) + args_size);
-  if (!g->spare_events.empty()) {
-    it.done = g->spare_events.back();
-    g->spare_events.pop_back();
-  } else {
-    cudaError_t e = cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-  }
-  cudaEventRecord(it.done, s);
   g->items.push_back(std::move(it));
-  g->info = inf;
   g->pushed++;
+  if (g->coalesce <= 1) {
+    if ((rc = launch_item(g, g->items.back())) != HPVM_OK) {
+      g->items.pop_back();
+      return rc;
+    }
+    return ok();
+  }
+  size_t waiting = 0;
+  for (auto& q : g->items) waiting += !q.launched;
+  if ((int)waiting >= g->coalesce && (rc = flush_items(g)) != HPVM_OK) return rc;
   return ok();
 }
 
@@ -1495,6 +1717,10 @@ int hpvm_pop(hpvm_graph* g, void* out, size_t out_size, int64_t timeout_ms) {
   if (!g->streaming) return fail(HPVM_ERR_INVALID_ARG, "pop needs a graph launched as a streaming graph");
   if (g->items.empty()) return fail(HPVM_ERR_INVALID_ARG, "pop on a stream with no pushed item");
   cudaSetDevice(ctx->device);
+  if (!g->items.front().launched) {
+    int rc0 = flush_items(g);
+    if (rc0 != HPVM_OK) return rc0;
+  }
   StreamItem& it = g->items.front();
   int rc = wait_event(it.done, timeout_ms);
   if (rc == HPVM_ERR_TIMEOUT) return rc;  // the item stays queued
@@ -1513,11 +1739,16 @@ int hpvm_wait(hpvm_graph* g, int64_t timeout_ms) {
   cudaSetDevice(ctx->device);
   int rc = HPVM_OK;
   if (g->streaming) {
+    // items still queued run now; if that fails, the launched ones are
+    // still waited for before the graph is freed
+    const int frc = flush_items(g);
     for (auto& it : g->items) {
+      if (!it.launched) continue;
       rc = wait_event(it.done, timeout_ms);
       if (rc == HPVM_ERR_TIMEOUT) return rc;
       if (rc != HPVM_OK) break;
     }
+    if (rc == HPVM_OK && frc != HPVM_OK) rc = frc;
   } else if (g->done) {
     rc = wait_event(g->done, timeout_ms);
     if (rc == HPVM_ERR_TIMEOUT) return rc;
@@ -1527,8 +1758,20 @@ int hpvm_wait(hpvm_graph* g, int64_t timeout_ms) {
   }
   if (rc == HPVM_OK) rc = check_status(ctx);
   ctx->graphs.erase(g);
-  free_graph(g);
+  free_graph(g, g->streaming && rc == HPVM_OK);  // a finished streaming graph's streams serve the next one
   return rc == HPVM_OK ? ok() : rc;
+}
+
+int hpvm_stream_coalesce(hpvm_graph* g, int items) {
+  if (!g || items < 1) return fail(HPVM_ERR_INVALID_ARG, "graph is NULL or items < 1");
+  if (!g->ctx->graphs.count(g)) return fail(HPVM_ERR_INVALID_ARG, "unknown or finished graph handle");
+  if (!g->streaming) return fail(HPVM_ERR_INVALID_ARG, "coalescing applies to a streaming graph");
+  g->coalesce = items;
+  if (items == 1) {
+    cudaSetDevice(g->ctx->device);
+    return flush_items(g) == HPVM_OK ? ok() : HPVM_ERR_CUDA;
+  }
+  return ok();
 }
 
 int hpvm_graph_info(hpvm_graph* g, hpvm_launch_info* out) {

@@ -534,3 +534,74 @@ def test_chain_workload_sampled_rows(cuda_device):
         assert np.isfinite(Wd[0].grad.cpu().numpy()).all()
     finally:
         eng.close()
+
+
+@pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16, H.HPVM_TIER_BF16X3])
+@pytest.mark.parametrize("coalesce", [2, 3, 4])
+@pytest.mark.parametrize("adjacent", [False, True])
+def test_coalesced_streaming_equals_item_by_item(cuda_device, tier, coalesce, adjacent):
+    # Items of one streaming graph run several at a time as one launch
+    # (hpvm_stream_coalesce): 7 items, so the last group is short, of
+    # differing rows (the columns of one item do not start on a tile
+    # boundary). Each output must equal the item pushed alone, bit for bit
+    # (these launches are too small to split a last round), pops come back
+    # in push order, and a pop of a queued item launches the queue.
+    layers, w = 3, 264
+    rows = [256, 100, 256, 77, 300, 256, 128]
+    g = torch.Generator().manual_seed(coalesce)
+    if adjacent:  # views of one tensor, item after item: used in place
+        whole = torch.randn(sum(rows), w, generator=g).cuda()
+        starts = [sum(rows[:i]) for i in range(len(rows) + 1)]
+        items = [whole[starts[i]:starts[i + 1]] for i in range(len(rows))]
+    else:         # separate tensors: gathered into the workspace
+        items = [torch.randn(r, w, generator=g).cuda() for r in rows]
+    Ws = [(torch.randn(w, w, generator=g) / w ** 0.5).cuda() for _ in range(layers)]
+    eng = ChainEngine(layers, tier=tier)
+    try:
+        one = eng.stream_forward(items, Ws, coalesce=1)
+        many = eng.stream_forward(items, Ws, coalesce=coalesce)
+        torch.cuda.synchronize()
+        for a, b in zip(one, many):
+            assert torch.equal(a, b)
+        if tier == H.HPVM_TIER_BF16:  # (the item-by-item results are checked against the oracle above)
+            _, _, ref = J.chain_forward(items[1].double().cpu().numpy(), [W.double().cpu().numpy() for W in Ws])
+            assert O.normwise_rel_err(many[1].double().cpu().numpy(), ref) <= TOL[tier]
+        # pop before the queue is full: the queued item is launched by the pop
+        outs = [torch.full((rows[0], w), float("nan"), device="cuda") for _ in range(layers)]
+        rec = eng.chain_records(items[0], Ws, outs)
+        gr = H.hpvm_launch(eng.ctx, eng.chain, rec, True, 0)
+        H.hpvm_stream_coalesce(gr, 8)
+        H.hpvm_push(gr, rec)
+        H.hpvm_pop(gr, None, 60000)
+        H.hpvm_wait(gr, 60000)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[-1], one[0])
+    finally:
+        eng.close()
+
+
+def test_coalescing_falls_back_for_items_that_differ(cuda_device):
+    # an item whose weights differ from the others' runs on its own, with
+    # the same result as when every item runs alone
+    layers, w, r = 2, 136, 64
+    g = torch.Generator().manual_seed(9)
+    Ws = [(torch.randn(w, w, generator=g) / w ** 0.5).cuda() for _ in range(layers)]
+    W2 = [(torch.randn(w, w, generator=g) / w ** 0.5).cuda() for _ in range(layers)]
+    X = [torch.randn(r, w, generator=g).cuda() for _ in range(4)]
+    eng = ChainEngine(layers, tier=H.HPVM_TIER_BF16)
+    try:
+        outs = [[torch.empty(r, w, device="cuda") for _ in range(layers)] for _ in range(4)]
+        ref = [[torch.empty(r, w, device="cuda") for _ in range(layers)] for _ in range(4)]
+        for coalesce, dst in ((4, outs), (1, ref)):
+            gr = H.hpvm_launch(eng.ctx, eng.chain, eng.chain_records(X[0], Ws, dst[0]), True, 0)
+            H.hpvm_stream_coalesce(gr, coalesce)
+            for i in range(4):
+                H.hpvm_push(gr, eng.chain_records(X[i], W2 if i == 2 else Ws, dst[i]))
+            for _ in range(4):
+                H.hpvm_pop(gr, None, 60000)
+            H.hpvm_wait(gr, 60000)
+        torch.cuda.synchronize()
+        for a, b in zip(outs, ref):
+            assert torch.equal(a[-1], b[-1])
+    finally:
+        eng.close()
