@@ -535,6 +535,16 @@ HPVM_API int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, cons
  * MMA or tensor memory is involved and the context stays usable. */
 HPVM_API int hpvm_selftest_wait_timeout(hpvm_ctx* ctx, int64_t limit_ms, void* cuda_stream);
 
+/* Limit of each bounded wait inside the tensor-core leaves of this
+ * context's later launches, in microseconds (0: the default of 2 s;
+ * 1..10^7). No paper counterpart. A wait that runs past it gives up: the
+ * kernel records it in the status word, stops every role, waits (bounded
+ * by the default) for the copies and MMAs it started, frees its tensor
+ * memory and returns, and hpvm_wait reports HPVM_ERR_DEVICE_FAULT. A short
+ * limit makes the waits of a normal launch run out, which is how the
+ * failure path is tested; the context stays usable. */
+HPVM_API int hpvm_set_wait_limit(hpvm_ctx* ctx, int64_t limit_us);
+
 /* Thread-local message of the last failed call ("" if none). */
 HPVM_API const char* hpvm_last_error(void);
 /* ABI version (major * 100 + minor). */

@@ -167,6 +167,7 @@ def _load() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_int64), I, ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_int32), I64, ctypes.POINTER(ctypes.c_int64)]),
         "hpvm_selftest_wait_timeout": (I, [P, I64, P]),
+        "hpvm_set_wait_limit": (I, [P, I64]),
         "hpvm_last_error": (ctypes.c_char_p, []),
         "hpvm_version": (I, []),
     }
@@ -408,6 +409,10 @@ def hpvm_batch_plan(M, N, K, policy: int):
 def hpvm_selftest_wait_timeout(ctx: int, limit_ms: int, cuda_stream: int = 0) -> None:
     """Raises HpvmError(HPVM_ERR_DEVICE_FAULT) when the bounded wait gave up, as it must."""
     _check(LIB.hpvm_selftest_wait_timeout(ctx, int(limit_ms), cuda_stream or None))
+
+
+def hpvm_set_wait_limit(ctx: int, limit_us: int) -> None:
+    _check(LIB.hpvm_set_wait_limit(ctx, int(limit_us)))
 
 
 def hpvm_last_error() -> str:

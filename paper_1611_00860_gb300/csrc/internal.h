@@ -40,6 +40,7 @@ struct KernelReport {
 struct DeviceStatus {
   int* dev = nullptr;   // device-visible address (mapped pinned memory)
   int* host = nullptr;  // host address of the same word
+  uint32_t wait_limit_us = 0;  // limit of each bounded wait in the kernels (0: 2 s)
 };
 
 // Optional CUDA events recorded on the launch stream right before and right

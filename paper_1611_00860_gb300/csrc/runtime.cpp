@@ -1762,6 +1762,14 @@ int hpvm_wait(hpvm_graph* g, int64_t timeout_ms) {
   return rc == HPVM_OK ? ok() : rc;
 }
 
+int hpvm_set_wait_limit(hpvm_ctx* ctx, int64_t limit_us) {
+  if (!ctx) return fail(HPVM_ERR_INVALID_ARG, "ctx is NULL");
+  if (limit_us < 0 || limit_us > 10000000)
+    return fail(HPVM_ERR_INVALID_ARG, "wait limit %lld us is outside 0..10^7", (long long)limit_us);
+  ctx->status.wait_limit_us = (uint32_t)limit_us;
+  return ok();
+}
+
 int hpvm_stream_coalesce(hpvm_graph* g, int items) {
   if (!g || items < 1) return fail(HPVM_ERR_INVALID_ARG, "graph is NULL or items < 1");
   if (!g->ctx->graphs.count(g)) return fail(HPVM_ERR_INVALID_ARG, "unknown or finished graph handle");

@@ -73,7 +73,7 @@ constexpr int LAUNCH_REGS = 168;
 // 48/224 differ by variant, and each takes the one that spills least.
 template <int MODE, int EPI, bool PAIR, bool CONVERT = false>
 struct RegSplit {
-  static constexpr int EPI_R = (MODE == 8 || (MODE == 3 && EPI == 2)) ? 224 : 232;
+  static constexpr int EPI_R = EPI == 2 ? 224 : 232;
   static constexpr int CTRL_R = EPI_R == 224 ? 48 : 40;
   static_assert(EPI_WARP0 * 32 * CTRL_R + EPI_WARPS * 32 * EPI_R <= THREADS * LAUNCH_REGS,
                 "register split exceeds the launch's registers");
@@ -181,7 +181,13 @@ struct TcParams {
   float* split_ws;
   // 1: C itself is not stored (only the planes of it this launch writes)
   int planes_only;
+  // limit of each bounded wait in microseconds (0: WAIT_LIMIT_NS)
+  uint32_t wait_limit_us;
 };
+static_assert(sizeof(TcParams) <= 128, "the leaf's parameters stay within 128 bytes");
+__device__ __forceinline__ uint64_t wait_limit(const TcParams& p) {
+  return p.wait_limit_us ? (uint64_t)p.wait_limit_us * 1000ull : WAIT_LIMIT_NS;
+}
 
 // In-leaf operand conversion (the BF16x3 leaf on pairs, op(A) and op(B)^T
 // with their rows contiguous, as in the example's NT form): instead of two
@@ -267,8 +273,40 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
 }
+// try_wait with a suspend-time hint: a thread whose phase is not complete
+// sleeps at most about hint_ns (it wakes as soon as the phase completes), so
+// a bounded wait regains control at a rate set by its own limit.
+template <bool CLUSTER = false>
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  if constexpr (CLUSTER) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+  }
+  return ok != 0;
+}
+// The hint of a bounded wait's polls: a quarter of its limit (the clock is
+// read every fourth poll), at most 20 us, so a raised abort flag is seen
+// within about 80 us even under the default 2 s limit.
+__device__ __forceinline__ uint32_t poll_hint(uint64_t limit_ns) {
+  const uint64_t h = limit_ns >> 2;
+  return h < 32ull ? 32u : h > 20000ull ? 20000u : (uint32_t)h;
+}
 // Wait for the phase of `bar` with the given parity. Gives up (returns
-// false) when another role raised the abort flag or after WAIT_LIMIT_NS, in
+// false) when another role raised the abort flag or after limit_ns, in
 // which case it records `code` in the status word and raises the flag.
 // peer_abort: shared::cluster address of the peer CTA's abort flag (a pair
 // of CTAs on one tile), raised too so the peer stops waiting; 0 for none.
@@ -276,11 +314,12 @@ template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           int* status, int code, uint64_t limit_ns = WAIT_LIMIT_NS,
                                           uint32_t peer_abort = 0) {
-  if (mbar_try_wait<CLUSTER>(bar, parity)) return true;
+  const uint32_t hint = poll_hint(limit_ns);
+  if (mbar_try_wait_hint<CLUSTER>(bar, parity, hint)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t n = 1;; ++n) {
-    if (mbar_try_wait<CLUSTER>(bar, parity)) return true;
-    if ((n & 63u) == 0) {
+    if (mbar_try_wait_hint<CLUSTER>(bar, parity, hint)) return true;
+    if ((n & 3u) == 0) {
       if (*abort_flag) return false;
       if (globaltimer() - t0 > limit_ns) {
         if (status) atomicOr_system(status, code);
@@ -295,26 +334,40 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
 // all lanes poll the barrier, and lane 0 alone decides to give up (abort
 // raised, or the limit passed), so the warp never splits between the two
 // outcomes.
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                               int* status, int code) {
+                                               int* status, int code, uint64_t limit_ns = WAIT_LIMIT_NS,
+                                               uint32_t peer_abort = 0) {
   const int lane = threadIdx.x & 31;
   const uint64_t t0 = globaltimer();
+  const uint32_t hint = poll_hint(limit_ns);
   for (uint32_t n = 1;; ++n) {
-    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
-    if ((n & 63u) == 0) {
+    if (__all_sync(0xffffffffu, mbar_try_wait_hint<CLUSTER>(bar, parity, hint))) return true;
+    if ((n & 3u) == 0) {
       int give_up = 0;
       if (lane == 0) {
         if (*abort_flag) {
           give_up = 1;
-        } else if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+        } else if (globaltimer() - t0 > limit_ns) {
           if (status) atomicOr_system(status, code);
           *abort_flag = 1;
+          if (peer_abort) st_cluster_u32(peer_abort, 1);
           give_up = 1;
         }
       }
       if (__shfl_sync(0xffffffffu, give_up, 0)) return false;
     }
   }
+}
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t cluster_addr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(cluster_addr) : "memory");
+  return v;
+}
+// Count tx bytes as arrived on an mbarrier's current phase (the drain uses
+// it for loads a stage expected that were never issued).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0,
                                             int c1) {
@@ -860,14 +913,14 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
 // warp), bounded as mbar_wait is; then order the TMA loads that follow
 // after the converter's writes.
 __device__ __forceinline__ bool flag_wait(const int* flag, volatile int* abort_flag, int* status, int code,
-                                          uint32_t peer_abort) {
+                                          uint32_t peer_abort, uint64_t limit_ns) {
   if (ld_acquire_gpu(flag) == 0) {
     const uint64_t t0 = globaltimer();
     for (uint32_t n = 1;; ++n) {
       if (ld_acquire_gpu(flag) != 0) break;
       if ((n & 15u) == 0) {
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+        if (globaltimer() - t0 > limit_ns) {
           if (status) atomicOr_system(status, code);
           *abort_flag = 1;
           if (peer_abort) st_cluster_u32(peer_abort, 1);
@@ -886,7 +939,7 @@ __device__ __forceinline__ bool flag_wait(const int* flag, volatile int* abort_f
 // [R * CV_TAB + 4]); bar, buf: this warp's two piece barriers and staging
 // buffers. Claims chunks until none is left or the kernel aborts.
 __device__ __forceinline__ void cv_convert(const ConvParams& cv, const int* tab, uint64_t* bar, uint8_t* buf,
-                                        int lane, volatile int* abort_flag, int* status) {
+                                        int lane, volatile int* abort_flag, int* status, uint64_t limit_ns) {
   const int R = tab[CV_MAX_ROUNDS * CV_TAB];
   const int total = tab[R * CV_TAB + 4];
   int r = 0;  // round cursor (a warp's claims only increase)
@@ -941,7 +994,7 @@ __device__ __forceinline__ void cv_convert(const ConvParams& cv, const int* tab,
       issue(nxt, b ^ 1);
       inflight |= 1u << (b ^ 1);
     }
-    if (!mbar_wait_warp(&bar[b], (ph >> b) & 1u, abort_flag, status, ST_CONVERT)) break;
+    if (!mbar_wait_warp(&bar[b], (ph >> b) & 1u, abort_flag, status, ST_CONVERT, limit_ns)) break;
     inflight &= ~(1u << b);
     ph ^= 1u << b;
     // The stage holds element (row i, k) at k * 32 + i. Lane l converts K
@@ -1090,6 +1143,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   // CONVERT: two piece barriers per converter warp (in the barrier area),
   // their staging buffers and the chunk order's round table after it
   uint64_t* cvbar = reinterpret_cast<uint64_t*>(smem + S * C_::STAGE_BYTES + 256);
+  // the drain's barrier (a last MMA commit arrives on it) and the stages
+  // this CTA's producer issued, read by the leader of a pair when it drains
+  uint64_t* drainbar = reinterpret_cast<uint64_t*>(smem + S * C_::STAGE_BYTES + 288);
+  volatile int* issued_sh = reinterpret_cast<volatile int*>(smem + S * C_::STAGE_BYTES + 296);
+  static_assert(2 * C_::STAGES * 8 + 2 * C_::NBUF * 8 + 8 <= 256, "barriers before the converters' and the drain's");
+  const uint64_t limit_ns = wait_limit(p);
   uint8_t* cvbuf = smem + S * C_::STAGE_BYTES + 512;
   int* cvtab = reinterpret_cast<int*>(cvbuf + CV_WARPS * 2 * CV_PIECE_BYTES);
 
@@ -1196,6 +1255,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&tempty[b], PAIR ? 2 * EPI_WARPS : EPI_WARPS);  // PAIR: both CTAs' epilogues
     }
     *abort_flag = 0;
+    mbar_init(drainbar, 1);
+    *issued_sh = 0;
     if constexpr (CONVERT) {
       for (int b = 0; b < 2 * CV_WARPS; ++b) mbar_init(&cvbar[b], 1);
       // Round r of the grouped order runs tiles [r U, (r + 1) U) (U units).
@@ -1250,7 +1311,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = *tmem_slot;
   // bookkeeping for the drain after an abort
   int issued = 0;     // producer: slabs requested (ring position)
-  int committed = 0;  // MMA: slabs whose MMAs were committed (ring position)
 
   if (warp < EPI_WARP0) {
     // control warpgroup: its registers go to the epilogue warpgroups
@@ -1295,7 +1355,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int kb = TAIL ? v.kb0 : 0; kb < kb_hi; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1;
-          if (!mbar_wait<PAIR>(&empty[s], ph ^ 1, abort_flag, p.status, ST_PRODUCER, WAIT_LIMIT_NS, peer_abort)) {
+          if (!mbar_wait<PAIR>(&empty[s], ph ^ 1, abort_flag, p.status, ST_PRODUCER, limit_ns, peer_abort)) {
             go = false;
             break;
           }
@@ -1310,9 +1370,9 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
               const uint32_t bit = 1u << (kb & 3);
               if (((ready_a & bit) == 0 &&
-                   !flag_wait(flag_a + kb, abort_flag, p.status, ST_PRODUCER | ST_CONVERT, peer_abort)) ||
+                   !flag_wait(flag_a + kb, abort_flag, p.status, ST_PRODUCER | ST_CONVERT, peer_abort, limit_ns)) ||
                   ((ready_b & bit) == 0 &&
-                   !flag_wait(flag_b + kb, abort_flag, p.status, ST_PRODUCER | ST_CONVERT, peer_abort))) {
+                   !flag_wait(flag_b + kb, abort_flag, p.status, ST_PRODUCER | ST_CONVERT, peer_abort, limit_ns))) {
                 go = false;
                 break;
               }
@@ -1349,6 +1409,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in->tm[i])) : "memory");
         }
       }
+      *issued_sh = issued;  // for the drain (read by the pair's leader)
     } else if (warp == 1 && lane == 0 && leader) {
       // ---- MMA issuer: per K chunk, a fresh accumulation in tensor-memory
       // buffer (chunk parity); three (or one) products per K step
@@ -1366,7 +1427,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int c = 0; go && c < num_chunks; ++c, ++g) {
           const int buf = g % NBUF;
           const uint32_t use = (uint32_t)(g / NBUF);
-          if (!mbar_wait<PAIR>(&tempty[buf], (use & 1) ^ 1, abort_flag, p.status, ST_MMA, WAIT_LIMIT_NS,
+          if (!mbar_wait<PAIR>(&tempty[buf], (use & 1) ^ 1, abort_flag, p.status, ST_MMA, limit_ns,
                                peer_abort)) {
             go = false;
             break;
@@ -1378,7 +1439,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int kb = kb_first; kb < kb_end; ++kb, ++it) {
             const int s = it % S;
             const uint32_t ph = (it / S) & 1;
-            if (!mbar_wait<PAIR>(&full[s], ph, abort_flag, p.status, ST_MMA, WAIT_LIMIT_NS, peer_abort)) {
+            if (!mbar_wait<PAIR>(&full[s], ph, abort_flag, p.status, ST_MMA, limit_ns, peer_abort)) {
               go = false;
               break;
             }
@@ -1412,7 +1473,6 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
             }
             umma_commit<CG>(&empty[s]);  // frees the slab (in both CTAs) once read
-            committed = it + 1;
           }
           if (!go) break;
           umma_commit<CG>(&tfull[buf]);  // chunk complete in buffer buf (both CTAs)
@@ -1424,20 +1484,39 @@ __global__ void __launch_bounds__(THREADS, 1)
       // is converted); lane l converts row l of a piece
       const int w = warp - 2;
       if constexpr (CONVERT)
-        cv_convert(cv, cvtab, cvbar + 2 * w, cvbuf + w * 2 * CV_PIECE_BYTES, lane, abort_flag, p.status);
+        cv_convert(cv, cvtab, cvbar + 2 * w, cvbuf + w * 2 * CV_PIECE_BYTES, lane, abort_flag, p.status, limit_ns);
     }
     __syncwarp();
     tc_fence_before();
     cta_barrier_all();  // every role of this CTA is done
     tc_fence_after();
-    if (*abort_flag) {
-      // Drain what this CTA started before returning (bounded waits): TMA
-      // loads not yet consumed and the MMAs of the last commit. PAIR: the
-      // loads of both CTAs complete on the leader's barriers, so the leader
-      // drains them; the cluster barrier below keeps the peer until then.
+    // Both CTAs of a pair are past their roles before either decides whether
+    // to drain: an abort either of them raised (its own flag, or the copy it
+    // stored in the peer's) is then seen by both.
+    if constexpr (PAIR) cluster_sync_all();
+    bool aborted = *abort_flag != 0;
+    if constexpr (PAIR) aborted = aborted || ld_cluster_u32(peer_abort) != 0;
+    if (aborted) {
+      // Drain what was started before returning (bounded waits).
+      // Loads: the last S stages either CTA issued (an earlier stage's slot
+      // was refilled, so its loads had landed). Both CTAs' loads complete on
+      // the leader's barrier, which at issue expects the pair's bytes; the
+      // leader squares that with what was issued: a stage only the leader
+      // issued counts the peer's bytes as arrived, a stage only the peer
+      // issued gets the leader's arrival and expects the peer's bytes. Each
+      // such stage then completes once its loads have landed.
       if (warp == 0 && lane == 0 && leader) {
-        for (int it = (issued > S ? issued - S : 0); it < issued; ++it) {
+        constexpr uint32_t CTA_BYTES = C_::PLANES * (C_::A_SLAB + C_::B_SLAB);
+        const int mine = issued;
+        int theirs = mine;
+        if constexpr (PAIR) theirs = (int)ld_cluster_u32(mapa_rank(smem_u32((const void*)issued_sh), 1));
+        const int hi = max(mine, theirs);
+        for (int it = max(0, hi - S); it < hi; ++it) {
           const int s = it % S;
+          if constexpr (PAIR) {
+            if (it < mine && it >= theirs) mbar_complete_tx(&full[s], CTA_BYTES);
+            else if (it >= mine && it < theirs) mbar_expect_tx(&full[s], CTA_BYTES);
+          }
           const uint64_t t0 = globaltimer();
           while (!mbar_try_wait<PAIR>(&full[s], (it / S) & 1)) {
             if (globaltimer() - t0 > WAIT_LIMIT_NS) {
@@ -1447,11 +1526,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
-      if (warp == 1 && lane == 0 && committed > 0) {
-        const int it = committed - 1;
-        const int s = it % S;
+      // MMAs: a last commit by the issuer, after every MMA it issued, arrives
+      // on the drain barrier of each CTA (both of a pair) once they are done
+      if (warp == 1 && lane == 0) {
+        if (leader) umma_commit<CG>(drainbar);
         const uint64_t t0 = globaltimer();
-        while (!mbar_try_wait<PAIR>(&empty[s], (it / S) & 1)) {
+        while (!mbar_try_wait<PAIR>(drainbar, 0)) {
           if (globaltimer() - t0 > WAIT_LIMIT_NS) {
             if (p.status) atomicOr_system(p.status, ST_DRAIN);
             break;
@@ -1524,9 +1604,18 @@ __global__ void __launch_bounds__(THREADS, 1)
           sb0 = sb1;
           if (live && c + 2 < num_chunks) sa1 = __ldg(sa + c + 2), sb1 = __ldg(sb + c + 2);
         }
-        if (!mbar_wait<PAIR>(&tfull[buf], use & 1, abort_flag, p.status, ST_EPILOGUE, WAIT_LIMIT_NS, peer_abort)) {
+        // Lane 0 alone waits (bounded) and the warp takes its outcome, so no
+        // warp splits between a lane that saw the chunk and one that saw the
+        // abort flag; after a success the other lanes observe the completed
+        // phase, which their first poll returns.
+        int seen = 0;
+        if (lane == 0)
+          seen = mbar_wait<PAIR>(&tfull[buf], use & 1, abort_flag, p.status, ST_EPILOGUE, wait_limit(p), peer_abort);
+        if (!__shfl_sync(0xffffffffu, seen, 0)) {
           go = false;
           break;
+        }
+        for (int n = 0; n < (1 << 20) && !mbar_try_wait<PAIR>(&tfull[buf], use & 1); ++n) {
         }
         tc_fence_after();
         __syncwarp();
@@ -1736,7 +1825,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     tc_fence_before();
     cta_barrier_all();
-    if constexpr (PAIR) cluster_sync_all();
+    if constexpr (PAIR) {  // the control warpgroup's two cluster barriers (before and after its drain)
+      cluster_sync_all();
+      cluster_sync_all();
+    }
   }
 }
 
@@ -2268,6 +2360,7 @@ cudaError_t run_tc(const SgemmDesc& d, void* ws, size_t ws_bytes, const DeviceSt
     if (MODE == 3 && F.lo != align256((size_t)M * prm.row_kp * 2)) return cudaErrorInvalidValue;
   }
   prm.planes_only = (epi.planes_only && !C_::FP8 && (epi.fwd || epi.rows)) ? 1 : 0;
+  prm.wait_limit_us = st.wait_limit_us;
   if (epi.fwd && !C_::FP8) {
     // the planes of C as op(B) of a leaf with K = M: rows = N, row length M
     const OperandLayout F = operand_layout(N, M, MODE);
@@ -2331,6 +2424,7 @@ cudaError_t launch_batch_kernels(const TcBatch& b, const DeviceStatus& st, cudaS
   memset(unused, 0, sizeof unused);
   TcParams prm{};
   prm.status = st.dev;
+  prm.wait_limit_us = st.wait_limit_us;
   GroupParams gp{static_cast<const GroupInst*>(b.d_insts), static_cast<const GroupTile*>(b.d_tiles), b.num_tiles};
   hook_begin(hooks, s);
   sgemm_tc<MODE, 0, true, false>

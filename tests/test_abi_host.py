@@ -384,3 +384,17 @@ def test_plane_cache_on_a_host_only_context(ctx):
     assert len(set(flags)) == 6 and all(f & (H.HPVM_LAUNCH_NO_EVENT | H.HPVM_LAUNCH_NO_FUSION) == 0 for f in flags)
     with pytest.raises(H.HpvmError):
         H.hpvm_plane_cache_bytes(None)
+
+
+def test_wait_limit_bounds():
+    # 0 (the default) .. 10^7 microseconds; a host-only context keeps it too
+    ctx = H.hpvm_init(-1)
+    try:
+        for bad in (-1, 10 ** 7 + 1):
+            with pytest.raises(H.HpvmError) as e:
+                H.hpvm_set_wait_limit(ctx, bad)
+            assert e.value.code == H.HPVM_ERR_INVALID_ARG
+        H.hpvm_set_wait_limit(ctx, 5)
+        H.hpvm_set_wait_limit(ctx, 0)
+    finally:
+        H.hpvm_cleanup(ctx)

@@ -79,6 +79,9 @@ def test_tail_split_matches_oracle_and_repeats(dfg, tier, transA, transB):
     a = dfg.args_for(M, N, K, A, p.lda, B, p.ldb, C, p.ldc, tier=tier, transA=transA, transB=transB)
     planes = (2 if tier == H.HPVM_TIER_BF16X3 else 1) * (_al(M * 520 * 2) + _al(N * 520 * 2))
     region = _al(n * 2 * 2 * EPI_WARPS * ACC * 32 * 4) + _al(n * 2 * EPI_WARPS * 4)
+    if tier == H.HPVM_TIER_BF16X3:  # the in-leaf conversion's flags, counts and counter (last)
+        blocks = -(-M // 128) + -(-N // 128)
+        region += _al(4 * (blocks * ((-(-K // 64) + 3) // 4 * 4) + blocks + 1))
     assert H.hpvm_workspace_size(dfg.ctx, dfg.nodes["root"], a) == planes + region
 
 
