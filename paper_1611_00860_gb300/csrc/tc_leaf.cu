@@ -443,6 +443,14 @@ __device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr) {
   d |= static_cast<uint64_t>(ROW_BYTES == 128 ? 2 : 4) << 61;  // 128B / 64B swizzle
   return d;
 }
+// The same descriptor in two halves: the low word (address >> 4 in bits
+// 0-13, shared-memory addresses below 256 KB, and the leading offset) varies
+// with the address; the high word is a constant of the swizzle.
+__device__ __forceinline__ uint32_t sdesc_lo(uint32_t saddr) { return ((saddr & 0x3FFFFu) >> 4) | (1u << 16); }
+template <int ROW_BYTES>
+__device__ __forceinline__ uint64_t sdesc_of(uint32_t lo) {
+  return static_cast<uint64_t>(lo) | (sdesc_k<ROW_BYTES>(0) & 0xFFFFFFFF00000000ull);
+}
 // Instruction descriptor of tcgen05.mma kind::f16: D format F32 (bits 4-5 =
 // 1), A and B BF16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
@@ -1444,32 +1452,34 @@ __global__ void __launch_bounds__(THREADS, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t ah = smem_u32(a_hi(s)), al = smem_u32(a_pl(s, 1));
-            const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_pl(s, 1));
+            // The slab's descriptors (their low words), built once: the K
+            // step's are the slab's plus off, the step's bytes >> 4.
+            constexpr int RB = C_::ROW_BYTES;
+            const uint32_t ah = sdesc_lo(smem_u32(a_hi(s))), al = sdesc_lo(smem_u32(a_pl(s, 1)));
+            const uint32_t bh = sdesc_lo(smem_u32(b_hi(s))), bl = sdesc_lo(smem_u32(b_pl(s, 1)));
 #pragma unroll
             for (int kk = 0; kk < BK / MMA_K; ++kk) {
-              const uint32_t off = kk * MMA_K * C_::ELEM_BYTES;  // bytes along the slab row
+              const uint32_t off = (kk * MMA_K * C_::ELEM_BYTES) >> 4;  // 16-byte units along the slab row
               const uint32_t acc = (kb == kb_first && kk == 0) ? 0u : 1u;
-              constexpr int RB = C_::ROW_BYTES;
               if (C_::FP8) {
-                umma_e4m3<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, acc);
+                umma_e4m3<CG>(dst, sdesc_of<RB>(ah + off), sdesc_of<RB>(bh + off), idesc, acc);
               } else if (NPROD == 3) {
-                umma_bf16<CG>(dst, sdesc_k<RB>(al + off), sdesc_k<RB>(bh + off), idesc, acc);
-                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bl + off), idesc, 1u);
-                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_of<RB>(al + off), sdesc_of<RB>(bh + off), idesc, acc);
+                umma_bf16<CG>(dst, sdesc_of<RB>(ah + off), sdesc_of<RB>(bl + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_of<RB>(ah + off), sdesc_of<RB>(bh + off), idesc, 1u);
               } else if constexpr (NPROD == 6) {
-                const uint32_t al2 = smem_u32(a_pl(s, 2)), bl2 = smem_u32(b_pl(s, 2));
+                const uint32_t al2 = sdesc_lo(smem_u32(a_pl(s, 2))), bl2 = sdesc_lo(smem_u32(b_pl(s, 2)));
                 // smallest first: lo*hi, hi*lo, mid*mid (2^-17 of hi*hi),
                 // mid*hi, hi*mid (2^-9), hi*hi (the lo planes hold mid, the
                 // lo2 planes lo)
-                umma_bf16<CG>(dst, sdesc_k<RB>(al2 + off), sdesc_k<RB>(bh + off), idesc, acc);
-                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bl2 + off), idesc, 1u);
-                umma_bf16<CG>(dst, sdesc_k<RB>(al + off), sdesc_k<RB>(bl + off), idesc, 1u);
-                umma_bf16<CG>(dst, sdesc_k<RB>(al + off), sdesc_k<RB>(bh + off), idesc, 1u);
-                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bl + off), idesc, 1u);
-                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_of<RB>(al2 + off), sdesc_of<RB>(bh + off), idesc, acc);
+                umma_bf16<CG>(dst, sdesc_of<RB>(ah + off), sdesc_of<RB>(bl2 + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_of<RB>(al + off), sdesc_of<RB>(bl + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_of<RB>(al + off), sdesc_of<RB>(bh + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_of<RB>(ah + off), sdesc_of<RB>(bl + off), idesc, 1u);
+                umma_bf16<CG>(dst, sdesc_of<RB>(ah + off), sdesc_of<RB>(bh + off), idesc, 1u);
               } else {
-                umma_bf16<CG>(dst, sdesc_k<RB>(ah + off), sdesc_k<RB>(bh + off), idesc, acc);
+                umma_bf16<CG>(dst, sdesc_of<RB>(ah + off), sdesc_of<RB>(bh + off), idesc, acc);
               }
             }
             umma_commit<CG>(&empty[s]);  // frees the slab (in both CTAs) once read
@@ -1587,22 +1597,25 @@ __global__ void __launch_bounds__(THREADS, 1)
         sa = p.scaleA + (int64_t)(m_cta / FP8_BLOCK) * p.nkb + (TAIL ? v.kb0 / KC_SLABS : 0);
         sb = p.scaleB + (int64_t)((v.n0 + coff) / FP8_BLOCK) * p.nkb + (TAIL ? v.kb0 / KC_SLABS : 0);
       }
-      // FP8: the block scales of chunks c and c + 1, loaded two chunks ahead
-      // so their L2 round trips stay off the chunk-to-chunk critical path
+      // FP8: the block scales 32 chunks at a time, lane l holding chunk
+      // 32 j + l's (one coalesced load per batch, read by shuffle), the next
+      // batch loaded a whole batch ahead
       float sa0 = 0.f, sb0 = 0.f, sa1 = 0.f, sb1 = 0.f;
       if (C_::FP8 && live) {
-        if (num_chunks > 0) sa0 = __ldg(sa), sb0 = __ldg(sb);
-        if (num_chunks > 1) sa1 = __ldg(sa + 1), sb1 = __ldg(sb + 1);
+        if (lane < num_chunks) sa0 = __ldg(sa + lane), sb0 = __ldg(sb + lane);
+        if (32 + lane < num_chunks) sa1 = __ldg(sa + 32 + lane), sb1 = __ldg(sb + 32 + lane);
       }
       for (int c = 0; c < num_chunks; ++c, ++g) {
         const int buf = g % NBUF;
         const uint32_t use = (uint32_t)(g / NBUF);
         float scale = 1.f;  // FP8: the chunk's sA * sB
         if (C_::FP8) {
-          scale = sa0 * sb0;
-          sa0 = sa1;
-          sb0 = sb1;
-          if (live && c + 2 < num_chunks) sa1 = __ldg(sa + c + 2), sb1 = __ldg(sb + c + 2);
+          scale = __shfl_sync(0xffffffffu, sa0, c & 31) * __shfl_sync(0xffffffffu, sb0, c & 31);
+          if ((c & 31) == 31) {
+            sa0 = sa1;
+            sb0 = sb1;
+            if (live && c + 33 + lane < num_chunks) sa1 = __ldg(sa + c + 33 + lane), sb1 = __ldg(sb + c + 33 + lane);
+          }
         }
         // Lane 0 alone waits (bounded) and the warp takes its outcome, so no
         // warp splits between a lane that saw the chunk and one that saw the
