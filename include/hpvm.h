@@ -486,11 +486,14 @@ HPVM_API int hpvm_sgemm_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, float al
  * one split pre-pass launch and one persistent launch of the grouped leaf
  * over every output tile of every instance, longest tiles first.
  * Instances take the BF16X3 or BF16 tier (the same for all) and device
- * pointers. Each instance's tile width (its leaf grid, block_y = 64, 128 or
- * 256 columns per internal instance) comes from a policy:
+ * pointers. The hierarchy of every instance (Section 3.4 leaves tile sizes
+ * to an autotuner) comes from a policy: its tile height, 128 rows on one
+ * persistent CTA (policies 0-3) or 256 rows on a persistent CTA pair of a
+ * cluster (4-7), and each instance's tile width (its leaf grid, block_y =
+ * 64, 128 or 256 columns per internal instance) by the rule policy & 3:
  *   0: 256 for all; 1: 128 for all; 2, 3: per instance, the width that
  *   minimises tiles x (width x padded K + overhead), overhead light (2) or
- *   heavy (3); -1: the policy hpvm_batch_autotune found for a batch of the
+ *   heavy (3). -1: the policy hpvm_batch_autotune found for a batch of the
  *   same shapes in this context, else 2.
  * prepare allocates the batch's operand planes and tables on the device
  * (runtime-owned, freed by hpvm_batch_free or hpvm_cleanup) and sets kernel
@@ -503,26 +506,27 @@ typedef struct hpvm_batch_stats {
   int32_t split_tiles;  /* 64 x 64 tiles of the pre-pass launch */
   int32_t grid;         /* persistent CTAs */
   int32_t tile_width_count[3]; /* instances with 64, 128, 256 columns */
-  int32_t reserved;
+  int32_t tile_m;       /* rows of an output tile: 128 or 256 (CTA pairs) */
   int64_t workspace_bytes;
 } hpvm_batch_stats;
 HPVM_API int hpvm_batch_prepare(hpvm_ctx* ctx, hpvm_node* root, const void* records, size_t record_bytes,
                                 int count, int policy, hpvm_batch** out);
 HPVM_API int hpvm_batch_run(hpvm_batch* batch, void* cuda_stream);
-/* Time each policy (reps runs after one warm-up, CUDA events on
+/* Time each policy, 0..7 (reps runs after one warm-up, CUDA events on
  * cuda_stream), keep the fastest for this batch and for later batches of
  * the same shapes in the context. Results of the timed runs are valid. */
 HPVM_API int hpvm_batch_autotune(hpvm_batch* batch, void* cuda_stream, int reps, int* best_policy,
                                  double* best_ms);
 HPVM_API int hpvm_batch_info(hpvm_batch* batch, hpvm_batch_stats* out);
 HPVM_API int hpvm_batch_free(hpvm_batch* batch);
-/* Host-only: the tile widths a policy (0..3) picks for instances of the
+/* Host-only: the tile widths a policy (0..7) picks for instances of the
  * given shapes, and the leaf's schedule in launch order, 4 ints per slot
- * (instance, m0, n0, cta): tiles go longest first to the persistent CTA
- * with the least work so far, CTA u runs slots u, u + G, u + 2G, ... (G =
- * the CTAs, at most the current device's SMs), and a CTA with fewer tiles
- * than the busiest has empty slots (instance -1). tiles may be NULL to
- * query num_tiles (the slot count). */
+ * (instance, m0, n0, unit): tiles (128 rows, or 256 for policies 4-7) go
+ * longest first to the persistent unit (a CTA, or a CTA pair) with the
+ * least work so far, unit u runs slots u, u + G, u + 2G, ... (G = the
+ * units, at most the current device's SMs, or half of them for pairs), and
+ * a unit with fewer tiles than the busiest has empty slots (instance -1).
+ * tiles may be NULL to query num_tiles (the slot count). */
 HPVM_API int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, const int64_t* K, int policy,
                              int32_t* bn, int32_t* tiles, int64_t tile_cap, int64_t* num_tiles);
 

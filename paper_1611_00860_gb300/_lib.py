@@ -108,12 +108,12 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [
         ("count", ctypes.c_int32), ("tier", ctypes.c_int32), ("policy", ctypes.c_int32),
         ("tiles", ctypes.c_int32), ("split_tiles", ctypes.c_int32), ("grid", ctypes.c_int32),
-        ("tile_width_count", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32),
+        ("tile_width_count", ctypes.c_int32 * 3), ("tile_m", ctypes.c_int32),
         ("workspace_bytes", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
         d["tile_width_count"] = list(self.tile_width_count)
         return d
 
@@ -393,8 +393,9 @@ def hpvm_batch_free(batch: int) -> None:
 
 
 def hpvm_batch_plan(M, N, K, policy: int):
-    """Tile widths and the schedule: one (instance, m0, n0, cta) per slot in
-    launch order, instance -1 for an empty slot."""
+    """Tile widths and the schedule: one (instance, m0, n0, unit) per slot in
+    launch order, instance -1 for an empty slot (policies 4-7: 256-row tiles
+    on CTA pairs, the unit a pair)."""
     n = len(M)
     arr = lambda v: (ctypes.c_int64 * max(n, 1))(*[int(x) for x in v])
     Ma, Na, Ka = arr(M), arr(N), arr(K)

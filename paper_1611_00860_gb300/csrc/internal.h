@@ -133,7 +133,11 @@ struct TcBatch {
   int tier = 2;
   std::vector<SgemmDesc> d;
   std::vector<int> bn;  // tile width of each instance (the policy's choice)
-  int policy = 2;       // 0: 256, 1: 128, 2/3: cost model (light/heavy tile overhead)
+  // width rule (policy & 3): 0: 256, 1: 128, 2/3: cost model (light/heavy
+  // tile overhead); policy 0-3 on single CTAs (128-row tiles), 4-7 on CTA
+  // pairs (256-row tiles)
+  int policy = 2;
+  int tile_m = 128;     // rows of an output tile (the policy's height)
   void* ws = nullptr;
   size_t ws_bytes = 0;
   std::vector<size_t> plane_off;
@@ -147,8 +151,11 @@ struct TcBatch {
   int grid = 0;
 };
 std::vector<int> batch_choose_bn(const std::vector<SgemmDesc>& d, int policy);
-// tiles: 4 ints per tile (instance, m0, n0, 0) in schedule order
-int batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, int units, std::vector<int>* tiles);
+// rows of a batch tile under a policy: 128 (single CTAs) or 256 (CTA pairs)
+int batch_tile_m(int policy);
+// tiles: 4 ints per slot (instance, m0, n0, unit) in schedule order
+int batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, int units, std::vector<int>* tiles,
+                   int tile_m);
 // SMs of the current device (148 when none answers): the persistent CTAs a
 // batch's leaf launch uses.
 int tc_num_sms();

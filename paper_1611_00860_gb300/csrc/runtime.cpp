@@ -1920,7 +1920,7 @@ int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, const int64_t
                     int32_t* tiles, int64_t tile_cap, int64_t* num_tiles) {
   if (count < 0 || (count > 0 && (!M || !N || !K)) || !num_tiles)
     return fail(HPVM_ERR_INVALID_ARG, "bad arguments");
-  if (policy < 0 || policy > 3) return fail(HPVM_ERR_INVALID_ARG, "policy must be 0..3");
+  if (policy < 0 || policy > 7) return fail(HPVM_ERR_INVALID_ARG, "policy must be 0..7");
   std::vector<hpvm::SgemmDesc> d(count);
   for (int i = 0; i < count; ++i) {
     if (M[i] < 0 || N[i] < 0 || K[i] < 0) return fail(HPVM_ERR_SHAPE, "negative extent in instance %d", i);
@@ -1930,7 +1930,8 @@ int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, const int64_t
   }
   auto w = hpvm::batch_choose_bn(d, policy);
   std::vector<int> t;
-  hpvm::batch_schedule(d, w, hpvm::tc_num_sms(), &t);
+  const int tm = hpvm::batch_tile_m(policy);
+  hpvm::batch_schedule(d, w, tm > 128 ? std::max(1, hpvm::tc_num_sms() / 2) : hpvm::tc_num_sms(), &t, tm);
   if (bn)
     for (int i = 0; i < count; ++i) bn[i] = w[i];
   *num_tiles = (int64_t)(t.size() / 4);
@@ -1946,7 +1947,7 @@ int hpvm_batch_prepare(hpvm_ctx* ctx, hpvm_node* root, const void* records, size
                        int policy, hpvm_batch** out) {
   if (out) *out = nullptr;
   if (!ctx || !out || !records || count <= 0) return fail(HPVM_ERR_INVALID_ARG, "bad arguments");
-  if (policy < -1 || policy > 3) return fail(HPVM_ERR_INVALID_ARG, "policy must be -1 (tuned) or 0..3");
+  if (policy < -1 || policy > 7) return fail(HPVM_ERR_INVALID_ARG, "policy must be -1 (tuned) or 0..7");
   if (ctx->device < 0) return fail(HPVM_ERR_NO_DEVICE, "host-only context");
   cudaSetDevice(ctx->device);
   std::vector<hpvm::SgemmDesc> d(count);
@@ -2037,6 +2038,7 @@ int hpvm_batch_info(hpvm_batch* b, hpvm_batch_stats* out) {
   out->tiles = b->tb.real_tiles;
   out->split_tiles = b->tb.num_split_tiles;
   out->grid = b->tb.grid;
+  out->tile_m = b->tb.tile_m;
   out->workspace_bytes = (int64_t)b->tb.ws_bytes;
   for (int w : b->tb.bn) out->tile_width_count[w == 64 ? 0 : w == 128 ? 1 : 2]++;
   return ok();

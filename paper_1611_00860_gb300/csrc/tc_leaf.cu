@@ -1108,11 +1108,12 @@ struct TileView {
 
 // EPI: 0 none; 1 C = tanh(alpha*acc + beta*C); 2 C = (alpha*acc + beta*C)*(1 - H^2)
 // (the elementwise leaf merged into the sgemm leaf, MergeDependentNodes).
-// GROUPED: the persistent CTAs walk the tile list of a batch of instances
-// (gp) instead of the tiles of the one instance of the kernel parameters.
+// GROUPED: the persistent CTAs (or pairs) walk the tile list of a batch of
+// instances (gp) instead of the tiles of the one instance of the kernel
+// parameters; a tile is BM (PAIR: 2 BM) rows by its instance's width bn.
 // PAIR: launched in clusters of 2 CTAs; each cluster takes 256 x 256 tiles
-// (the internal node's instance maps to a CTA pair) and the leader CTA
-// (rank 0) issues the pair's MMAs. Roles per CTA:
+// (256 x bn when GROUPED; the internal node's instance maps to a CTA pair)
+// and the leader CTA (rank 0) issues the pair's MMAs. Roles per CTA:
 //   warp 0      TMA producer (both CTAs: each loads its own half)
 //   warp 1      tensor-memory allocation; MMA issuer (leader only)
 //   warps 2, 3  idle (they complete the control warpgroup)
@@ -1125,7 +1126,8 @@ __global__ void __launch_bounds__(THREADS, 1)
              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
              const __grid_constant__ CUtensorMap tmA_lo2, const __grid_constant__ CUtensorMap tmB_lo2,
              TcParams p, GroupParams gp, const __grid_constant__ ConvParams cv) {
-  static_assert(!(GROUPED && PAIR), "batches run on single CTAs");
+  static_assert(!(GROUPED && PAIR) || (EPI == 0 && !CONVERT && MODE != 8 && MODE != 6),
+                "batches on pairs: the BF16x3 and BF16 leaves, plain epilogue");
   static_assert(!CONVERT || (MODE == 3 && PAIR && !GROUPED && Cfg<MODE, PAIR>::BK == CV_BK),
                 "in-leaf conversion: the BF16x3 leaf on pairs, one chunk per slab");
   static_assert(MODE != 6 || (!GROUPED && EPI == 0), "BF16x6: single instances, plain epilogue");
@@ -1155,6 +1157,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   // this CTA's producer issued, read by the leader of a pair when it drains
   uint64_t* drainbar = reinterpret_cast<uint64_t*>(smem + S * C_::STAGE_BYTES + 288);
   volatile int* issued_sh = reinterpret_cast<volatile int*>(smem + S * C_::STAGE_BYTES + 296);
+  // GROUPED pairs: the bytes this CTA's producer loaded into each stage (a
+  // batch's tiles differ in width), for the drain's reconciliation
+  uint32_t* stage_bytes_sh = reinterpret_cast<uint32_t*>(smem + S * C_::STAGE_BYTES + 304);
+  static_assert(304 + 4 * C_::STAGES <= 512, "stage byte counts inside the barrier area");
   static_assert(2 * C_::STAGES * 8 + 2 * C_::NBUF * 8 + 8 <= 256, "barriers before the converters' and the drain's");
   const uint64_t limit_ns = wait_limit(p);
   uint8_t* cvbuf = smem + S * C_::STAGE_BYTES + 512;
@@ -1338,10 +1344,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         const GroupTile cur = nx;
         nx = fetch(t + num_units);
         const TileView v = view(t, cur);
-        const uint32_t b_rows = PAIR ? (uint32_t)C_::B_ROWS : (uint32_t)v.bn;
+        // this CTA's rows of B: PAIR, half of the tile's (B_ROWS, or bn / 2 of
+        // a batch's tile of width bn); single CTAs all bn
+        const int b_half = PAIR ? (GROUPED ? v.bn / 2 : C_::B_ROWS) : 0;
+        const uint32_t b_rows = PAIR ? (uint32_t)b_half : (uint32_t)v.bn;
         const uint32_t bytes = C_::PLANES * (C_::A_SLAB + b_rows * C_::ROW_BYTES);
         const int ma = v.m0 + (int)rank * BM;
-        const int nb = v.n0 + (int)rank * C_::B_ROWS;
+        const int nb = v.n0 + (int)rank * b_half;
         const int kb_hi = TAIL ? v.kb1 : (v.K + BK - 1) / BK;
         // CONVERT: whether every chunk of this CTA's A block, and of its B
         // block, is ready (split before the launch, or all converted): such
@@ -1390,6 +1399,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
           }
           if constexpr (PAIR) {
+            if constexpr (GROUPED) stage_bytes_sh[s] = bytes;
             if (leader) mbar_expect_tx(&full[s], 2 * bytes);
             const uint32_t bar = mapa_rank(smem_u32(&full[s]), 0);
             tma_load_2d_pair(v.tm[0], bar, a_hi(s), k, ma);
@@ -1524,8 +1534,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int it = max(0, hi - S); it < hi; ++it) {
           const int s = it % S;
           if constexpr (PAIR) {
-            if (it < mine && it >= theirs) mbar_complete_tx(&full[s], CTA_BYTES);
-            else if (it >= mine && it < theirs) mbar_expect_tx(&full[s], CTA_BYTES);
+            // the bytes of stage it's tile for one CTA: a constant, except
+            // in a batch (its issuer's record: ours, or the peer's)
+            uint32_t own = CTA_BYTES, peer = CTA_BYTES;
+            if constexpr (GROUPED) {
+              own = stage_bytes_sh[s];
+              peer = ld_cluster_u32(mapa_rank(smem_u32(&stage_bytes_sh[s]), 1));
+            }
+            if (it < mine && it >= theirs) mbar_complete_tx(&full[s], own);
+            else if (it >= mine && it < theirs) mbar_expect_tx(&full[s], peer);
           }
           const uint64_t t0 = globaltimer();
           while (!mbar_try_wait<PAIR>(&full[s], (it / S) & 1)) {
@@ -2439,6 +2456,26 @@ cudaError_t launch_batch_kernels(const TcBatch& b, const DeviceStatus& st, cudaS
   prm.status = st.dev;
   prm.wait_limit_us = st.wait_limit_us;
   GroupParams gp{static_cast<const GroupInst*>(b.d_insts), static_cast<const GroupTile*>(b.d_tiles), b.num_tiles};
+  if (b.tile_m > BM) {
+    // 256-row tiles on CTA pairs: clusters of two
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.grid);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = Cfg<MODE, true>::SMEM_BYTES;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    hook_begin(hooks, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, sgemm_tc<MODE, 0, true, true, false>, unused[0], unused[1], unused[2],
+                                       unused[3], unused[4], unused[5], prm, gp, ConvParams{});
+    hook_end(hooks, s);
+    return e;
+  }
   hook_begin(hooks, s);
   sgemm_tc<MODE, 0, true, false>
       <<<b.grid, THREADS, C_::SMEM_BYTES, s>>>(unused[0], unused[1], unused[2], unused[3], unused[4], unused[5], prm,
@@ -2467,22 +2504,25 @@ int upload(void** dst, const std::vector<T>& v, std::string* err) {
 
 }  // namespace
 
+int batch_tile_m(int policy) { return policy >= 4 ? 2 * BM : BM; }
+
 std::vector<int> batch_choose_bn(const std::vector<SgemmDesc>& d, int policy) {
   std::vector<int> bn(d.size(), BN);
-  if (policy == 0) return bn;
-  if (policy == 1) {
+  const int rule = policy & 3, tm = batch_tile_m(policy);
+  if (rule == 0) return bn;
+  if (rule == 1) {
     std::fill(bn.begin(), bn.end(), 128);
     return bn;
   }
-  // Model policies: for each instance pick the tile width that minimises
+  // Model rules: for each instance pick the tile width that minimises
   // tiles x (columns x padded K + per-tile overhead), the overhead counted
-  // in the same column-K units (policy 2: light, 3: heavy).
-  const double overhead = policy == 2 ? 8192.0 : 65536.0;
+  // in the same column-K units (rule 2: light, 3: heavy).
+  const double overhead = rule == 2 ? 8192.0 : 65536.0;
   for (size_t i = 0; i < d.size(); ++i) {
     const double kp = (double)((d[i].K + 127) / 128 * 128);
     double best = -1;
     for (int w : {64, 128, 256}) {
-      const double tiles = (double)((d[i].M + BM - 1) / BM) * (double)((d[i].N + w - 1) / w);
+      const double tiles = (double)((d[i].M + tm - 1) / tm) * (double)((d[i].N + w - 1) / w);
       const double cost = tiles * (w * kp + overhead);
       if (best < 0 || cost < best - 1e-9) {
         best = cost;
@@ -2493,13 +2533,15 @@ std::vector<int> batch_choose_bn(const std::vector<SgemmDesc>& d, int policy) {
   return bn;
 }
 
-int batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, int units, std::vector<int>* tiles) {
-  // Every output tile of every instance, longest first (cost: padded K x
-  // width plus a per-tile overhead), each given to the persistent CTA with
-  // the least work so far (LPT). CTA u runs slots u, u + G, u + 2G, ...:
-  // slot r * G + u holds its r-th tile, or an empty record (instance -1)
-  // when it has fewer tiles than the busiest CTA. 4 ints per slot:
-  // (instance, m0, n0, CTA). Returns G, the CTAs the launch needs.
+int batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, int units, std::vector<int>* tiles,
+                   int tile_m) {
+  // Every output tile (tile_m rows by its instance's width) of every
+  // instance, longest first (cost: padded K x width x tile_m / 128 plus a
+  // per-tile overhead), each given to the persistent unit (CTA, or CTA pair)
+  // with the least work so far (LPT). Unit u runs slots u, u + G, u + 2G,
+  // ...: slot r * G + u holds its r-th tile, or an empty record (instance
+  // -1) when it has fewer tiles than the busiest unit. 4 ints per slot:
+  // (instance, m0, n0, unit). Returns G, the units the launch needs.
   struct T {
     int64_t cost;
     int inst, m0, n0;
@@ -2509,7 +2551,8 @@ int batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, 
     if (d[i].M <= 0 || d[i].N <= 0) continue;
     const int64_t kp = (d[i].K + 127) / 128 * 128;
     for (int64_t n0 = 0; n0 < d[i].N; n0 += bn[i])
-      for (int64_t m0 = 0; m0 < d[i].M; m0 += BM) v.push_back({kp * bn[i] + 4096, (int)i, (int)m0, (int)n0});
+      for (int64_t m0 = 0; m0 < d[i].M; m0 += tile_m)
+        v.push_back({kp * bn[i] * (tile_m / BM) + 4096, (int)i, (int)m0, (int)n0});
   }
   std::stable_sort(v.begin(), v.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
   tiles->clear();
@@ -2537,6 +2580,38 @@ int batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, 
       tiles->push_back(u);
     }
   return G;
+}
+
+// The grouped leaf's kernel attributes (dynamic shared memory, register
+// split check) and how many persistent units it runs at once: one CTA per
+// SM, or (PAIR) the clusters of two that fit, at most half the SMs.
+template <int MODE, bool PAIR>
+cudaError_t batch_kernel_setup(int* units) {
+  using C_ = Cfg<MODE, PAIR>;
+  auto kernel = sgemm_tc<MODE, 0, true, PAIR, false>;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
+  if (e == cudaSuccess) e = check_register_split(kernel);
+  if (e != cudaSuccess) return e;
+  if constexpr (!PAIR) {
+    *units = num_sms();
+  } else {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = C_::SMEM_BYTES;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * (num_sms() / 2));
+    int n = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(&n, kernel, &cfg)) != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    *units = std::min(n, num_sms() / 2);
+  }
+  return cudaSuccess;
 }
 
 int tc_batch_build(TcBatch* b, std::string* err) {
@@ -2583,8 +2658,23 @@ int tc_batch_build(TcBatch* b, std::string* err) {
     if (upload(&b->d_ops, ops, err) || upload(&b->d_split_tiles, st, err)) return -1;
     b->num_split_tiles = (int)st.size();
   }
-  // tile widths, tensor maps and the tile schedule of the current policy
+  // kernel attributes first (so a run can be captured into a CUDA graph),
+  // and the persistent units the leaf can run at once: CTAs, or CTA pairs
+  const bool pair = b->policy >= 4;
+  int units = 0;
+  cudaError_t e = mode == 3 ? (pair ? batch_kernel_setup<3, true>(&units) : batch_kernel_setup<3, false>(&units))
+                            : (pair ? batch_kernel_setup<1, true>(&units) : batch_kernel_setup<1, false>(&units));
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return -1;
+  }
+  // tile widths, tensor maps and the tile schedule of the current policy:
+  // a CTA loads 128 rows of A and all bn rows of B of its tile; a pair's
+  // CTAs 128 rows of A each and bn / 2 rows of B each
   b->bn = batch_choose_bn(b->d, b->policy);
+  b->tile_m = batch_tile_m(b->policy);
+  const int rb = pair ? (mode == 3 ? Cfg<3, true>::ROW_BYTES : Cfg<1, true>::ROW_BYTES)
+                      : (mode == 3 ? Cfg<3>::ROW_BYTES : Cfg<1>::ROW_BYTES);
   std::vector<GroupInst> insts(count);
   for (int i = 0; i < count; ++i) {
     const SgemmDesc& d = b->d[i];
@@ -2601,13 +2691,13 @@ int tc_batch_build(TcBatch* b, std::string* err) {
     if (d.M <= 0 || d.N <= 0 || d.K <= 0) continue;
     const WsLayout L = ws_layout(d, mode);
     uint8_t* w = static_cast<uint8_t*>(b->ws) + b->plane_off[i];
-    const int rb = mode == 3 ? Cfg<3>::ROW_BYTES : Cfg<1>::ROW_BYTES;
+    const int brows = pair ? g.bn / 2 : g.bn;
     if (!encode_plane(&g.tm[0], w + L.a_hi, (int)d.M, (int)d.K, (int)L.Kp, BM, 2, rb, err) ||
-        !encode_plane(&g.tm[2], w + L.b_hi, (int)d.N, (int)d.K, (int)L.Kp, g.bn, 2, rb, err))
+        !encode_plane(&g.tm[2], w + L.b_hi, (int)d.N, (int)d.K, (int)L.Kp, brows, 2, rb, err))
       return -1;
     if (mode == 3) {
       if (!encode_plane(&g.tm[1], w + L.a_lo, (int)d.M, (int)d.K, (int)L.Kp, BM, 2, rb, err) ||
-          !encode_plane(&g.tm[3], w + L.b_lo, (int)d.N, (int)d.K, (int)L.Kp, g.bn, 2, rb, err))
+          !encode_plane(&g.tm[3], w + L.b_lo, (int)d.N, (int)d.K, (int)L.Kp, brows, 2, rb, err))
         return -1;
     } else {
       g.tm[1] = g.tm[0];
@@ -2615,7 +2705,7 @@ int tc_batch_build(TcBatch* b, std::string* err) {
     }
   }
   std::vector<int> tiles;
-  const int G = batch_schedule(b->d, b->bn, num_sms(), &tiles);
+  const int G = batch_schedule(b->d, b->bn, units, &tiles, b->tile_m);
   std::vector<GroupTile> gt(tiles.size() / 4);
   b->real_tiles = 0;
   for (size_t t = 0; t < gt.size(); ++t) {
@@ -2638,22 +2728,7 @@ int tc_batch_build(TcBatch* b, std::string* err) {
   }
   if (upload(&b->d_insts, insts, err) || upload(&b->d_tiles, gt, err)) return -1;
   b->num_tiles = (int)gt.size();
-  b->grid = G;
-  // kernel attributes now, so a run can be captured into a CUDA graph
-  cudaError_t e;
-  if (mode == 3) {
-    e = cudaFuncSetAttribute(sgemm_tc<3, 0, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cfg<3>::SMEM_BYTES);
-    if (e == cudaSuccess) e = check_register_split(sgemm_tc<3, 0, true, false>);
-  } else {
-    e = cudaFuncSetAttribute(sgemm_tc<1, 0, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cfg<1>::SMEM_BYTES);
-    if (e == cudaSuccess) e = check_register_split(sgemm_tc<1, 0, true, false>);
-  }
-  if (e != cudaSuccess) {
-    *err = cudaGetErrorString(e);
-    return -1;
-  }
+  b->grid = pair ? 2 * G : G;
   return 0;
 }
 
@@ -2669,7 +2744,7 @@ int tc_batch_autotune(TcBatch* b, const DeviceStatus& st, cudaStream_t s, int re
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int pol = 0; pol < 4; ++pol) {
+  for (int pol = 0; pol < 8; ++pol) {  // four width rules x single CTAs, CTA pairs
     b->policy = pol;
     if (tc_batch_build(b, err)) break;
     if (tc_batch_run(*b, st, s, nullptr) != cudaSuccess) break;  // warm-up

@@ -5,26 +5,28 @@ import workloads as W
 from paper_1611_00860_gb300 import _lib as H
 
 
-def _grid(M, N, bn):
-    return {(m0, n0) for m0 in range(0, M, 128) for n0 in range(0, N, bn)}
+def _grid(M, N, bn, tm=128):
+    return {(m0, n0) for m0 in range(0, M, tm) for n0 in range(0, N, bn)}
 
 
-@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+@pytest.mark.parametrize("policy", range(8))
 def test_schedule_covers_every_tile_once(policy):
+    # policies 4-7: 256-row tiles on CTA pairs, the units half as many
     shapes = W.batched_shapes(64, seed=5)
     M, N, K = zip(*shapes)
     bn, slots = H.hpvm_batch_plan(M, N, K, policy)
+    tm = 256 if policy >= 4 else 128
     tiles = [t for t in slots if t[0] >= 0]
     assert len(tiles) == len(set(tiles))
     for i, (m, n, _k) in enumerate(shapes):
         got = {(t[1], t[2]) for t in tiles if t[0] == i}
-        assert got == _grid(m, n, bn[i])
+        assert got == _grid(m, n, bn[i], tm)
     # CTA u runs slots u, u + G, ...; each CTA's tiles longest first, and
     # the CTAs' loads (longest-first to the least loaded) differ by at most
     # one tile's cost
     G = max(t[3] for t in slots) + 1
     assert len(slots) % G == 0 and all(t[3] == p % G for p, t in enumerate(slots))
-    cost = lambda t: ((K[t[0]] + 127) // 128 * 128) * bn[t[0]] + 4096
+    cost = lambda t: ((K[t[0]] + 127) // 128 * 128) * bn[t[0]] * (tm // 128) + 4096
     loads = []
     for u in range(G):
         c = [cost(t) for t in slots[u::G] if t[0] >= 0]
@@ -43,6 +45,20 @@ def test_policies():
     # a heavier per-tile overhead never asks for more tiles than a lighter one
     bn3 = H.hpvm_batch_plan(M, N, K, 3)[0]
     assert all(b3 >= b2 for b2, b3 in zip(bn2, bn3))
+    # the pair policies apply the same rules to 256-row tiles
+    assert H.hpvm_batch_plan(M, N, K, 4)[0] == [256, 256, 256]
+    assert H.hpvm_batch_plan(M, N, K, 5)[0] == [128, 128, 128]
+    assert H.hpvm_batch_plan(M, N, K, 6)[0][0] == 64
+
+
+def test_pair_policies_halve_the_units():
+    shapes = W.batched_shapes(64, seed=5)
+    M, N, K = zip(*shapes)
+    g1 = max(t[3] for t in H.hpvm_batch_plan(M, N, K, 2)[1]) + 1
+    g2 = max(t[3] for t in H.hpvm_batch_plan(M, N, K, 6)[1]) + 1
+    assert g2 <= max(1, g1 // 2)
+    # 256-row tiles: no tile starts at an odd multiple of 128 rows
+    assert all(t[1] % 256 == 0 for t in H.hpvm_batch_plan(M, N, K, 6)[1] if t[0] >= 0)
 
 
 def test_batched_workload_plan():
@@ -57,6 +73,6 @@ def test_batched_workload_plan():
 
 def test_bad_policy_and_shapes():
     with pytest.raises(H.HpvmError):
-        H.hpvm_batch_plan([1], [1], [1], 7)
+        H.hpvm_batch_plan([1], [1], [1], 8)
     with pytest.raises(H.HpvmError):
         H.hpvm_batch_plan([-1], [1], [1], 0)

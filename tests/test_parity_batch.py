@@ -1,8 +1,9 @@
 """Batches of independent sgemm DFG instances on the GPU (one batched split
 pre-pass launch and one persistent grouped leaf launch), through the C-ABI:
-every instance against the FP64 oracle for every tile-width policy, the
-batch against one launch per instance, a CUDA-graph replay against a direct
-run, and the autotuner."""
+every instance against the FP64 oracle for every policy (four tile-width
+rules, on single CTAs with 128-row tiles and on CTA pairs with 256-row
+tiles), the batch against one launch per instance (bit for bit, on either
+tile height), a CUDA-graph replay against a direct run, and the autotuner."""
 import math
 
 import numpy as np
@@ -46,7 +47,7 @@ def small_batch():
 
 
 @pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16X3, H.HPVM_TIER_BF16])
-@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+@pytest.mark.parametrize("policy", range(8))
 def test_every_instance_matches_oracle(cuda_device, small_batch, tier, policy):
     probs, refs = small_batch
     dev = _device(probs)
@@ -55,6 +56,7 @@ def test_every_instance_matches_oracle(cuda_device, small_batch, tier, policy):
         b.prepare(probs, dev, tier=tier, policy=policy)
         info = b.info()
         assert info["count"] == 40 and info["policy"] == policy and info["tiles"] > 0
+        assert info["tile_m"] == (256 if policy >= 4 else 128)
         b.run()
         torch.cuda.synchronize()
         for p, (_, _, C), ref in zip(probs, dev, refs):
@@ -65,14 +67,17 @@ def test_every_instance_matches_oracle(cuda_device, small_batch, tier, policy):
         b.close()
 
 
-def test_batch_equals_one_launch_per_instance(cuda_device, small_batch):
+@pytest.mark.parametrize("policy", [0, 4])
+def test_batch_equals_one_launch_per_instance(cuda_device, small_batch, policy):
     probs, _ = small_batch
     dev_b = _device(probs)
     dev_s = _device(probs)
     b = BatchDFG(0)
     s = SgemmDFG(0)
     try:
-        b.prepare(probs, dev_b, tier=H.HPVM_TIER_BF16X3, policy=0)  # 256-wide tiles, as the single leaf
+        # 256-wide tiles as the single leaf's, 128 rows a CTA (0) or 256 a
+        # CTA pair (4, as the single leaf)
+        b.prepare(probs, dev_b, tier=H.HPVM_TIER_BF16X3, policy=policy)
         b.run()
         for p, t in zip(probs, dev_s):
             s.run_problem(p, H.HPVM_TIER_BF16X3, t)
@@ -120,7 +125,7 @@ def test_autotune_picks_a_policy_and_keeps_results_right(cuda_device, small_batc
     try:
         b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=0)
         best, ms = b.autotune(reps=2)
-        assert best in (0, 1, 2, 3) and ms > 0
+        assert best in range(8) and ms > 0
         assert b.info()["policy"] == best
         # a new batch of the same shapes starts from the tuned policy
         b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=-1)
@@ -136,14 +141,15 @@ def test_autotune_picks_a_policy_and_keeps_results_right(cuda_device, small_batc
 
 
 @pytest.mark.slow
-def test_batched_workload_512_instances(cuda_device):
+@pytest.mark.parametrize("policy", [2, 6])
+def test_batched_workload_512_instances(cuda_device, policy):
     # the batched workload: 512 instances, M, N, K log-uniform in [32, 2048]
     shapes = W.batched_shapes()
     probs = [W.sgemm_problem(m, n, k, seed=20000 + i, alpha=1.0, beta=0.0) for i, (m, n, k) in enumerate(shapes)]
     dev = _device(probs)
     b = BatchDFG(0)
     try:
-        b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=2)
+        b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=policy)
         b.run()
         torch.cuda.synchronize()
         worst = 0.0
