@@ -398,3 +398,36 @@ def test_wait_limit_bounds():
         H.hpvm_set_wait_limit(ctx, 0)
     finally:
         H.hpvm_cleanup(ctx)
+
+
+def test_workspace_size_bf16x6_on_host(ctx):
+    # three planes (hi, mid, lo) of each operand; no in-leaf conversion region
+    nodes = build_sgemm_graph(ctx)
+    a = make_args(300, 200, 100, 0x1000, 4 * 300 * 100, 300, 0x2000, 4 * 200 * 100, 200,
+                  0x3000, 4 * 300 * 200, 300, 1.0, 0.0, False, True, H.HPVM_TIER_BF16X6)
+    def al(x):
+        return (x + 255) // 256 * 256
+    assert H.hpvm_workspace_size(ctx, nodes["root"], a) == 3 * (al(300 * 104 * 2) + al(200 * 104 * 2))
+
+
+def _code(fn, *args):
+    try:
+        fn(*args)
+    except H.HpvmError as e:
+        return e.code
+    return H.HPVM_OK
+
+
+def test_split3_argument_checks():
+    # checked before anything reaches the device
+    ok = 0x10000
+    assert _code(H.hpvm_split3_bf16, ok, 64, True, 0, 64, ok, ok, ok) == H.HPVM_OK  # nothing to do
+    assert _code(H.hpvm_split3_bf16, ok, 64, True, -1, 64, ok, ok, ok) == H.HPVM_ERR_SHAPE
+    assert _code(H.hpvm_split3_bf16, None, 64, True, 8, 64, ok, ok, ok) == H.HPVM_ERR_INVALID_ARG
+    assert _code(H.hpvm_split3_bf16, ok, 64, True, 8, 64, ok, None, ok) == H.HPVM_ERR_INVALID_ARG
+    assert _code(H.hpvm_split3_bf16, ok, 32, True, 8, 64, ok, ok, ok) == H.HPVM_ERR_SHAPE  # ld < K
+    assert _code(H.hpvm_split3_bf16, ok, 64, True, 8, 64, ok, ok + 8, ok) == H.HPVM_ERR_ALIGN
+
+
+def test_stream_coalesce_argument_checks():
+    assert _code(H.hpvm_stream_coalesce, None, 4) == H.HPVM_ERR_INVALID_ARG
