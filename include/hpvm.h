@@ -489,21 +489,26 @@ HPVM_API int hpvm_sgemm_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, float al
  * pointers. The hierarchy of every instance (Section 3.4 leaves tile sizes
  * to an autotuner) comes from a policy: its tile height, 128 rows on one
  * persistent CTA (policies 0-3) or 256 rows on a persistent CTA pair of a
- * cluster (4-7), and each instance's tile width (its leaf grid, block_y =
- * 64, 128 or 256 columns per internal instance) by the rule policy & 3:
+ * cluster (4-7; 8-11 the same, BF16X3 only, with the operand planes made
+ * inside the leaf: the pre-pass splits only what the leaf's first round of
+ * tiles reads, and idle warps of the leaf convert the rest, in the order
+ * the tiles first read it), and each instance's tile width (its leaf grid,
+ * block_y = 64, 128 or 256 columns per internal instance) by the rule
+ * policy & 3:
  *   0: 256 for all; 1: 128 for all; 2, 3: per instance, the width that
  *   minimises tiles x (width x padded K + overhead), overhead light (2) or
  *   heavy (3). -1: the policy hpvm_batch_autotune found for a batch of the
  *   same shapes in this context, else 2.
  * prepare allocates the batch's operand planes and tables on the device
  * (runtime-owned, freed by hpvm_batch_free or hpvm_cleanup) and sets kernel
- * attributes; run only enqueues the two kernels, so it can be captured in
+ * attributes; run only enqueues the two kernels (8-11: a reset of the
+ * conversion's flags too), so it can be captured in
  * a CUDA graph. A batch reads the pointers of its records at every run. */
 typedef struct hpvm_batch hpvm_batch;
 typedef struct hpvm_batch_stats {
   int32_t count, tier, policy;
   int32_t tiles;        /* output tiles of the leaf launch */
-  int32_t split_tiles;  /* 64 x 64 tiles of the pre-pass launch */
+  int32_t split_tiles;  /* 64 x 64 tiles of the pre-pass launch (8-11: the first round's) */
   int32_t grid;         /* persistent CTAs */
   int32_t tile_width_count[3]; /* instances with 64, 128, 256 columns */
   int32_t tile_m;       /* rows of an output tile: 128 or 256 (CTA pairs) */
@@ -512,16 +517,16 @@ typedef struct hpvm_batch_stats {
 HPVM_API int hpvm_batch_prepare(hpvm_ctx* ctx, hpvm_node* root, const void* records, size_t record_bytes,
                                 int count, int policy, hpvm_batch** out);
 HPVM_API int hpvm_batch_run(hpvm_batch* batch, void* cuda_stream);
-/* Time each policy, 0..7 (reps runs after one warm-up, CUDA events on
+/* Time each policy, 0..11 (0..7 for BF16) (reps runs after one warm-up, CUDA events on
  * cuda_stream), keep the fastest for this batch and for later batches of
  * the same shapes in the context. Results of the timed runs are valid. */
 HPVM_API int hpvm_batch_autotune(hpvm_batch* batch, void* cuda_stream, int reps, int* best_policy,
                                  double* best_ms);
 HPVM_API int hpvm_batch_info(hpvm_batch* batch, hpvm_batch_stats* out);
 HPVM_API int hpvm_batch_free(hpvm_batch* batch);
-/* Host-only: the tile widths a policy (0..7) picks for instances of the
+/* Host-only: the tile widths a policy (0..11) picks for instances of the
  * given shapes, and the leaf's schedule in launch order, 4 ints per slot
- * (instance, m0, n0, unit): tiles (128 rows, or 256 for policies 4-7) go
+ * (instance, m0, n0, unit): tiles (128 rows, or 256 for policies 4-11) go
  * longest first to the persistent unit (a CTA, or a CTA pair) with the
  * least work so far, unit u runs slots u, u + G, u + 2G, ... (G = the
  * units, at most the current device's SMs, or half of them for pairs), and

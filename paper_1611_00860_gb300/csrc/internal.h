@@ -135,7 +135,8 @@ struct TcBatch {
   std::vector<int> bn;  // tile width of each instance (the policy's choice)
   // width rule (policy & 3): 0: 256, 1: 128, 2/3: cost model (light/heavy
   // tile overhead); policy 0-3 on single CTAs (128-row tiles), 4-7 on CTA
-  // pairs (256-row tiles)
+  // pairs (256-row tiles), 8-11 on CTA pairs converting the operands in the
+  // leaf (BF16x3)
   int policy = 2;
   int tile_m = 128;     // rows of an output tile (the policy's height)
   void* ws = nullptr;
@@ -149,6 +150,18 @@ struct TcBatch {
   int num_tiles = 0;   // slots of the schedule (output tiles and empty slots)
   int real_tiles = 0;  // output tiles
   int grid = 0;
+  // in-leaf conversion (policies 8-11, BF16x3): the operand records of each
+  // instance (index into the split's operand table, -1 for none), the
+  // flags (and claim counter) region, the chunk list the leaf's converters
+  // claim from, and the first round's split tiles
+  std::vector<int> op_a, op_b;
+  bool convert = false;
+  int* d_flags = nullptr;
+  size_t flags_count = 0;  // ints, the claim counter last
+  void* d_chunks = nullptr;
+  int num_chunks = 0;
+  void* d_pre_tiles = nullptr;
+  int num_pre_tiles = 0;
 };
 std::vector<int> batch_choose_bn(const std::vector<SgemmDesc>& d, int policy);
 // rows of a batch tile under a policy: 128 (single CTAs) or 256 (CTA pairs)

@@ -1920,7 +1920,7 @@ int hpvm_batch_plan(int count, const int64_t* M, const int64_t* N, const int64_t
                     int32_t* tiles, int64_t tile_cap, int64_t* num_tiles) {
   if (count < 0 || (count > 0 && (!M || !N || !K)) || !num_tiles)
     return fail(HPVM_ERR_INVALID_ARG, "bad arguments");
-  if (policy < 0 || policy > 7) return fail(HPVM_ERR_INVALID_ARG, "policy must be 0..7");
+  if (policy < 0 || policy > 11) return fail(HPVM_ERR_INVALID_ARG, "policy must be 0..11");
   std::vector<hpvm::SgemmDesc> d(count);
   for (int i = 0; i < count; ++i) {
     if (M[i] < 0 || N[i] < 0 || K[i] < 0) return fail(HPVM_ERR_SHAPE, "negative extent in instance %d", i);
@@ -1947,7 +1947,7 @@ int hpvm_batch_prepare(hpvm_ctx* ctx, hpvm_node* root, const void* records, size
                        int policy, hpvm_batch** out) {
   if (out) *out = nullptr;
   if (!ctx || !out || !records || count <= 0) return fail(HPVM_ERR_INVALID_ARG, "bad arguments");
-  if (policy < -1 || policy > 7) return fail(HPVM_ERR_INVALID_ARG, "policy must be -1 (tuned) or 0..7");
+  if (policy < -1 || policy > 11) return fail(HPVM_ERR_INVALID_ARG, "policy must be -1 (tuned) or 0..11");
   if (ctx->device < 0) return fail(HPVM_ERR_NO_DEVICE, "host-only context");
   cudaSetDevice(ctx->device);
   std::vector<hpvm::SgemmDesc> d(count);
@@ -1973,6 +1973,8 @@ int hpvm_batch_prepare(hpvm_ctx* ctx, hpvm_node* root, const void* records, size
     if (d[i].M > INT32_MAX / 2 || d[i].N > INT32_MAX / 2 || d[i].K > INT32_MAX / 2)
       return fail(HPVM_ERR_SHAPE, "instance %d is too large for a batch", i);
   }
+  if (policy >= 8 && tier != HPVM_TIER_BF16X3)
+    return fail(HPVM_ERR_INVALID_ARG, "policies 8..11 (in-leaf conversion) take the BF16X3 tier");
   auto b = std::make_unique<hpvm_batch>();
   b->ctx = ctx;
   b->tb.tier = tier;
@@ -2036,7 +2038,7 @@ int hpvm_batch_info(hpvm_batch* b, hpvm_batch_stats* out) {
   out->tier = b->tb.tier;
   out->policy = b->tb.policy;
   out->tiles = b->tb.real_tiles;
-  out->split_tiles = b->tb.num_split_tiles;
+  out->split_tiles = b->tb.convert ? b->tb.num_pre_tiles : b->tb.num_split_tiles;
   out->grid = b->tb.grid;
   out->tile_m = b->tb.tile_m;
   out->workspace_bytes = (int64_t)b->tb.ws_bytes;

@@ -216,6 +216,8 @@ constexpr int CV_WARPS = 2;     // warps 2 and 3
 constexpr int CV_MAX_ROUNDS = 64;
 constexpr int CV_TAB = 5;       // per round: A blocks [lo, hi), B blocks [lo, hi), first chunk
 constexpr uint32_t CV_SMEM = CV_WARPS * 2 * CV_PIECE_BYTES + (CV_MAX_ROUNDS + 1) * CV_TAB * 4;
+struct SplitOp;
+struct SplitTile;
 struct ConvParams {
   CUtensorMap src[2];  // FP32 op(A) and op(B)^T, rows contiguous: box of 32 rows x 64 K
   __nv_bfloat16* hi[2];
@@ -228,6 +230,13 @@ struct ConvParams {
   int Kp, num_kb;
   int kb_stride;       // num_kb rounded up to 4: a block's flags, 16-byte aligned
   int pre[2];          // blocks [0, pre) of each operand: converted before the launch
+  // a batch (the grouped leaf): the chunks in claim order, each (operand,
+  // first row (a multiple of 128), first K element (of 64), flag index),
+  // and the operands they name; flags and claim as above (the per-instance
+  // flag bases are in the instances' records)
+  const SplitTile* chunks;
+  const SplitOp* ops;
+  int num_chunks;
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -723,18 +732,25 @@ struct SplitOp {
   __nv_bfloat16* hi;
   __nv_bfloat16* lo;
 };
+// A tile of the batch's split (64 x 64), or a chunk of its in-leaf
+// conversion (128 rows x 64 K); flag: the in-leaf conversion's flag of its
+// chunk, or -1.
 struct SplitTile {
-  int op, r0, k0, pad;
+  int op, r0, k0, flag;
 };
 
-// The pre-pass of a whole batch in one launch: CTA i splits tile i.
+// The pre-pass of a whole batch in one launch: CTA i splits tile i. With
+// in-leaf conversion (flags given) it splits only the chunks the leaf's
+// first round reads and marks their flags; the leaf starts after this
+// kernel has finished, so nothing more orders them.
 template <int NPROD>
 __global__ void __launch_bounds__(256) split_batch(const SplitOp* __restrict__ ops,
-                                                   const SplitTile* __restrict__ tiles) {
+                                                   const SplitTile* __restrict__ tiles, int* flags) {
   const SplitTile t = tiles[blockIdx.x];
   const SplitOp o = ops[t.op];
   if (o.mmajor) split_tile_m<NPROD>(o.X, o.ld, o.rows, o.K, o.Kp, o.hi, o.lo, nullptr, t.r0, t.k0);
   else split_tile_k<NPROD>(o.X, o.ld, o.rows, o.K, o.Kp, o.hi, o.lo, nullptr, t.r0, t.k0);
+  if (flags && t.flag >= 0 && threadIdx.x == 0) flags[t.flag] = 1;
 }
 
 // X "k-major": element (r, k) at X[k + r*ld] (K contiguous).
@@ -1064,6 +1080,125 @@ __device__ __forceinline__ void cv_convert(const ConvParams& cv, const int* tab,
   __syncwarp();
 }
 
+// 4-byte asynchronous copy global -> shared (src_bytes 0: the destination is
+// zero-filled and nothing is read).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One converter warp of a batch's in-leaf conversion: the chunks of
+// cv.chunks in claim order, each in four pieces of 32 rows x 64 K staged by
+// 4-byte cp.async copies (any leading dimension, either layout of the FP32
+// operand; zeros past its rows and K) into two buffers, the next piece in
+// flight while this one is converted. A piece holds element (row i, k) at
+// k * 32 + (i ^ k % 32), so both layouts' copies and the conversion's reads
+// spread over the banks. The conversion and the release of the chunk's flag
+// are cv_convert's. cp.async waits on the warp's own copies only, which
+// always complete.
+__device__ __forceinline__ void cv_convert_batch(const ConvParams& cv, uint8_t* buf, int lane,
+                                                 volatile int* abort_flag) {
+  auto claim = [&]() -> int {
+    int c = cv.num_chunks;
+    if (lane == 0 && !*abort_flag) c = atomicAdd(cv.claim, 1);
+    return __shfl_sync(0xffffffffu, c, 0);
+  };
+  auto stage = [&](int c, int j, int b) {
+    const SplitTile ch = cv.chunks[c];
+    const SplitOp o = cv.ops[ch.op];
+    float* st = reinterpret_cast<float*>(buf + b * CV_PIECE_BYTES);
+    const int r0 = ch.r0 + j * CV_PIECE;
+    if (o.mmajor) {
+      // element (r, k) at X[r + k ld]: lane l copies row r0 + l of each K column
+      const int r = r0 + lane;
+#pragma unroll 4
+      for (int k = 0; k < CV_BK; ++k) {
+        const int kk = ch.k0 + k;
+        const bool in = r < o.rows && kk < o.K;
+        cp_async4(st + k * CV_PIECE + (lane ^ (k & 31)), in ? o.X + (int64_t)kk * o.ld + r : o.X, in ? 4u : 0u);
+      }
+    } else {
+      // element (r, k) at X[k + r ld]: lane l copies K elements l and l + 32 of each row
+#pragma unroll 4
+      for (int i = 0; i < CV_PIECE; ++i) {
+        const int r = r0 + i;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = lane + 32 * h, kk = ch.k0 + k;
+          const bool in = r < o.rows && kk < o.K;
+          cp_async4(st + k * CV_PIECE + (i ^ lane), in ? o.X + (int64_t)r * o.ld + kk : o.X, in ? 4u : 0u);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  int c = claim();
+  if (c >= cv.num_chunks) return;
+  stage(c, 0, 0);
+  int j = 0, b = 0;
+  for (;;) {
+    // the next piece: of this chunk, or of the next claimed one
+    int nc = c, nj = j + 1;
+    if (nj == CV_PIECES) {
+      nc = claim();
+      nj = 0;
+    }
+    const bool has_next = nc < cv.num_chunks;
+    __syncwarp();  // every lane is done reading buffer b ^ 1 (the piece converted last)
+    if (has_next) {
+      stage(nc, nj, b ^ 1);
+      cp_async_wait<1>();  // this piece's copies (the next one's may still fly)
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();  // every lane's copies of this piece are visible to the warp
+    const SplitTile ch = cv.chunks[c];
+    const SplitOp o = cv.ops[ch.op];
+    const float* st = reinterpret_cast<const float*>(buf + b * CV_PIECE_BYTES);
+    const int g8 = (lane & 7) * 8;
+    const int k0 = ch.k0 + g8;
+    if (k0 < o.Kp) {
+      __nv_bfloat16* hp = o.hi + k0;
+      __nv_bfloat16* lp = o.lo + k0;
+#pragma unroll 1
+      for (int t = 0; t < CV_PIECE / 4; ++t) {
+        const int r = (lane >> 3) + 4 * t;
+        const int row = ch.r0 + j * CV_PIECE + r;
+        if (row < o.rows) {
+          __align__(16) __nv_bfloat16 h[8];
+          __align__(16) __nv_bfloat16 l[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int k = g8 + u;
+            split_pair(st[k * CV_PIECE + (r ^ (k & 31))], h[u], l[u]);
+          }
+          *reinterpret_cast<uint4*>(hp + (int64_t)row * o.Kp) = *reinterpret_cast<const uint4*>(h);
+          *reinterpret_cast<uint4*>(lp + (int64_t)row * o.Kp) = *reinterpret_cast<const uint4*>(l);
+        }
+      }
+    }
+    if (j + 1 == CV_PIECES) {
+      // the chunk's planes are written: visible to other CTAs' TMA loads,
+      // then its flag released
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_release_gpu(cv.flags + ch.flag, 1);
+    }
+    if (!has_next) break;
+    c = nc;
+    j = nj;
+    b ^= 1;
+  }
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
 // One instance of a batch of independent sgemm DFGs (device memory): its
 // four operand-plane tensor maps (64-byte aligned), its result, and the tile
 // width bn (64, 128 or 256 columns) its schedule chose.
@@ -1073,7 +1208,10 @@ struct GroupInst {
   int64_t ldc;
   int M, N, K, bn;
   float alpha, beta;
-  int pad[10];
+  // in-leaf conversion: the flags of A's 128-row blocks start at flag_a
+  // (block b's slab k at flag_a + b kb_stride + k), B's at flag_b
+  int flag_a, flag_b, kb_stride;
+  int pad[7];
 };
 static_assert(sizeof(GroupInst) % 64 == 0, "tensor maps stay 64-byte aligned in an array");
 // One output tile of the batch's schedule, with what every role needs of
@@ -1126,9 +1264,9 @@ __global__ void __launch_bounds__(THREADS, 1)
              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
              const __grid_constant__ CUtensorMap tmA_lo2, const __grid_constant__ CUtensorMap tmB_lo2,
              TcParams p, GroupParams gp, const __grid_constant__ ConvParams cv) {
-  static_assert(!(GROUPED && PAIR) || (EPI == 0 && !CONVERT && MODE != 8 && MODE != 6),
+  static_assert(!(GROUPED && PAIR) || (EPI == 0 && MODE != 8 && MODE != 6),
                 "batches on pairs: the BF16x3 and BF16 leaves, plain epilogue");
-  static_assert(!CONVERT || (MODE == 3 && PAIR && !GROUPED && Cfg<MODE, PAIR>::BK == CV_BK),
+  static_assert(!CONVERT || (MODE == 3 && PAIR && Cfg<MODE, PAIR>::BK == CV_BK),
                 "in-leaf conversion: the BF16x3 leaf on pairs, one chunk per slab");
   static_assert(MODE != 6 || (!GROUPED && EPI == 0), "BF16x6: single instances, plain epilogue");
   using C_ = Cfg<MODE, PAIR>;
@@ -1271,7 +1409,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     *abort_flag = 0;
     mbar_init(drainbar, 1);
     *issued_sh = 0;
-    if constexpr (CONVERT) {
+    if constexpr (CONVERT && !GROUPED) {
       for (int b = 0; b < 2 * CV_WARPS; ++b) mbar_init(&cvbar[b], 1);
       // Round r of the grouped order runs tiles [r U, (r + 1) U) (U units).
       // Row tile rt is first used by tile rt * gn0 (group 0), column tile
@@ -1361,7 +1499,17 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t ready_a = 0xFu, ready_b = 0xFu;
         const int* flag_a = nullptr;
         const int* flag_b = nullptr;
-        if constexpr (CONVERT) {
+        if constexpr (CONVERT && GROUPED) {
+          // a batch: this CTA's A block and B block (its bn / 2 rows of B lie
+          // in one 128-row block) of the tile's instance; a block split
+          // before the launch has its flags set
+          const GroupInst* in = gp.insts + cur.inst;
+          flag_a = cv.flags + in->flag_a + (int64_t)(ma / CV_ROWS) * in->kb_stride;
+          flag_b = cv.flags + in->flag_b + (int64_t)(nb / CV_ROWS) * in->kb_stride;
+          done_a = ma >= v.M;
+          done_b = nb >= v.N;
+          if (done_a && done_b) fence_acquire_for_tma();
+        } else if constexpr (CONVERT) {
           const int ba = ma / CV_ROWS, bb = cv.blocks[0] + nb / CV_ROWS;
           flag_a = cv.flags + (int64_t)ba * cv.kb_stride;
           flag_b = cv.flags + (int64_t)bb * cv.kb_stride;
@@ -1503,7 +1651,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       // staging buffers (the next piece's TMA load in flight while this one
       // is converted); lane l converts row l of a piece
       const int w = warp - 2;
-      if constexpr (CONVERT)
+      if constexpr (CONVERT && GROUPED)
+        cv_convert_batch(cv, cvbuf + w * 2 * CV_PIECE_BYTES, lane, abort_flag);
+      else if constexpr (CONVERT)
         cv_convert(cv, cvtab, cvbar + 2 * w, cvbuf + w * 2 * CV_PIECE_BYTES, lane, abort_flag, p.status, limit_ns);
     }
     __syncwarp();
@@ -2443,9 +2593,25 @@ cudaError_t launch_batch_kernels(const TcBatch& b, const DeviceStatus& st, cudaS
                                  const LaunchHooks* hooks) {
   using C_ = Cfg<MODE>;
   constexpr int NPROD = MODE == 3 ? 3 : 1;
-  if (b.num_split_tiles > 0) {
+  ConvParams cvp{};
+  if (b.convert) {
+    // flags and claim counter zeroed, then the first round's blocks split
+    // (marking their flags); the leaf's converters do the rest
+    cudaError_t e = cudaMemsetAsync(b.d_flags, 0, b.flags_count * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if (b.num_pre_tiles > 0) {
+      split_batch<NPROD><<<b.num_pre_tiles, 256, 0, s>>>(static_cast<const SplitOp*>(b.d_ops),
+                                                         static_cast<const SplitTile*>(b.d_pre_tiles), b.d_flags);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    cvp.flags = b.d_flags;
+    cvp.claim = b.d_flags + (b.flags_count - 4);
+    cvp.chunks = static_cast<const SplitTile*>(b.d_chunks);
+    cvp.ops = static_cast<const SplitOp*>(b.d_ops);
+    cvp.num_chunks = b.num_chunks;
+  } else if (b.num_split_tiles > 0) {
     split_batch<NPROD><<<b.num_split_tiles, 256, 0, s>>>(static_cast<const SplitOp*>(b.d_ops),
-                                                         static_cast<const SplitTile*>(b.d_split_tiles));
+                                                         static_cast<const SplitTile*>(b.d_split_tiles), nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -2466,13 +2632,23 @@ cudaError_t launch_batch_kernels(const TcBatch& b, const DeviceStatus& st, cudaS
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(b.grid);
     cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = Cfg<MODE, true>::SMEM_BYTES;
+    cfg.dynamicSmemBytes = Cfg<MODE, true>::SMEM_BYTES + (b.convert ? CV_SMEM : 0);
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     hook_begin(hooks, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, sgemm_tc<MODE, 0, true, true, false>, unused[0], unused[1], unused[2],
-                                       unused[3], unused[4], unused[5], prm, gp, ConvParams{});
+    cudaError_t e;
+    if constexpr (MODE == 3) {
+      if (b.convert)
+        e = cudaLaunchKernelEx(&cfg, sgemm_tc<3, 0, true, true, true>, unused[0], unused[1], unused[2], unused[3],
+                               unused[4], unused[5], prm, gp, cvp);
+      else
+        e = cudaLaunchKernelEx(&cfg, sgemm_tc<3, 0, true, true, false>, unused[0], unused[1], unused[2], unused[3],
+                               unused[4], unused[5], prm, gp, cvp);
+    } else {
+      e = cudaLaunchKernelEx(&cfg, sgemm_tc<MODE, 0, true, true, false>, unused[0], unused[1], unused[2],
+                             unused[3], unused[4], unused[5], prm, gp, cvp);
+    }
     hook_end(hooks, s);
     return e;
   }
@@ -2585,11 +2761,12 @@ int batch_schedule(const std::vector<SgemmDesc>& d, const std::vector<int>& bn, 
 // The grouped leaf's kernel attributes (dynamic shared memory, register
 // split check) and how many persistent units it runs at once: one CTA per
 // SM, or (PAIR) the clusters of two that fit, at most half the SMs.
-template <int MODE, bool PAIR>
+template <int MODE, bool PAIR, bool CONVERT = false>
 cudaError_t batch_kernel_setup(int* units) {
   using C_ = Cfg<MODE, PAIR>;
-  auto kernel = sgemm_tc<MODE, 0, true, PAIR, false>;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM_BYTES);
+  auto kernel = sgemm_tc<MODE, 0, true, PAIR, CONVERT>;
+  constexpr uint32_t smem = C_::SMEM_BYTES + (CONVERT ? CV_SMEM : 0);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = check_register_split(kernel);
   if (e != cudaSuccess) return e;
   if constexpr (!PAIR) {
@@ -2602,7 +2779,7 @@ cudaError_t batch_kernel_setup(int* units) {
     attr[0].val.clusterDim.z = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = C_::SMEM_BYTES;
+    cfg.dynamicSmemBytes = smem;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cfg.gridDim = dim3(2 * (num_sms() / 2));
@@ -2639,9 +2816,13 @@ int tc_batch_build(TcBatch* b, std::string* err) {
     // split pre-pass tables (independent of the tile widths)
     std::vector<SplitOp> ops;
     std::vector<SplitTile> st;
+    b->op_a.assign(count, -1);
+    b->op_b.assign(count, -1);
     for (int i = 0; i < count; ++i) {
       const SgemmDesc& d = b->d[i];
       if (d.M <= 0 || d.N <= 0 || d.K <= 0) continue;
+      b->op_a[i] = (int)ops.size();
+      b->op_b[i] = (int)ops.size() + 1;
       const WsLayout L = ws_layout(d, mode);
       uint8_t* w = static_cast<uint8_t*>(b->ws) + b->plane_off[i];
       const SplitOp a{d.A, d.lda, d.transA ? 0 : 1, (int)d.M, (int)d.K, (int)L.Kp,
@@ -2652,7 +2833,7 @@ int tc_batch_build(TcBatch* b, std::string* err) {
         const int id = (int)ops.size();
         ops.push_back(o);
         for (int r0 = 0; r0 < o.rows; r0 += 64)
-          for (int k0 = 0; k0 < o.Kp; k0 += 64) st.push_back({id, r0, k0, 0});
+          for (int k0 = 0; k0 < o.Kp; k0 += 64) st.push_back({id, r0, k0, -1});
       }
     }
     if (upload(&b->d_ops, ops, err) || upload(&b->d_split_tiles, st, err)) return -1;
@@ -2661,8 +2842,15 @@ int tc_batch_build(TcBatch* b, std::string* err) {
   // kernel attributes first (so a run can be captured into a CUDA graph),
   // and the persistent units the leaf can run at once: CTAs, or CTA pairs
   const bool pair = b->policy >= 4;
+  b->convert = b->policy >= 8;
+  if (b->convert && mode != 3) {
+    *err = "in-leaf conversion (policies 8-11) takes the BF16x3 tier";
+    return -1;
+  }
   int units = 0;
-  cudaError_t e = mode == 3 ? (pair ? batch_kernel_setup<3, true>(&units) : batch_kernel_setup<3, false>(&units))
+  cudaError_t e = mode == 3 ? (b->convert ? batch_kernel_setup<3, true, true>(&units)
+                               : pair     ? batch_kernel_setup<3, true>(&units)
+                                          : batch_kernel_setup<3, false>(&units))
                             : (pair ? batch_kernel_setup<1, true>(&units) : batch_kernel_setup<1, false>(&units));
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
@@ -2726,6 +2914,87 @@ int tc_batch_build(TcBatch* b, std::string* err) {
     g.alpha = in.alpha;
     g.beta = in.beta;
   }
+  if (b->convert) {
+    // Flags: per instance, its A blocks' then its B blocks' (128 rows each),
+    // a block's slabs (64 K each) padded to 4; the claim counter last.
+    size_t off = 0;
+    std::vector<int> kb4(count, 0);
+    for (int i = 0; i < count; ++i) {
+      const SgemmDesc& d = b->d[i];
+      insts[i].flag_a = insts[i].flag_b = -1;
+      if (b->op_a[i] < 0) continue;
+      kb4[i] = (int)(((d.K + CV_BK - 1) / CV_BK + 3) / 4 * 4);
+      insts[i].kb_stride = kb4[i];
+      insts[i].flag_a = (int)off;
+      off += (size_t)((d.M + CV_ROWS - 1) / CV_ROWS) * kb4[i];
+      insts[i].flag_b = (int)off;
+      off += (size_t)((d.N + CV_ROWS - 1) / CV_ROWS) * kb4[i];
+    }
+    if (off + 4 > (size_t)INT32_MAX) {
+      *err = "too many conversion chunks for one batch";
+      return -1;
+    }
+    b->flags_count = off + 4;  // (the counter at off, 16-byte padding)
+    // Chunks in the order the schedule first reads them: round r = slots
+    // [r G, (r + 1) G); the blocks round 0 reads are split before the launch
+    // (64 x 64 tiles that mark their chunks' flags), those a later round
+    // reads first are converted in the leaf, slab by slab across the round's
+    // new blocks.
+    struct Blk {
+      int inst, op, blk;
+    };
+    std::vector<char> seen(off, 0);  // by a block's first flag
+    std::vector<SplitTile> pre, chunks;
+    const int slots = (int)(tiles.size() / 4);
+    for (int r0 = 0; r0 < slots; r0 += G) {
+      std::vector<Blk> fresh;
+      for (int t = r0; t < std::min(slots, r0 + G); ++t) {
+        const int i = tiles[4 * t];
+        if (i < 0 || b->op_a[i] < 0) continue;
+        const SgemmDesc& d = b->d[i];
+        const int m0 = tiles[4 * t + 1], n0 = tiles[4 * t + 2], bn = b->bn[i];
+        const int ablk = (int)((d.M + CV_ROWS - 1) / CV_ROWS), bblk = (int)((d.N + CV_ROWS - 1) / CV_ROWS);
+        for (int q = m0 / CV_ROWS; q < std::min(ablk, (m0 + b->tile_m + CV_ROWS - 1) / CV_ROWS); ++q)
+          fresh.push_back({i, 0, q});
+        for (int q = n0 / CV_ROWS; q < std::min(bblk, (n0 + bn + CV_ROWS - 1) / CV_ROWS); ++q)
+          fresh.push_back({i, 1, q});
+      }
+      std::vector<Blk> round;
+      for (const Blk& x : fresh) {
+        const int f = (x.op ? insts[x.inst].flag_b : insts[x.inst].flag_a) + x.blk * kb4[x.inst];
+        if (seen[f]) continue;
+        seen[f] = 1;
+        round.push_back(x);
+      }
+      int max_kb = 0;
+      for (const Blk& x : round) max_kb = std::max(max_kb, kb4[x.inst]);
+      for (int kb = 0; kb < max_kb; ++kb) {
+        for (const Blk& x : round) {
+          const SgemmDesc& d = b->d[x.inst];
+          const int nkb = (int)((d.K + CV_BK - 1) / CV_BK);
+          if (kb >= nkb) continue;
+          const int opi = x.op ? b->op_b[x.inst] : b->op_a[x.inst];
+          const int f = (x.op ? insts[x.inst].flag_b : insts[x.inst].flag_a) + x.blk * kb4[x.inst] + kb;
+          const int rows = (int)(x.op ? d.N : d.M);
+          if (r0 == 0) {
+            for (int rr = x.blk * CV_ROWS; rr < std::min(rows, (x.blk + 1) * CV_ROWS); rr += 64)
+              pre.push_back({opi, rr, kb * CV_BK, f});
+          } else {
+            chunks.push_back({opi, x.blk * CV_ROWS, kb * CV_BK, f});
+          }
+        }
+      }
+    }
+    free_dev(reinterpret_cast<void**>(&b->d_flags));
+    if (cudaMalloc(reinterpret_cast<void**>(&b->d_flags), b->flags_count * sizeof(int)) != cudaSuccess) {
+      b->d_flags = nullptr;
+      *err = "cannot allocate the in-leaf conversion's flags";
+      return -1;
+    }
+    if (upload(&b->d_chunks, chunks, err) || upload(&b->d_pre_tiles, pre, err)) return -1;
+    b->num_chunks = (int)chunks.size();
+    b->num_pre_tiles = (int)pre.size();
+  }
   if (upload(&b->d_insts, insts, err) || upload(&b->d_tiles, gt, err)) return -1;
   b->num_tiles = (int)gt.size();
   b->grid = pair ? 2 * G : G;
@@ -2744,7 +3013,9 @@ int tc_batch_autotune(TcBatch* b, const DeviceStatus& st, cudaStream_t s, int re
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int pol = 0; pol < 8; ++pol) {  // four width rules x single CTAs, CTA pairs
+  // four width rules x single CTAs, CTA pairs, CTA pairs converting in the leaf (BF16x3)
+  const int policies = mode_of_tier(b->tier) == 3 ? 12 : 8;
+  for (int pol = 0; pol < policies; ++pol) {
     b->policy = pol;
     if (tc_batch_build(b, err)) break;
     if (tc_batch_run(*b, st, s, nullptr) != cudaSuccess) break;  // warm-up
@@ -2782,6 +3053,9 @@ cudaError_t launch_wait_selftest(const DeviceStatus& st, uint64_t limit_ns, cuda
 }
 
 void tc_batch_free(TcBatch* b) {
+  free_dev(reinterpret_cast<void**>(&b->d_flags));
+  free_dev(&b->d_chunks);
+  free_dev(&b->d_pre_tiles);
   free_dev(&b->ws);
   free_dev(&b->d_ops);
   free_dev(&b->d_split_tiles);

@@ -9,9 +9,9 @@ def _grid(M, N, bn, tm=128):
     return {(m0, n0) for m0 in range(0, M, tm) for n0 in range(0, N, bn)}
 
 
-@pytest.mark.parametrize("policy", range(8))
+@pytest.mark.parametrize("policy", range(12))
 def test_schedule_covers_every_tile_once(policy):
-    # policies 4-7: 256-row tiles on CTA pairs, the units half as many
+    # policies 4-11: 256-row tiles on CTA pairs, the units half as many
     shapes = W.batched_shapes(64, seed=5)
     M, N, K = zip(*shapes)
     bn, slots = H.hpvm_batch_plan(M, N, K, policy)
@@ -57,6 +57,8 @@ def test_pair_policies_halve_the_units():
     g1 = max(t[3] for t in H.hpvm_batch_plan(M, N, K, 2)[1]) + 1
     g2 = max(t[3] for t in H.hpvm_batch_plan(M, N, K, 6)[1]) + 1
     assert g2 <= max(1, g1 // 2)
+    # the in-leaf conversion's policies schedule as the pair policies do
+    assert H.hpvm_batch_plan(M, N, K, 10) == H.hpvm_batch_plan(M, N, K, 6)
     # 256-row tiles: no tile starts at an odd multiple of 128 rows
     assert all(t[1] % 256 == 0 for t in H.hpvm_batch_plan(M, N, K, 6)[1] if t[0] >= 0)
 
@@ -73,6 +75,6 @@ def test_batched_workload_plan():
 
 def test_bad_policy_and_shapes():
     with pytest.raises(H.HpvmError):
-        H.hpvm_batch_plan([1], [1], [1], 8)
+        H.hpvm_batch_plan([1], [1], [1], 12)
     with pytest.raises(H.HpvmError):
         H.hpvm_batch_plan([-1], [1], [1], 0)

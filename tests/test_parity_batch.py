@@ -1,9 +1,11 @@
 """Batches of independent sgemm DFG instances on the GPU (one batched split
 pre-pass launch and one persistent grouped leaf launch), through the C-ABI:
 every instance against the FP64 oracle for every policy (four tile-width
-rules, on single CTAs with 128-row tiles and on CTA pairs with 256-row
-tiles), the batch against one launch per instance (bit for bit, on either
-tile height), a CUDA-graph replay against a direct run, and the autotuner."""
+rules, on single CTAs with 128-row tiles, on CTA pairs with 256-row tiles,
+and on CTA pairs converting the operands inside the leaf), the batch against
+one launch per instance (bit for bit, on either tile height and with the
+in-leaf conversion), a CUDA-graph replay against a direct run, and the
+autotuner."""
 import math
 
 import numpy as np
@@ -47,8 +49,10 @@ def small_batch():
 
 
 @pytest.mark.parametrize("tier", [H.HPVM_TIER_BF16X3, H.HPVM_TIER_BF16])
-@pytest.mark.parametrize("policy", range(8))
+@pytest.mark.parametrize("policy", range(12))
 def test_every_instance_matches_oracle(cuda_device, small_batch, tier, policy):
+    if policy >= 8 and tier != H.HPVM_TIER_BF16X3:
+        pytest.skip("in-leaf conversion takes the BF16x3 tier")
     probs, refs = small_batch
     dev = _device(probs)
     b = BatchDFG(0)
@@ -67,7 +71,7 @@ def test_every_instance_matches_oracle(cuda_device, small_batch, tier, policy):
         b.close()
 
 
-@pytest.mark.parametrize("policy", [0, 4])
+@pytest.mark.parametrize("policy", [0, 4, 8])
 def test_batch_equals_one_launch_per_instance(cuda_device, small_batch, policy):
     probs, _ = small_batch
     dev_b = _device(probs)
@@ -76,7 +80,7 @@ def test_batch_equals_one_launch_per_instance(cuda_device, small_batch, policy):
     s = SgemmDFG(0)
     try:
         # 256-wide tiles as the single leaf's, 128 rows a CTA (0) or 256 a
-        # CTA pair (4, as the single leaf)
+        # CTA pair (4, as the single leaf; 8 with the planes made in the leaf)
         b.prepare(probs, dev_b, tier=H.HPVM_TIER_BF16X3, policy=policy)
         b.run()
         for p, t in zip(probs, dev_s):
@@ -125,7 +129,7 @@ def test_autotune_picks_a_policy_and_keeps_results_right(cuda_device, small_batc
     try:
         b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=0)
         best, ms = b.autotune(reps=2)
-        assert best in range(8) and ms > 0
+        assert best in range(12) and ms > 0
         assert b.info()["policy"] == best
         # a new batch of the same shapes starts from the tuned policy
         b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=-1)
@@ -141,7 +145,7 @@ def test_autotune_picks_a_policy_and_keeps_results_right(cuda_device, small_batc
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("policy", [2, 6])
+@pytest.mark.parametrize("policy", [2, 6, 10])
 def test_batched_workload_512_instances(cuda_device, policy):
     # the batched workload: 512 instances, M, N, K log-uniform in [32, 2048]
     shapes = W.batched_shapes()
@@ -164,5 +168,39 @@ def test_batched_workload_512_instances(cuda_device, policy):
             worst = max(worst, err)
         print(f"512-instance batch: worst normwise error {worst:.3e}; {b.info()}")
         assert worst <= 5e-6 and math.isfinite(worst)
+    finally:
+        b.close()
+
+
+def test_in_leaf_conversion_needs_bf16x3(cuda_device, small_batch):
+    probs, _ = small_batch
+    dev = _device(probs)
+    b = BatchDFG(0)
+    try:
+        with pytest.raises(H.HpvmError) as e:
+            b.prepare(probs, dev, tier=H.HPVM_TIER_BF16, policy=8)
+        assert e.value.code == H.HPVM_ERR_INVALID_ARG
+    finally:
+        b.close()
+
+
+def test_in_leaf_conversion_repeats_bit_for_bit(cuda_device, small_batch):
+    # the converters claim chunks in whatever order the CTAs reach them; the
+    # planes, and so C, must not depend on it
+    probs, _ = small_batch
+    dev = _device(probs)
+    C0 = [t[2].clone() for t in dev]
+    b = BatchDFG(0)
+    try:
+        b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=10)
+        outs = []
+        for _ in range(3):
+            for (_, _, C), c0 in zip(dev, C0):
+                C.copy_(c0)
+            b.run()
+            torch.cuda.synchronize()
+            outs.append([t[2].cpu().view(torch.int32).clone() for t in dev])
+        for later in outs[1:]:
+            assert all(torch.equal(x, y) for x, y in zip(outs[0], later))
     finally:
         b.close()
