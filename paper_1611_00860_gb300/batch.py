@@ -1,11 +1,13 @@
 """Batches of independent sgemm DFG instances in one persistent launch.
 
 Argument marshalling only: the instances are records of the sgemm example
-graph (one per instance); ``hpvm_batch_prepare`` lowers each, picks every
-instance's tile width from a policy (or the one ``hpvm_batch_autotune``
-measured best), and lays the operand planes and schedule out on the device;
-``hpvm_batch_run`` enqueues the batched split pre-pass and the grouped
-persistent leaf. ``capture`` records a run in a CUDA graph for replay.
+graph (one per instance); ``hpvm_batch_prepare`` lowers each, takes the
+tile height (a CTA or a CTA pair), every instance's tile width and where the
+operand planes are made (a split launch, or inside the leaf) from a policy
+(or the one ``hpvm_batch_autotune`` measured best), and lays the operand
+planes and schedule out on the device; ``hpvm_batch_run`` enqueues the
+batched split pre-pass and the grouped persistent leaf. ``capture`` records
+a run in a CUDA graph for replay.
 """
 from __future__ import annotations
 

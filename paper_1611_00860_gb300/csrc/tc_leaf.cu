@@ -28,8 +28,9 @@
 //       roundup(K, 8) elements.
 //   quant_fp8: FP32 op(X) -> E4M3 codes and one FP32 scale per 128 x 128
 //       block.
-//   sgemm_tc<MODE, EPI, GROUPED, PAIR>: persistent; warp 0 issues TMA loads,
-//       warp 1 allocates tensor memory and issues the MMAs, warps 4..11
+//   sgemm_tc<MODE, EPI, GROUPED, PAIR, CONVERT>: persistent; warp 0 issues
+//       TMA loads, warp 1 allocates tensor memory and issues the MMAs,
+//       warps 2, 3 convert FP32 operands into planes (CONVERT), warps 4..11
 //       read the accumulator (tcgen05.ld) into FP32 registers and write C
 //       (with a merged elementwise leaf, EPI), and on request the BF16
 //       planes of C a later leaf reads (forwarded to the next stage of a
@@ -102,7 +103,7 @@ struct Cfg {
   static constexpr int ELEM_BYTES = FP8 ? 1 : 2;
   // One K slab row in shared memory: 128 bytes (128-byte swizzle), so a
   // slab carries 4 K steps and the per-slab handshake is paid once per 4.
-  // BF16x3 on a single CTA (the batch) keeps 64-byte rows (64-byte swizzle):
+  // BF16x3 on a single CTA (batch policies 0-3) keeps 64-byte rows (64-byte swizzle):
   // its 4 planes of 384 rows would leave two 96 KiB stages; on a pair each
   // CTA stages 256 rows and three 64 KiB stages fit. BF16x6 (on pairs)
   // takes 64-byte rows: six 128-row planes per stage in four 48 KiB stages,
@@ -1254,10 +1255,11 @@ struct TileView {
 // and the leader CTA (rank 0) issues the pair's MMAs. Roles per CTA:
 //   warp 0      TMA producer (both CTAs: each loads its own half)
 //   warp 1      tensor-memory allocation; MMA issuer (leader only)
-//   warps 2, 3  idle (they complete the control warpgroup)
+//   warps 2, 3  idle (they complete the control warpgroup), or CONVERT
 //   warps 4-11  epilogue (both CTAs: each drains its own 128 rows)
-// CONVERT: warps 2 and 3 write the operand planes (see ConvParams) and the
-// producer waits for each slab's chunks.
+// CONVERT: warps 2 and 3 write the operand planes (see ConvParams; a batch
+// (GROUPED): cv_convert_batch) and the producer waits for each slab's
+// chunks.
 template <int MODE, int EPI, bool GROUPED, bool PAIR, bool CONVERT = false>
 __global__ void __launch_bounds__(THREADS, 1)
     sgemm_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
