@@ -91,3 +91,40 @@ def test_waits_that_run_out_mid_tile_drain_and_return(dfg, name, tier, shape, fl
                  for (i0, j0) in blocks]
         assert O.block_errors(pairs) <= TOL[tier]
 
+
+
+def test_batch_waits_that_run_out_drain_and_return(cuda_device):
+    # The grouped leaves drain too: single CTAs, CTA pairs (whose stages carry
+    # bytes that differ from tile to tile) and pairs converting their own
+    # operands. The autotuner runs every policy with a 1 us limit and reports
+    # the context's status at its end; then, with the default limit, each
+    # kind of leaf computes the oracle's product.
+    from paper_1611_00860_gb300.batch import BatchDFG
+    shapes = W.batched_shapes(48, 64, 512, seed=9)
+    probs = [W.sgemm_problem(m, n, k, seed=900 + i, alpha=1.0, beta=0.0) for i, (m, n, k) in enumerate(shapes)]
+    dev = [tuple(t.cuda() for t in (p.A, p.B, p.C)) for p in probs]
+    refs = [O.sgemm_f64(p) for p in probs]
+    b = BatchDFG(0)
+    try:
+        b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=4)
+        H.hpvm_set_wait_limit(b.ctx, 1)
+        t0 = time.perf_counter()
+        with pytest.raises(H.HpvmError) as e:
+            b.autotune(reps=1)
+        dt = time.perf_counter() - t0
+        assert e.value.code == H.HPVM_ERR_DEVICE_FAULT, str(e.value)
+        bits = _status_bits(e.value)
+        assert bits != 0 and not (bits & ST_DRAIN), hex(bits)
+        assert dt < 5.0, dt
+        torch.cuda.synchronize()
+        H.hpvm_set_wait_limit(b.ctx, 0)
+        for policy in (1, 4, 8):
+            b.prepare(probs, dev, tier=H.HPVM_TIER_BF16X3, policy=policy)
+            b.run()
+            torch.cuda.synchronize()
+            for p, (_, _, C), ref in zip(probs, dev, refs):
+                got = W.col_major(C.cpu(), p.M, p.N, p.ldc).double().numpy()
+                assert O.normwise_rel_err(got, ref) <= 5e-6, (policy, p.M, p.N, p.K)
+    finally:
+        H.hpvm_set_wait_limit(b.ctx, 0)
+        b.close()
